@@ -291,7 +291,7 @@ static double q_entry(const uint8_t *blk, int f, int64_t idx) {
  *           result of applying the stored low-precision operator);
  *   mode 1: "compute in p_l": each row is a binary32 dot product accumulated in natural
  *           order j = 0, 1, ... with fused multiply-add, acc = fmaf(Q_ij, r-hat_j, acc),
- *           then widened and multiplied by s_b (exact). */
+ *           multiplied by s_b in binary32 (a power of two), then widened to binary64. */
 void orc_apply(int32_t nb, const int32_t *block_ptr, const uint8_t *fmt, const uint8_t *pool,
                const int64_t *qoff, const float *scale, const double *r, double *z, int32_t mode) {
     for (int32_t b = 0; b < nb; ++b) {
@@ -317,7 +317,7 @@ void orc_apply(int32_t nb, const int32_t *block_ptr, const uint8_t *fmt, const u
                     float q = (float)q_entry(blk, f, (int64_t)i * bs + j);
                     acc = fmaf(q, rh, acc);
                 }
-                z[s + i] = (double)acc * (double)scale[b];
+                z[s + i] = (double)(acc * scale[b]);
             }
         }
     }
