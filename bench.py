@@ -1,0 +1,356 @@
+"""Benchmark: time-to-solution of mixed-precision BJAC-PCG vs uniform binary64 BJAC-PCG.
+
+Workload: 3D 7-point variable-coefficient diffusion on a 128^3 grid (n = 2,097,152,
+nnz = 14,581,760, Table 4.1 size), coefficient log-uniform in [1e-3, 1e3] constant on 8^3
+subcubes, harmonic-mean faces, diagonal shift 1/dt = 100; x* ~ U[-1, 1] (seeded), b = A x*,
+x0 = 0, tol 1e-10 on ||r||/||b||. A step is one bjac_setup + pcg_solve + bjac_destroy of
+that system with the chosen policy (every kernel of the hot path runs in it). The
+matrix (175 MB) and the block inverses (134-537 MB) are larger than the 129 MB L2, so no
+explicit L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank solves its own system (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-solution at ||r||/||b||≤1e-10: mixed vs FP64 BJAC on 1 GB300; HBM GB/s"
+TOL = 1e-10
+MAXIT = 5000
+FMT = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16s": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=128, help="grid side (128 = the named workload)")
+    ap.add_argument("--bs", type=int, default=32)
+    ap.add_argument("--fmt", default="bf16", choices=list(FMT))
+    ap.add_argument("--no-modes", action="store_true", help="skip the per-mode table")
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"diffusion3d-7pt-{args.m}^3-subcube8-logU[1e-3,1e3]-dt1e-2",
+            "n": args.m ** 3, "block_size": args.bs, "mixed_format": args.fmt, "tol": TOL,
+            "step": "bjac_setup + pcg_solve + bjac_destroy", "l2": "inputs larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        self.out.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def algorithmic_bytes(n, nnz, nb, bs, fmt_bytes):
+    """Bytes each kernel of one PCG iteration must move (values read or written once)."""
+    spmv = 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n                 # A, rowptr, p, q
+    apply_fused = nb * bs * bs * fmt_bytes + 4 * nb * (fmt_bytes == 2) + 8 * n * 4   # Q, scales, r, q in; r, z out
+    update_xp = 8 * n * 5                                          # x, p, z in; x, p out
+    return {"spmv": spmv, "apply": apply_fused, "update_xp": update_xp}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel, {}).get(workload_key)
+    if not e:
+        return None
+    if e.get("source_hash") != source_hash(e.get("sources", [])):
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2407_15973_gb300 import binding as B
+    from paper_2407_15973_gb300 import problems as PB
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    B.lib()
+    pr = PB.make_problem("subcube3d", seed=rank, m=args.m, bs=args.bs)
+    A, n, nnz, nb = pr.A, pr.A.n, pr.A.nnz, pr.nb
+    dA = B.DeviceCSR(A)
+    xs = torch.as_tensor(pr.x_star).cuda()
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.bjac_spmv(dA, xs, b)                       # input construction, not timed
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def step(pol, want_stats=False):
+        x.zero_()
+        h = B.bjac_setup(dA, pr.block_ptr, **pol)
+        st = h.solve(b, x, tol=TOL, maxit=MAXIT)
+        h.close()
+        return st
+
+    def timed(pol, k, w):
+        for _ in range(w):
+            st = step(pol)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(k):
+            stats.append(step(pol))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats
+
+    head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt])
+    with ClockSampler(dev) as clk:
+        ms_mixed, st_mixed = timed(head, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM), args.steps, args.warmup)
+    sm = st_mixed[-1]
+    s64 = st_fp64[-1]
+    err_x = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+
+    # per-mode table (setup + solve, one warm-up, two timed)
+    modes = {}
+    if not args.no_modes:
+        table = {"uniform-fp64": dict(select=B.SELECT_UNIFORM)}
+        for f in ("fp32", "bf16", "fp16s"):
+            table[f"fmp-{f}"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[f])
+        table["amp-hl10-bf16"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"], temporal=B.TEMPORAL_HL,
+                                      adp_tol=10.0)
+        table["amp-lh1e-5-bf16"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"], temporal=B.TEMPORAL_LH,
+                                        adp_tol=1e-5)
+        table["rule"] = dict(select=B.SELECT_RULE)
+        for name, pol in table.items():
+            ms, sts = timed(pol, 2, 1)
+            s = sts[-1]
+            modes[name] = {"ms": round(ms, 3), "solve_ms": round(s["solve_ms"], 3), "setup_ms": round(s["setup_ms"], 3),
+                           "iters": s["iters"], "true_relres": s["true_relres"], "converged": s["converged"],
+                           "blocks_per_fmt": s["blocks_per_fmt"]}
+
+    # per-kernel device times of one iteration (eager launches, CUDA events on the stream)
+    h = B.bjac_setup(dA, pr.block_ptr, **head)
+    x.zero_()
+    prof = h.profile(b, x, tol=TOL, maxit=MAXIT)
+    h.close()
+    fb = {0: 8, 1: 4, 2: 2, 3: 2}[FMT[args.fmt]]
+    alg = algorithmic_bytes(n, nnz, nb, args.bs, fb)
+    shares = {k: prof[k] for k in ("spmv", "apply", "update_xp")}
+    dom = max(shares, key=shares.get)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = alg[dom] / (prof[dom] * 1e-3) / 1e9
+    wl_key = f"m{args.m}_bs{args.bs}_{args.fmt}"
+    kernel_name = {"spmv": "k_spmv", "apply": "k_apply_tma", "update_xp": "k_update_xp"}[dom]
+    roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": committed_traffic(kernel_name, wl_key), "algorithmic_bytes": alg[dom],
+                "launch_ms": round(prof[dom], 5),
+                "per_kernel_ms": {k: round(v, 5) for k, v in shares.items()},
+                "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares}}
+
+    # end to end through the public API with host buffers: upload A and b from pinned host
+    # memory, set up, solve, read x back
+    hA = [torch.as_tensor(np.asarray(a)).pin_memory() for a in (A.rowptr, A.colidx, A.val)]
+    hb = b.cpu().pin_memory()
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        t = [a.to("cuda", non_blocking=True) for a in hA]
+        d = B.DeviceCSR.__new__(B.DeviceCSR)
+        d.n, d.rowptr, d.colidx, d.val, d.nnz = n, t[0], t[1], t[2], nnz
+        d.c = B.bjac_csr(n, nnz, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr())
+        bd = hb.to("cuda", non_blocking=True)
+        xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        h = B.bjac_setup(d, pr.block_ptr, **head)
+        h.solve(bd, xd, tol=TOL, maxit=MAXIT)
+        h.close()
+        hx.copy_(xd, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / args.steps
+    h2d = sum(a.numel() * a.element_size() for a in hA) + n * 8
+    d2h = n * 8
+
+    setup_kernels = 2 + (0 if head["select"] in (B.SELECT_FIXED, B.SELECT_UNIFORM) else 1)
+    per_step = [setup_kernels + 3 + 3 * s["iters"] + 1 for s in st_mixed]
+    out = {
+        "metric": METRIC, "value": round(ms_mixed, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_mixed, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (block apply), bf16/fp16/fp32 storage",
+        "data": "synthetic (seeded generator, b = A x*)",
+        "config": workload_config(args),
+        "iters": sm["iters"], "true_relres": sm["true_relres"], "x_rel_err": err_x,
+        "setup_ms": round(sm["setup_ms"], 3), "solve_ms": round(sm["solve_ms"], 3),
+        "fp64_uniform": {"ms": round(ms_fp64, 4), "iters": s64["iters"], "true_relres": s64["true_relres"],
+                         "setup_ms": round(s64["setup_ms"], 3), "solve_ms": round(s64["solve_ms"], 3)},
+        "speedup_vs_fp64": round(ms_fp64 / ms_mixed, 3),
+        "modes": modes,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(sum(per_step)),
+        "clocks": clocks,
+    }
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+def oracle_sample(args, gpu_iters=None):
+    """The CPU oracle, unchanged, on a bounded sample of the same workload: the full setup
+    (block LU inverses + rounding) and args.cpu_iters PCG iterations, scaled to a whole
+    solve of `gpu_iters` (or the oracle's own count at the reduced sample) iterations."""
+    import oracle as O
+    from paper_2407_15973_gb300 import problems as PB
+    pr = PB.make_problem("subcube3d", seed=0, m=args.m, bs=args.bs)
+    b = O.spmv(pr.A, pr.x_star)
+    t0 = time.perf_counter()
+    P = O.Preconditioner(pr.A, pr.block_ptr, fmt=FMT[args.fmt])
+    t_setup = time.perf_counter() - t0
+    k = args.cpu_iters
+    t0 = time.perf_counter()
+    O.pcg(pr.A, P, b, tol=TOL, maxit=k, policy=O.POLICY_FMP, mode=1)
+    t_iter = (time.perf_counter() - t0) / k
+    iters = gpu_iters if gpu_iters else 150
+    ms = (t_setup + t_iter * iters) * 1e3
+    return {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"full setup ({t_setup:.1f} s) + {k} PCG iterations ({t_iter*1e3:.0f} ms each) of the same "
+                      f"{args.m}^3 system, scaled to {iters} iterations"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = oracle_sample(args)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"], "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle; f32 emulated block apply)",
+                "data": "synthetic", "config": workload_config(args), "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    out = run_ours(args, rank, world, dist)
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = oracle_sample(args, out["iters"])
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * mpbjac -- mixed-precision block-Jacobi preconditioned conjugate gradient on one GB300.
+ *
+ * C ABI. Every pointer is plain memory; which side (host or device) is stated per
+ * argument. No function throws; each returns an int status (0 = success, < 0 = error,
+ * > 0 = finished without meeting the tolerance) and leaves a thread-local message for
+ * bjac_last_error(). Work is enqueued on the CUDA stream given in the policy or the call
+ * (NULL = the legacy default stream); functions that return host data synchronise that
+ * stream first, and say so.
+ *
+ * Method: arXiv 2407.15973, "Mixed Precision Block-Jacobi Preconditioner".
+ *   BJAC            Eq. 3-1 with k = 1 and exact diagonal-block inverses (the special case
+ *                   stated after Eq. 3-3): M^-1 = D_b^-1, D_b = diag{A_ii}.
+ *   fMP-BJAC        Algorithm 3.1: r-hat = ConvertPrecision(r, p_l); z-hat = M^-1(p_l) r-hat;
+ *                   z = ConvertPrecision(z-hat, p_w). Working precision p_w = binary64.
+ *   aMP-BJAC(hl)    Algorithm 3.2: binary64 M^-1 while relres >= adp_tol, else fMP.
+ *   aMP-BJAC(lh)    Algorithm 3.3: fMP while relres >= adp_tol, else binary64 M^-1.
+ *   PCG             Section 3.2 (Hestenes-Stiefel CG), stopping rule of Section 4.2:
+ *                   ||r_k||_2 / ||b||_2 <= tol with the recurrence residual, followed by a
+ *                   true-residual check b - A x (Section 4.5.1).
+ * Beyond the paper (its exact blocks are the special case it names): per-block storage
+ * formats FP32, BF16 and power-of-two-scaled FP16, chosen per block by a condition-number
+ * rule or a learned selector.
+ */
+#ifndef MPBJAC_H
+#define MPBJAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define MPBJAC_OK 0
+#define MPBJAC_NOT_CONVERGED 1        /* maxit reached; x holds the last iterate        */
+#define MPBJAC_ERR_INVALID_ARG (-1)   /* bad sizes / pointers / non-monotone offsets    */
+#define MPBJAC_ERR_NOT_SPD (-2)       /* a diagonal block has a non-positive pivot      */
+#define MPBJAC_ERR_CUDA (-3)          /* a CUDA runtime call failed                     */
+#define MPBJAC_ERR_BREAKDOWN (-4)     /* PCG breakdown: p.Ap <= 0, r.z <= 0 or non-finite */
+#define MPBJAC_ERR_TIMEOUT (-5)       /* a bounded device wait expired                  */
+#define MPBJAC_ERR_NO_MEMORY (-6)     /* device allocation failed                       */
+#define MPBJAC_ERR_UNSUPPORTED (-7)   /* option not available for these inputs          */
+
+/* ---- storage formats of the block inverses ----------------------------------------- */
+#define BJAC_FP64 0    /* binary64 (8 B per entry)                                          */
+#define BJAC_FP32 1    /* binary32 (4 B)                                                    */
+#define BJAC_BF16 2    /* bfloat16 (2 B) of G / s_b, s_b a per-block power of two          */
+#define BJAC_FP16S 3   /* binary16 (2 B) of G / s_b, s_b = 2^(floor(log2 max|G_b|) - 14)     */
+
+/* ---- how each block's format is chosen --------------------------------------------- */
+#define BJAC_SELECT_UNIFORM 0   /* every block binary64 (the paper's uniform BJAC)          */
+#define BJAC_SELECT_FIXED 1     /* every block policy.fixed_fmt (fMP-BJAC, Algorithm 3.1)   */
+#define BJAC_SELECT_RULE 2      /* cheapest f with kappa_1(B_b) u_f <= theta                 */
+#define BJAC_SELECT_MLP 3       /* learned 12-64-64-3 selector, then promoted until          */
+                                /* kappa_1 u_f <= safety_theta                               */
+
+/* ---- residual-driven switching (the paper's aMP-BJAC) ------------------------------- */
+#define BJAC_TEMPORAL_NONE 0
+#define BJAC_TEMPORAL_HL 1      /* Algorithm 3.2 */
+#define BJAC_TEMPORAL_LH 2      /* Algorithm 3.3 */
+
+/* Sparse matrix in CSR form. All three arrays are DEVICE pointers owned by the caller and
+ * borrowed by every call (and by a handle for its whole life). rowptr has n+1 entries,
+ * rowptr[0] = 0, rowptr[n] = nnz, non-decreasing; colidx[k] in [0, n). The matrix must
+ * be symmetric positive definite for PCG (not checked beyond the block pivots). */
+typedef struct bjac_csr {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const double *val;
+} bjac_csr;
+
+/* Preconditioner options. */
+typedef struct bjac_policy {
+    int32_t select;         /* BJAC_SELECT_*                                               */
+    int32_t fixed_fmt;      /* BJAC_* format for BJAC_SELECT_FIXED                         */
+    int32_t temporal;       /* BJAC_TEMPORAL_*; HL / LH keep the binary64 set as well      */
+    int32_t fp64_fallback;  /* 1: if a mixed solve fails, re-solve with binary64 blocks    */
+    double adp_tol;         /* aMP threshold on relres (paper defaults: 10 for hl, 1e-5 lh)*/
+    double theta;           /* rule threshold on kappa_1 * u_f (0.1 if <= 0)               */
+    double safety_theta;    /* MLP promotion threshold on kappa_1 * u_f (0.5 if <= 0)      */
+    const float *mlp_params;/* HOST pointer, bjac_mlp_param_count() floats, for SELECT_MLP */
+    int32_t apply_variant;  /* 0 automatic, 1 generic warp-per-block, 2 TMA-staged uniform  */
+    int32_t reserved;
+    void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
+} bjac_policy;
+
+/* Per-solve report (host struct, filled by pcg_solve, which synchronises the stream). */
+typedef struct pcg_stats {
+    int32_t iters;          /* SpMVs performed in the PCG loop                            */
+    int32_t converged;      /* 1 if both the recurrence and the true residual meet tol    */
+    int32_t status;         /* same value pcg_solve returns                               */
+    int32_t restarts;       /* restarts from the true residual                            */
+    int32_t fallback_used;  /* 1 if the binary64 fallback re-solve ran                    */
+    int32_t low_applies;    /* preconditioner applications with the low-precision set     */
+    int32_t high_applies;   /* ... with the binary64 set                                  */
+    int32_t graph_launches; /* CUDA graph launches (one per restart)                       */
+    double relres;          /* final recurrence ||r||/||b||                               */
+    double true_relres;     /* final ||b - A x|| / ||b||                                  */
+    int32_t blocks_per_fmt[4];
+    float setup_ms;         /* time of bjac_setup (copied from the handle)                */
+    float solve_ms;         /* device time of this solve (CUDA events on the stream)      */
+} pcg_stats;
+
+typedef struct bjac_handle bjac_handle;
+
+/* Build the preconditioner of A for the contiguous row blocks
+ *   block b = rows [block_ptr[b], block_ptr[b+1]),  b = 0 .. nb-1,
+ * block_ptr is a HOST array of nb+1 int32 (block_ptr[0] = 0, block_ptr[nb] = n, every
+ * block 1 .. 128 rows). Each block B_b = A[rows_b, rows_b] is inverted in binary64 on the
+ * GPU (symmetric Gauss-Jordan sweep, SPD pivots checked), then rounded to its format.
+ * *out receives a handle that owns all device memory it allocated; A stays borrowed.
+ * Errors: INVALID_ARG, NOT_SPD (the handle is not created), CUDA, NO_MEMORY. */
+int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bjac_policy *policy,
+               bjac_handle **out);
+
+/* Solve A x = b by PCG. b, x: DEVICE arrays of n doubles; x holds x0 on entry and the
+ * solution on exit. tol: relative residual target; maxit: iteration cap (>= 0).
+ * stats (HOST, nullable) is filled after a stream synchronisation. relres_hist (DEVICE,
+ * nullable, maxit+1 doubles) receives relres after each iteration (index 0 = initial).
+ * Returns OK, NOT_CONVERGED, BREAKDOWN, or an error code. */
+int pcg_solve(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit,
+              pcg_stats *stats, double *relres_hist);
+
+/* Release everything the handle owns (synchronises its stream first). NULL is ignored. */
+void bjac_destroy(bjac_handle *h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *bjac_last_error(void);
+
+/* ---- the steps of one PCG iteration, callable alone ---------------------------------- */
+
+/* y = A x (DEVICE x, y; n doubles). If xy (DEVICE, nullable) is given, *xy = x . y is
+ * written as well (deterministic two-stage reduction). */
+int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *stream);
+
+/* r = b - A x and, if rr (DEVICE, nullable) is given, *rr = r . r. */
+int bjac_residual(const bjac_csr *A, const double *b, const double *x, double *r, double *rr,
+                  void *stream);
+
+/* z = M^-1 r with the handle's binary64 set (set = 0) or low-precision set (set = 1),
+ * Algorithm 3.1 for the latter. r, z: DEVICE, n doubles. rz (DEVICE, nullable): r . z.
+ * Uses the handle's stream. Error UNSUPPORTED if the requested set was not kept. */
+int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *z, double *rz);
+
+/* Same iterations as pcg_solve (no restart, no fallback), launched kernel by kernel
+ * without the graph and with CUDA events around each kernel of the loop body, to time
+ * them. ms (HOST, 4 floats) receives the mean device milliseconds per iteration of:
+ * [0] q = A p with p.q, [1] r -= alpha q with ||r|| (aMP only, else 0),
+ * [2] z = M^-1 r with r.z (fused with the r update outside aMP), [3] x += alpha p, p = z + beta p.
+ * iters (HOST, nullable) receives the iterations run. x: DEVICE x0 in / iterate out.
+ * Synchronises the stream once per iteration. */
+int pcg_profile(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, float *ms,
+                int32_t *iters);
+
+/* ---- inspection (tests, tools) ------------------------------------------------------- */
+
+/* Sizes: nb, bytes of the low-precision pool, entries of the binary64 pool (0 if not kept). */
+int bjac_info(const bjac_handle *h, int32_t *nb, int64_t *pool_bytes, int64_t *g_entries);
+
+/* Copy device state to HOST arrays (each nullable; synchronises the stream):
+ * fmt[nb] (uint8), scale[nb] (float), qoff[nb+1] (int64 byte offsets of each block in the
+ * pool), pool[pool_bytes], G[g_entries] (binary64 blocks, row-major, consecutive),
+ * feat[nb*12] (double, computed on first request). */
+int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *qoff, uint8_t *pool,
+                double *G, double *feat);
+
+/* Replace the binary64 inverses by G (HOST, g_entries doubles, same layout as bjac_export)
+ * and re-round every block to its current format. Lets a test feed identical inputs to
+ * the GPU rounding and to an independent implementation. */
+int bjac_import_inverse(bjac_handle *h, const double *G);
+
+/* Number of floats of the selector's parameter vector:
+ * W1[64][12] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[12] sd[12]. */
+int32_t bjac_mlp_param_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPBJAC_H */

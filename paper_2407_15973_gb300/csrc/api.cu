@@ -1,0 +1,768 @@
+// C ABI of mpbjac: handle lifecycle, setup orchestration, the PCG driver (one CUDA graph
+// with a device-side while loop per solve), and the single-step entry points.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "apply.cuh"
+#include "common.cuh"
+#include "mlp.cuh"
+#include "setup.cuh"
+
+namespace mpbjac {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? MPBJAC_ERR_NO_MEMORY : MPBJAC_ERR_CUDA;
+}
+
+int sm_count() {
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    }
+    return v;
+}
+
+static int fmt_bytes(int f) { return f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2; }
+
+// ----------------------------------------------------------------------------------------
+// vector kernels of the PCG loop
+// ----------------------------------------------------------------------------------------
+static int vec_grid(int n) {
+    int g = sm_count() * 4;
+    const int need = (n + kNT - 1) / kNT;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return g < 1 ? 1 : g;
+}
+
+// aMP loop: r -= alpha q, relres = ||r|| / ||b||, convergence test, precision for the next
+// preconditioner application (Algorithms 3.2 / 3.3 read this relres).
+__global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
+                                                  double *part, SolverState *S) {
+    __shared__ double red[kWarps];
+    if (S->state != kRunning) return;
+    const double alpha = S->alpha;
+    double rr = 0.0;
+    for (int i = blockIdx.x * kNT + threadIdx.x; i < n; i += gridDim.x * kNT) {
+        const double v = fma(-alpha, q[i], r[i]);
+        r[i] = v;
+        rr = fma(v, v, rr);
+    }
+    const double bsum = block_sum<kNT>(rr, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+    if (!last_cta(&S->tickets[kTicketUpdR])) return;
+    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
+    if (threadIdx.x != 0) return;
+    S->iter += 1;
+    S->x_pending = 1;
+    S->rr = t;
+    const double rel = sqrt(t) / S->bnorm;
+    S->relres = rel;
+    if (S->hist) S->hist[S->iter] = rel;
+    if (!(rel < 1.0e308)) S->state = kBreakdown;
+    else if (rel <= S->tol) S->state = kConverged;
+    else if (S->iter >= S->maxit) S->state = kMaxit;
+    S->use_low = choose_low(S, rel);
+}
+
+// x += alpha p (the update deferred from this iteration); p = z + beta p while running.
+// The last CTA closes the iteration and sets the graph's while-condition.
+__global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
+                                                   SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
+    const int xp = S->x_pending;
+    const int run = S->state == kRunning;
+    double *__restrict__ x = S->x;
+    const double alpha = S->alpha, beta = S->beta;
+    if (xp | run) {
+        for (int i = blockIdx.x * kNT + threadIdx.x; i < n; i += gridDim.x * kNT) {
+            const double pi = p[i];
+            if (xp) x[i] = fma(alpha, pi, x[i]);
+            if (run) p[i] = fma(beta, pi, z[i]);
+        }
+    }
+    if (!last_cta(&S->tickets[kTicketUpdXP])) return;
+    if (threadIdx.x == 0) {
+        S->x_pending = 0;
+        if (use_cond) cudaGraphSetConditional(cond, run ? 1u : 0u);
+    }
+}
+
+__global__ void k_zero_if_zero_rhs(int n, SolverState *S) {
+    if (S->bnorm != 0.0) return;
+    double *x = S->x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
+}
+
+__global__ void k_validate_csr(int n, int nnz, const int32_t *rowptr, const int32_t *colidx, int *status) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    if (tid == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) atomicCAS(status, 0, MPBJAC_ERR_INVALID_ARG);
+    for (int i = tid; i < n; i += stride)
+        if (rowptr[i + 1] < rowptr[i]) atomicCAS(status, 0, MPBJAC_ERR_INVALID_ARG);
+    for (int k = tid; k < nnz; k += stride) {
+        const int c = colidx[k];
+        if (c < 0 || c >= n) atomicCAS(status, 0, MPBJAC_ERR_INVALID_ARG);
+    }
+}
+
+}  // namespace mpbjac
+
+using namespace mpbjac;
+
+// ------------------------------------------------------------------------------------------
+// handle
+// ------------------------------------------------------------------------------------------
+struct bjac_handle {
+    bjac_csr A{};
+    bjac_policy pol{};
+    cudaStream_t stream = nullptr;
+    int n = 0, nb = 0, bs_max = 0, ubs = 0;
+    std::vector<int32_t> h_block_ptr;
+    std::vector<int64_t> h_goff, h_qoff;
+    int32_t *d_block_ptr = nullptr;
+    int64_t *d_goff = nullptr;
+    double *d_G = nullptr;
+    uint8_t *d_fmt_hi = nullptr;
+    float *d_scale_hi = nullptr;
+    int64_t *d_qoff_hi = nullptr;
+    uint8_t *d_fmt = nullptr;
+    float *d_scale = nullptr;
+    int64_t *d_qoff = nullptr;
+    uint8_t *d_pool = nullptr;
+    int64_t pool_bytes = 0;
+    double *d_feat = nullptr;
+    double *d_kap = nullptr;
+    int *d_status = nullptr;
+    bool have_lo = false, have_hi = false;
+    PSet lo{}, hi{};
+    // solve workspace
+    double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_x0 = nullptr;
+    double *d_part = nullptr;
+    SolverState *d_S = nullptr;
+    SolverState *h_S = nullptr;   // pinned mirror
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float setup_ms = 0.0f;
+    int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
+};
+
+static void free_handle(bjac_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
+        if (h->graph[i]) cudaGraphDestroy(h->graph[i]);
+    }
+    void *ptrs[] = {h->d_block_ptr, h->d_goff, h->d_G, h->d_fmt_hi, h->d_scale_hi, h->d_qoff_hi, h->d_fmt,
+                    h->d_scale, h->d_qoff, h->d_pool, h->d_feat, h->d_kap, h->d_status, h->d_r, h->d_z,
+                    h->d_p, h->d_q, h->d_x0, h->d_part, h->d_S};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_S) cudaFreeHost(h->h_S);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+template <typename T>
+static int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    MPB_CUDA(cudaMalloc((void **)p, count * sizeof(T)));
+    return MPBJAC_OK;
+}
+
+#define MPB_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != MPBJAC_OK) {       \
+            free_handle(h);           \
+            return rc_;               \
+        }                             \
+    } while (0)
+
+static int check_csr_host(const bjac_csr *A) {
+    if (!A) return fail(MPBJAC_ERR_INVALID_ARG, "A is NULL");
+    if (A->n <= 0) return fail(MPBJAC_ERR_INVALID_ARG, "n must be positive");
+    if (A->nnz < 0) return fail(MPBJAC_ERR_INVALID_ARG, "nnz must be non-negative");
+    if (!A->rowptr || (A->nnz > 0 && (!A->colidx || !A->val)))
+        return fail(MPBJAC_ERR_INVALID_ARG, "CSR pointers must be non-NULL");
+    return MPBJAC_OK;
+}
+
+static PSet make_pset(const bjac_handle *h, const uint8_t *fmt, const float *scale, const int64_t *qoff,
+                      const uint8_t *pool, int ufmt) {
+    PSet P;
+    P.block_ptr = h->d_block_ptr;
+    P.fmt = fmt;
+    P.scale = scale;
+    P.qoff = qoff;
+    P.pool = pool;
+    P.nb = h->nb;
+    P.ubs = h->ubs;
+    P.ufmt = ufmt;
+    P.pad = 0;
+    return P;
+}
+
+extern "C" {
+
+const char *bjac_last_error(void) { return g_err.c_str(); }
+
+int32_t bjac_mlp_param_count(void) { return kMlpParams; }
+
+int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bjac_policy *policy,
+               bjac_handle **out) {
+    if (!out) return fail(MPBJAC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_csr_host(A);
+    if (rc) return rc;
+    if (!policy) return fail(MPBJAC_ERR_INVALID_ARG, "policy is NULL");
+    if (!block_ptr || nb < 1) return fail(MPBJAC_ERR_INVALID_ARG, "need nb >= 1 blocks");
+    if (block_ptr[0] != 0 || block_ptr[nb] != A->n)
+        return fail(MPBJAC_ERR_INVALID_ARG, "block_ptr must start at 0 and end at n");
+    int bs_max = 0, ubs = block_ptr[1] - block_ptr[0];
+    for (int b = 0; b < nb; ++b) {
+        const int bs = block_ptr[b + 1] - block_ptr[b];
+        if (bs < 1 || bs > 128) return fail(MPBJAC_ERR_INVALID_ARG, "every block needs 1..128 rows");
+        bs_max = std::max(bs_max, bs);
+        if (bs != ubs) ubs = 0;
+    }
+    const bjac_policy &P = *policy;
+    if (P.select < BJAC_SELECT_UNIFORM || P.select > BJAC_SELECT_MLP)
+        return fail(MPBJAC_ERR_INVALID_ARG, "unknown select");
+    if (P.select == BJAC_SELECT_FIXED && (P.fixed_fmt < BJAC_FP64 || P.fixed_fmt > BJAC_FP16S))
+        return fail(MPBJAC_ERR_INVALID_ARG, "unknown fixed_fmt");
+    if (P.temporal < BJAC_TEMPORAL_NONE || P.temporal > BJAC_TEMPORAL_LH)
+        return fail(MPBJAC_ERR_INVALID_ARG, "unknown temporal policy");
+    if (P.select == BJAC_SELECT_MLP && !P.mlp_params)
+        return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_MLP needs mlp_params");
+    if (P.temporal != BJAC_TEMPORAL_NONE && P.select == BJAC_SELECT_UNIFORM)
+        return fail(MPBJAC_ERR_INVALID_ARG, "aMP switching needs a low-precision set");
+
+    bjac_handle *h = new bjac_handle();
+    h->A = *A;
+    h->pol = P;
+    if (h->pol.theta <= 0.0) h->pol.theta = 0.1;
+    if (h->pol.safety_theta <= 0.0) h->pol.safety_theta = 0.5;
+    h->pol.mlp_params = nullptr;   // not retained
+    h->stream = (cudaStream_t)P.stream;
+    h->n = A->n;
+    h->nb = nb;
+    h->bs_max = bs_max;
+    h->ubs = ubs;
+    h->h_block_ptr.assign(block_ptr, block_ptr + nb + 1);
+    cudaStream_t st = h->stream;
+    MPB_TRY(cudaEventCreate(&h->ev0) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    MPB_TRY(cudaEventCreate(&h->ev1) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    if (cudaEventRecord(h->ev0, st) != cudaSuccess) { free_handle(h); return cuda_fail(cudaGetLastError(), "event"); }
+
+    // geometry
+    h->h_goff.resize(nb + 1);
+    h->h_goff[0] = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t bs = block_ptr[b + 1] - block_ptr[b];
+        h->h_goff[b + 1] = h->h_goff[b] + bs * bs;
+    }
+    const bool fixed_now = P.select == BJAC_SELECT_FIXED || P.select == BJAC_SELECT_UNIFORM;
+    h->have_hi = P.select == BJAC_SELECT_UNIFORM || P.temporal != BJAC_TEMPORAL_NONE || P.fp64_fallback ||
+                 !fixed_now;
+    h->have_lo = P.select != BJAC_SELECT_UNIFORM;
+
+    MPB_TRY(dalloc(&h->d_block_ptr, nb + 1));
+    MPB_TRY(dalloc(&h->d_goff, nb + 1));
+    MPB_TRY(dalloc(&h->d_status, 2));
+    MPB_TRY(dalloc(&h->d_fmt, nb));
+    MPB_TRY(dalloc(&h->d_scale, nb));
+    MPB_TRY(dalloc(&h->d_qoff, nb + 1));
+    MPB_TRY(dalloc(&h->d_kap, 2 * (size_t)nb));
+    MPB_TRY(dalloc(&h->d_feat, 12 * (size_t)nb));
+    if (h->have_hi) MPB_TRY(dalloc(&h->d_G, (size_t)h->h_goff[nb]));
+    MPB_TRY(cudaMemcpyAsync(h->d_block_ptr, block_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                    cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy block_ptr"));
+    MPB_TRY(cudaMemcpyAsync(h->d_goff, h->h_goff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                    cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy goff"));
+    MPB_TRY(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) == cudaSuccess ? 0
+                                                                                : cuda_fail(cudaGetLastError(), "memset"));
+    k_validate_csr<<<std::max(1, std::min(sm_count() * 4, (A->nnz + 255) / 256)), 256, 0, st>>>(
+        A->n, A->nnz, A->rowptr, A->colidx, h->d_status);
+    int hstat[2] = {0, 0};
+    MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
+    MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "validate csr"));
+    if (hstat[0] != 0) {
+        free_handle(h);
+        return fail(MPBJAC_ERR_INVALID_ARG, "CSR arrays are inconsistent (rowptr not monotone / column out of range)");
+    }
+
+    // low-precision pool offsets known now for fixed formats
+    int fixed_fmt = P.select == BJAC_SELECT_UNIFORM ? BJAC_FP64 : P.fixed_fmt;
+    auto set_qoff = [&](const std::vector<uint8_t> &fmts) {
+        h->h_qoff.assign(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) {
+            const int64_t bs = block_ptr[b + 1] - block_ptr[b];
+            int64_t bytes = bs * bs * fmt_bytes(fmts.empty() ? fixed_fmt : fmts[b]);
+            bytes = (bytes + 15) & ~int64_t(15);
+            h->h_qoff[b + 1] = h->h_qoff[b] + bytes;
+        }
+        h->pool_bytes = h->h_qoff[nb];
+    };
+    SetupArgs a{};
+    a.n = A->n;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.val = A->val;
+    a.block_ptr = h->d_block_ptr;
+    a.nb = nb;
+    a.goff = h->d_goff;
+    a.G = h->d_G;
+    a.select = P.select;
+    a.fixed_fmt = fixed_fmt;
+    a.theta = h->pol.theta;
+    a.fmt = h->d_fmt;
+    a.scale = h->d_scale;
+    a.feat = h->d_feat;
+    a.kap = h->d_kap;
+    a.status = h->d_status;
+    if (h->have_lo && fixed_now) {
+        set_qoff({});
+        MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
+        MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                                st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
+        a.qoff = h->d_qoff;
+        a.pool = h->d_pool;
+    }
+    MPB_TRY(launch_setup_blocks(a, bs_max, st));
+    if (P.select == BJAC_SELECT_MLP) {
+        MPB_TRY(launch_mlp_select(P.mlp_params, nb, h->d_feat, h->d_kap, h->pol.safety_theta, h->d_fmt, st));
+    }
+    std::vector<uint8_t> hfmt(nb);
+    MPB_TRY(cudaMemcpyAsync(hfmt.data(), h->d_fmt, nb, cudaMemcpyDeviceToHost, st) == cudaSuccess
+                ? 0 : cuda_fail(cudaGetLastError(), "copy fmt"));
+    MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
+    MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "setup kernel"));
+    if (hstat[0] != 0) {
+        free_handle(h);
+        return fail(MPBJAC_ERR_NOT_SPD, "diagonal block " + std::to_string(hstat[1]) +
+                                            " has a non-positive pivot (not positive definite)");
+    }
+    if (h->have_lo && !fixed_now) {     // per-block formats: compact pool, second pass
+        set_qoff(hfmt);
+        MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
+        MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                                st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
+        MPB_TRY(launch_pack(nb, h->d_block_ptr, h->d_goff, h->d_G, h->d_fmt, h->d_qoff, h->d_pool, h->d_scale, st));
+    }
+    int ufmt = -1;
+    if (h->have_lo) {
+        ufmt = hfmt[0];
+        for (int b = 0; b < nb; ++b) {
+            h->blocks_per_fmt[hfmt[b] & 3] += 1;
+            if (hfmt[b] != ufmt) ufmt = -1;
+        }
+        h->lo = make_pset(h, h->d_fmt, h->d_scale, h->d_qoff, h->d_pool, ufmt);
+        if (tma_supported(h->lo, h->n)) MPB_TRY(prepare_apply_tma(h->lo));
+    } else {
+        h->blocks_per_fmt[BJAC_FP64] = nb;
+    }
+    if (h->have_hi) {
+        std::vector<int64_t> qhi(nb + 1);
+        for (int b = 0; b <= nb; ++b) qhi[b] = h->h_goff[b] * 8;
+        std::vector<float> ones(nb, 1.0f);
+        MPB_TRY(dalloc(&h->d_fmt_hi, nb));
+        MPB_TRY(dalloc(&h->d_scale_hi, nb));
+        MPB_TRY(dalloc(&h->d_qoff_hi, nb + 1));
+        MPB_TRY(cudaMemsetAsync(h->d_fmt_hi, 0, nb, st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "memset"));
+        MPB_TRY(cudaMemcpyAsync(h->d_scale_hi, ones.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, st) ==
+                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
+        MPB_TRY(cudaMemcpyAsync(h->d_qoff_hi, qhi.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
+        h->hi = make_pset(h, h->d_fmt_hi, h->d_scale_hi, h->d_qoff_hi, reinterpret_cast<uint8_t *>(h->d_G),
+                          BJAC_FP64);
+    }
+    // solve workspace
+    const size_t n = (size_t)A->n;
+    MPB_TRY(dalloc(&h->d_r, n));
+    MPB_TRY(dalloc(&h->d_z, n));
+    MPB_TRY(dalloc(&h->d_p, n));
+    MPB_TRY(dalloc(&h->d_q, n));
+    MPB_TRY(dalloc(&h->d_part, 2 * (size_t)kMaxGrid));
+    MPB_TRY(dalloc(&h->d_S, 1));
+    if (P.fp64_fallback) MPB_TRY(dalloc(&h->d_x0, n));
+    MPB_TRY(cudaMallocHost((void **)&h->h_S, sizeof(SolverState)) == cudaSuccess
+                ? 0 : cuda_fail(cudaGetLastError(), "cudaMallocHost"));
+    memset(h->h_S, 0, sizeof(SolverState));
+    MPB_TRY(cudaMemsetAsync(h->d_S, 0, sizeof(SolverState), st) == cudaSuccess
+                ? 0 : cuda_fail(cudaGetLastError(), "memset"));
+    MPB_TRY(cudaEventRecord(h->ev1, st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "event"));
+    MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "setup"));
+    cudaEventElapsedTime(&h->setup_ms, h->ev0, h->ev1);
+    *out = h;
+    return MPBJAC_OK;
+}
+
+void bjac_destroy(bjac_handle *h) { free_handle(h); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// PCG driver
+// ------------------------------------------------------------------------------------------
+static ApplyIO base_io(bjac_handle *h) {
+    ApplyIO io{};
+    io.r = h->d_r;
+    io.r_out = h->d_r;
+    io.q = h->d_q;
+    io.z = h->d_z;
+    io.p = h->d_p;
+    io.part = h->d_part;
+    io.ticket = &h->d_S->tickets[kTicketApply];
+    io.out = nullptr;
+    io.err = nullptr;
+    io.set = 1;
+    io.only_set = -1;
+    return io;
+}
+
+// Apply for the init / aMP modes: the set is read on the device (S->use_low). The
+// binary64 set always goes to the generic kernel; the low set to the TMA kernel when it
+// fits one, each launch returning at once when the other set is selected.
+static bool lo_uses_tma(const bjac_handle *h) {
+    return h->have_lo && h->pol.apply_variant != 1 && tma_supported(h->lo, h->n);
+}
+
+static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool low_only, bool high_only) {
+    ApplyIO io = base_io(h);
+    const bool lo_tma = lo_uses_tma(h);
+    PSet lo = h->have_lo ? h->lo : h->hi;
+    PSet hi = h->have_hi ? h->hi : h->lo;
+    if (lo_tma && !high_only) {
+        int rc = launch_apply_tma(mode, h->lo, io, h->d_S, h->n, st);
+        if (rc) return rc;
+        if (low_only) return MPBJAC_OK;
+        io.only_set = 0;
+        return launch_apply_generic(mode, lo, hi, io, h->d_S, st);
+    }
+    io.only_set = low_only ? 1 : (high_only ? 0 : -1);
+    return launch_apply_generic(mode, lo, hi, io, h->d_S, st);
+}
+
+// One PCG iteration: captured into the body of a device-side while loop, or launched
+// eagerly by the profiler with an event between kernels (ev != nullptr: ev[0..4]).
+static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphConditionalHandle cond,
+                        cudaEvent_t *ev = nullptr) {
+    const bool temporal = (which == 0) && h->pol.temporal != BJAC_TEMPORAL_NONE;
+    const bool use_low = (which == 0) && h->have_lo;
+    if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
+    int rc = launch_spmv(h->A, h->d_p, h->d_q, h->d_part, &h->d_S->tickets[kTicketSpmv], nullptr, h->d_S, 2, cs);
+    if (rc) return rc;
+    if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
+    if (temporal) {
+        k_update_r<<<vec_grid(h->n), kNT, 0, cs>>>(h->n, h->d_q, h->d_r, h->d_part, h->d_S);
+        MPB_CUDA(cudaGetLastError());
+        if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
+        rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
+        if (rc) return rc;
+    } else {
+        if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
+        ApplyIO io = base_io(h);
+        io.set = use_low ? 1 : 0;
+        if (use_low && lo_uses_tma(h)) rc = launch_apply_tma(kApplyFused, h->lo, io, h->d_S, h->n, cs);
+        else rc = launch_apply_generic(kApplyFused, use_low ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
+                                       h->d_S, cs);
+        if (rc) return rc;
+    }
+    if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));
+    k_update_xp<<<vec_grid(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, ev ? 0 : 1);
+    MPB_CUDA(cudaGetLastError());
+    if (ev) MPB_CUDA(cudaEventRecord(ev[4], cs));
+    return MPBJAC_OK;
+}
+
+static int build_graph(bjac_handle *h, int which) {
+    cudaGraph_t g = nullptr;
+    MPB_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphConditionalHandleCreate"); }
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphAddNode(while)"); }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaStreamCreate"); }
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); return cuda_fail(e, "BeginCaptureToGraph"); }
+    int rc = capture_body(h, which, cs, cond);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (rc || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return rc ? rc : cuda_fail(e, "EndCapture");
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphInstantiate"); }
+    h->graph[which] = g;
+    h->exec[which] = ex;
+    return MPBJAC_OK;
+}
+
+// One full solve with preconditioner selection `which` (0 = policy, 1 = binary64 fallback).
+static int run_solve(bjac_handle *h, int which, const double *b, double *x, double tol, int maxit, double *hist,
+                     int *graph_launches) {
+    cudaStream_t st = h->stream;
+    SolverState &hs = *h->h_S;
+    memset(&hs, 0, sizeof(SolverState));
+    hs.tol = tol;
+    hs.adp_tol = h->pol.adp_tol;
+    hs.x = x;
+    hs.hist = hist;
+    hs.maxit = maxit;
+    hs.temporal = which == 0 ? h->pol.temporal : BJAC_TEMPORAL_NONE;
+    hs.low_default = (which == 0 && h->have_lo) ? 1 : 0;
+    MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
+    int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
+    if (rc) return rc;
+    k_zero_if_zero_rhs<<<vec_grid(h->n), kNT, 0, st>>>(h->n, h->d_S);
+    if (!h->exec[which]) {
+        rc = build_graph(h, which);
+        if (rc) return rc;
+    }
+    for (int pass = 0; pass < 9; ++pass) {
+        const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
+        rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1,
+                                 !temporal && hs.low_default == 0);
+        if (rc) return rc;
+        MPB_CUDA(cudaGraphLaunch(h->exec[which], st));
+        *graph_launches += 1;
+        rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 2, st);
+        if (rc) return rc;
+        MPB_CUDA(cudaMemcpyAsync(&hs, h->d_S, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+        MPB_CUDA(cudaStreamSynchronize(st));
+        if (hs.state != kRunning) break;      // no restart requested
+    }
+    return MPBJAC_OK;
+}
+
+extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, pcg_stats *stats,
+                         double *relres_hist) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    if (!b || !x) return fail(MPBJAC_ERR_INVALID_ARG, "b and x must be device pointers");
+    if (maxit < 0 || !(tol >= 0.0)) return fail(MPBJAC_ERR_INVALID_ARG, "need maxit >= 0 and tol >= 0");
+    cudaStream_t st = h->stream;
+    MPB_CUDA(cudaEventRecord(h->ev0, st));
+    if (h->d_x0) MPB_CUDA(cudaMemcpyAsync(h->d_x0, x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    int launches = 0;
+    int rc = run_solve(h, 0, b, x, tol, maxit, relres_hist, &launches);
+    if (rc) return rc;
+    SolverState res = *h->h_S;
+    int fallback = 0;
+    auto status_of = [&](const SolverState &s) {
+        if (s.state == kBreakdown || s.state == kBreakdownSigma) return MPBJAC_ERR_BREAKDOWN;
+        if (s.state == kConverged && s.true_relres <= tol) return MPBJAC_OK;
+        return MPBJAC_NOT_CONVERGED;
+    };
+    int status = status_of(res);
+    if (status != MPBJAC_OK && h->pol.fp64_fallback && h->have_lo && h->have_hi) {
+        MPB_CUDA(cudaMemcpyAsync(x, h->d_x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+        rc = run_solve(h, 1, b, x, tol, maxit, relres_hist, &launches);
+        if (rc) return rc;
+        const int lo_ap = res.low_applies;
+        res = *h->h_S;
+        res.low_applies += lo_ap;
+        status = status_of(res);
+        fallback = 1;
+    }
+    MPB_CUDA(cudaEventRecord(h->ev1, st));
+    MPB_CUDA(cudaEventSynchronize(h->ev1));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iters = res.iter;
+        stats->converged = status == MPBJAC_OK;
+        stats->status = status;
+        stats->restarts = res.restarts;
+        stats->fallback_used = fallback;
+        stats->low_applies = res.low_applies;
+        stats->high_applies = res.high_applies;
+        stats->graph_launches = launches;
+        stats->relres = res.relres;
+        stats->true_relres = res.true_relres;
+        for (int i = 0; i < 4; ++i) stats->blocks_per_fmt[i] = h->blocks_per_fmt[i];
+        stats->setup_ms = h->setup_ms;
+        cudaEventElapsedTime(&stats->solve_ms, h->ev0, h->ev1);
+    }
+    if (status == MPBJAC_ERR_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0 or r.z <= 0 or non-finite)");
+    else if (status == MPBJAC_NOT_CONVERGED) set_error("maximum number of iterations reached");
+    return status;
+}
+
+// ------------------------------------------------------------------------------------------
+// single steps
+// ------------------------------------------------------------------------------------------
+extern "C" int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *stream) {
+    int rc = check_csr_host(A);
+    if (rc) return rc;
+    if (!x || !y) return fail(MPBJAC_ERR_INVALID_ARG, "x and y must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!xy) return launch_spmv(*A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st);
+    // scratch for the deterministic reduction: partial sums and a ticket counter
+    void *scratch = nullptr;
+    const size_t bytes = sizeof(double) * kMaxGrid + 256;
+    MPB_CUDA(cudaMallocAsync(&scratch, bytes, st));
+    double *part = static_cast<double *>(scratch);
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * kMaxGrid);
+    MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+    rc = launch_spmv(*A, x, y, part, ticket, xy, nullptr, 1, st);
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
+
+extern "C" int bjac_residual(const bjac_csr *A, const double *b, const double *x, double *r, double *rr,
+                             void *stream) {
+    int rc = check_csr_host(A);
+    if (rc) return rc;
+    if (!b || !x || !r) return fail(MPBJAC_ERR_INVALID_ARG, "b, x and r must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    const size_t bytes = sizeof(double) * 2 * kMaxGrid + 256;
+    MPB_CUDA(cudaMallocAsync(&scratch, bytes, st));
+    double *part = static_cast<double *>(scratch);
+    unsigned int *ticket =
+        reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * 2 * kMaxGrid);
+    double *dummy = reinterpret_cast<double *>(static_cast<char *>(scratch) + sizeof(double) * 2 * kMaxGrid + 64);
+    MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+    rc = launch_residual(*A, b, x, r, part, ticket, rr ? rr : dummy, nullptr, 0, st);
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
+
+extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *z, double *rz) {
+    if (!h || !r || !z) return fail(MPBJAC_ERR_INVALID_ARG, "handle, r and z must be non-NULL");
+    if (set != 0 && set != 1) return fail(MPBJAC_ERR_INVALID_ARG, "set must be 0 or 1");
+    if ((set == 1 && !h->have_lo) || (set == 0 && !h->have_hi))
+        return fail(MPBJAC_ERR_UNSUPPORTED, "requested preconditioner set was not kept");
+    ApplyIO io = base_io(h);
+    io.r = r;
+    io.r_out = nullptr;
+    io.q = nullptr;
+    io.z = z;
+    io.p = nullptr;
+    io.out = rz;
+    io.set = set;
+    // bulk copies need 16-byte aligned sources
+    const bool aligned = (reinterpret_cast<uintptr_t>(r) & 15) == 0;
+    const bool tma = set == 1 && aligned && tma_supported(h->lo, h->n) && h->pol.apply_variant != 1;
+    if (tma) return launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, h->stream);
+    return launch_apply_generic(kApplyStandalone, h->have_lo ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
+                                nullptr, h->stream);
+}
+
+extern "C" int bjac_info(const bjac_handle *h, int32_t *nb, int64_t *pool_bytes, int64_t *g_entries) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    if (nb) *nb = h->nb;
+    if (pool_bytes) *pool_bytes = h->have_lo ? h->pool_bytes : 0;
+    if (g_entries) *g_entries = h->have_hi ? h->h_goff[h->nb] : 0;
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *qoff, uint8_t *pool, double *G,
+                           double *feat) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t st = h->stream;
+    const int nb = h->nb;
+    if (fmt) MPB_CUDA(cudaMemcpyAsync(fmt, h->have_lo ? h->d_fmt : h->d_fmt_hi, nb, cudaMemcpyDeviceToHost, st));
+    if (scale)
+        MPB_CUDA(cudaMemcpyAsync(scale, h->have_lo ? h->d_scale : h->d_scale_hi, sizeof(float) * nb,
+                                 cudaMemcpyDeviceToHost, st));
+    if (qoff && h->have_lo) memcpy(qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1));
+    if (pool && h->have_lo)
+        MPB_CUDA(cudaMemcpyAsync(pool, h->d_pool, (size_t)h->pool_bytes, cudaMemcpyDeviceToHost, st));
+    if (G && h->have_hi)
+        MPB_CUDA(cudaMemcpyAsync(G, h->d_G, sizeof(double) * (size_t)h->h_goff[nb], cudaMemcpyDeviceToHost, st));
+    if (feat) MPB_CUDA(cudaMemcpyAsync(feat, h->d_feat, sizeof(double) * 12 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+    MPB_CUDA(cudaStreamSynchronize(st));
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_import_inverse(bjac_handle *h, const double *G) {
+    if (!h || !G) return fail(MPBJAC_ERR_INVALID_ARG, "handle and G must be non-NULL");
+    if (!h->have_hi) return fail(MPBJAC_ERR_UNSUPPORTED, "this handle keeps no binary64 set");
+    cudaStream_t st = h->stream;
+    MPB_CUDA(cudaMemcpyAsync(h->d_G, G, sizeof(double) * (size_t)h->h_goff[h->nb], cudaMemcpyHostToDevice, st));
+    if (h->have_lo) {
+        int rc = launch_pack(h->nb, h->d_block_ptr, h->d_goff, h->d_G, h->d_fmt, h->d_qoff, h->d_pool, h->d_scale, st);
+        if (rc) return rc;
+    }
+    MPB_CUDA(cudaStreamSynchronize(st));
+    return MPBJAC_OK;
+}
+
+// Eager (graph-free) run of the same PCG iterations with CUDA events around every kernel
+// of the loop body; ms[0..3] receive the mean device time per iteration of: the SpMV step,
+// the residual-update step (aMP only; 0 otherwise), the preconditioner apply step, and the
+// x/p update step. iters receives the iterations run. x holds x0 on entry.
+extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, float *ms,
+                           int32_t *iters) {
+    if (!h || !b || !x || !ms) return fail(MPBJAC_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = h->stream;
+    SolverState &hs = *h->h_S;
+    memset(&hs, 0, sizeof(SolverState));
+    hs.tol = tol;
+    hs.adp_tol = h->pol.adp_tol;
+    hs.x = x;
+    hs.maxit = maxit;
+    hs.temporal = h->pol.temporal;
+    hs.low_default = h->have_lo ? 1 : 0;
+    MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
+    int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
+    if (rc) return rc;
+    const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
+    rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1, !temporal && hs.low_default == 0);
+    if (rc) return rc;
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) MPB_CUDA(cudaEventCreate(&ev[i]));
+    double acc[4] = {0, 0, 0, 0};
+    int k = 0;
+    int32_t state = kRunning;
+    while (k < maxit) {
+        rc = capture_body(h, 0, st, cudaGraphConditionalHandle{}, ev);
+        if (rc) break;
+        MPB_CUDA(cudaMemcpyAsync(&state, &h->d_S->state, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MPB_CUDA(cudaStreamSynchronize(st));
+        float t[4];
+        for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+        for (int i = 0; i < 4; ++i) acc[i] += t[i];
+        ++k;
+        if (state != kRunning) break;
+    }
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    if (rc) return rc;
+    for (int i = 0; i < 4; ++i) ms[i] = k ? (float)(acc[i] / k) : 0.0f;
+    if (iters) *iters = k;
+    return MPBJAC_OK;
+}

@@ -1,0 +1,39 @@
+// Declarations shared by the apply kernels and their callers.
+#pragma once
+#include "common.cuh"
+
+namespace mpbjac {
+
+enum ApplyMode {
+    kApplyStandalone = 0,  // z = M^-1 r (set = io.set); optional r.z to io.out
+    kApplyInit = 1,        // PCG start: z = M^-1 r, p = z, rho = r.z (set from S->use_low)
+    kApplyTemporal = 2,    // PCG loop, aMP: set from S->use_low; beta = rho_new / rho
+    kApplyFused = 3,       // PCG loop: r -= alpha q; z = M^-1 r; r.r, r.z; convergence; beta
+};
+
+struct ApplyIO {
+    const double *r;       // residual in
+    double *r_out;         // residual out (fused mode; may alias r)
+    const double *q;       // A p (fused mode)
+    double *z;
+    double *p;             // init mode: p = z
+    double *part;          // >= 2 * grid partial sums
+    unsigned int *ticket;
+    double *out;           // standalone: r.z (nullable)
+    int *err;              // device error word (nullable)
+    int set;               // 1 low-precision set, 0 binary64 set (standalone / fused)
+    int only_set;          // -1: this launch serves both sets; else it serves only that set
+};
+
+bool tma_supported(const PSet &P, int n);
+int prepare_apply_tma(const PSet &P);   // set kernel attributes (call before any capture)
+int launch_apply_tma(int mode, const PSet &P, const ApplyIO &io, SolverState *S, int n, cudaStream_t st);
+int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S,
+                         cudaStream_t st);
+
+int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
+                double *dot_out, SolverState *S, int mode, cudaStream_t st);
+int launch_residual(const bjac_csr &A, const double *b, const double *x, double *r, double *part,
+                    unsigned int *ticket, double *rr_out, SolverState *S, int mode, cudaStream_t st);
+
+}  // namespace mpbjac

@@ -1,0 +1,140 @@
+// Shared device helpers and host-side declarations of the mpbjac library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mpbjac.h"
+
+namespace mpbjac {
+
+// ----------------------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MPB_CUDA(call)                                                    \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::mpbjac::cuda_fail(e_, #call);     \
+    } while (0)
+
+// ----------------------------------------------------------------------------------------
+// launch geometry
+// ----------------------------------------------------------------------------------------
+constexpr int kNT = 256;                 // threads per CTA of the streaming kernels
+constexpr int kWarps = kNT / 32;
+constexpr int kMaxGrid = 152 * 8;        // upper bound on CTAs of any reducing kernel
+int sm_count();
+
+// ----------------------------------------------------------------------------------------
+// solver state shared by the kernels of one PCG loop (device memory, one per handle)
+// ----------------------------------------------------------------------------------------
+enum SolverStateCode : int32_t {
+    kRunning = 0,
+    kConverged = 1,
+    kMaxit = 2,
+    kBreakdown = 3,        // r.z <= 0 or non-finite scalars after the x/r update
+    kBreakdownSigma = 4,   // p.Ap <= 0 before the x/r update of this iteration
+};
+
+struct SolverState {
+    // configuration, written by the host before each solve
+    double tol;
+    double adp_tol;
+    double *x;             // solution vector (device)
+    double *hist;          // relres history (device, nullable)
+    int32_t maxit;
+    int32_t temporal;      // BJAC_TEMPORAL_*
+    int32_t low_default;   // set used when temporal == NONE: 1 low, 0 binary64
+    int32_t pad0;
+    // dynamic state
+    double bnorm;
+    double rho, sigma, alpha, beta, rr, relres, true_relres;
+    int32_t iter, state, use_low, x_pending;
+    int32_t low_applies, high_applies, restarts, pad1;
+    unsigned int tickets[8];
+};
+
+enum Ticket { kTicketSpmv = 0, kTicketUpdR = 1, kTicketApply = 2, kTicketUpdXP = 3, kTicketRes = 4,
+              kTicketInit = 5 };
+
+__device__ __forceinline__ int choose_low(const SolverState *S, double relres) {
+    if (S->temporal == BJAC_TEMPORAL_HL) return !(relres >= S->adp_tol);   // Algorithm 3.2
+    if (S->temporal == BJAC_TEMPORAL_LH) return relres >= S->adp_tol;      // Algorithm 3.3
+    return S->low_default;
+}
+
+// ----------------------------------------------------------------------------------------
+// a preconditioner set: nb blocks, each stored row-major in its own format in a byte pool
+// ----------------------------------------------------------------------------------------
+struct PSet {
+    const int32_t *block_ptr;  // [nb+1]
+    const uint8_t *fmt;        // [nb]
+    const float *scale;        // [nb]
+    const int64_t *qoff;       // [nb+1] byte offsets into pool
+    const uint8_t *pool;
+    int32_t nb;
+    int32_t ubs;               // common block size if every block has it (else 0)
+    int32_t ufmt;              // common format (else -1)
+    int32_t pad;
+};
+
+// ----------------------------------------------------------------------------------------
+// deterministic reductions
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA in a fixed order; result valid in every thread. sm: >= NT/32 doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += sm[i];
+    return t;
+}
+
+// Every CTA publishes its partials, then the last CTA to arrive (ticket) sees them all.
+// Returns true in every thread of that last CTA. The ticket counter is reset there.
+__device__ __forceinline__ bool last_cta(unsigned int *ticket) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+    return s_last != 0;
+}
+
+// Sum of part[0..count) (written by other CTAs) in fixed order, by a whole CTA.
+template <int NT>
+__device__ __forceinline__ double reduce_partials(const double *part, int count, int stride, double *sm) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += NT) v += __ldcg(part + (size_t)i * stride);
+    return block_sum<NT>(v, sm);
+}
+
+__device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e308; }
+
+}  // namespace mpbjac

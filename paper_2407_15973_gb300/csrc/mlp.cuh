@@ -1,0 +1,24 @@
+// Learned per-block format selector: a 12 -> 64 -> 64 -> 3 ReLU MLP over block features.
+#pragma once
+#include "common.cuh"
+
+namespace mpbjac {
+
+constexpr int kFeat = 12, kH1 = 64, kH2 = 64, kCls = 3;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kH1 * kFeat;
+constexpr int kOffW2 = kOffB1 + kH1;
+constexpr int kOffB2 = kOffW2 + kH2 * kH1;
+constexpr int kOffW3 = kOffB2 + kH2;
+constexpr int kOffB3 = kOffW3 + kCls * kH2;
+constexpr int kMlpWeights = kOffB3 + kCls;          // 5187 trainable parameters
+constexpr int kOffMu = kMlpWeights;
+constexpr int kOffSd = kOffMu + kFeat;
+constexpr int kMlpParams = kOffSd + kFeat;          // + feature mean and standard deviation
+
+// params: HOST floats [kMlpParams]. Writes fmt[b] for every block (class -> format, then
+// promotion until kappa_1 * u_f <= safety_theta).
+int launch_mlp_select(const float *params, int nb, const double *feat, const double *kap, double safety_theta,
+                      uint8_t *fmt, cudaStream_t st);
+
+}  // namespace mpbjac

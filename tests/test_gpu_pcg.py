@@ -1,0 +1,157 @@
+"""Solver-level parity: GPU PCG with the BJAC policies against the oracle's PCG."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2407_15973_gb300 import problems as PB
+from gpu_util import cuda, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    return need_gpu()
+
+
+PROBLEMS = {
+    "poisson2d_bs8": lambda: PB.make_problem("poisson2d", bs=8),
+    "subcube24_bs32": lambda: PB.make_problem("subcube3d", seed=1, m=24, bs=32),
+    "subcube24_bs64": lambda: PB.make_problem("subcube3d", seed=2, m=24, bs=64),
+    "aniso27_12_bs64": lambda: PB.make_problem("aniso27", seed=3, m=12, bs=64),
+    "voronoi24_uneven": lambda: PB.make_problem("voronoi3d", seed=4, m=24),
+    "ragged13_bs32": lambda: PB.make_problem("subcube3d", seed=5, m=13, bs=32),
+}
+
+_cache = {}
+
+
+def _problem(name):
+    if name not in _cache:
+        pr = PROBLEMS[name]()
+        b = O.spmv(pr.A, pr.x_star)
+        _cache[name] = (pr, b, O.Preconditioner(pr.A, pr.block_ptr))
+    return _cache[name]
+
+
+def _gpu_solve(B, pr, b, maxit=3000, hist=False, **pol):
+    dA = B.DeviceCSR(pr.A)
+    h = B.bjac_setup(dA, pr.block_ptr, **pol)
+    x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+    hh = torch.full((maxit + 1,), float("nan"), dtype=torch.float64, device="cuda") if hist else None
+    st = h.solve(cuda(b), x, tol=TOL, maxit=maxit, hist=hh)
+    xs = host(x)
+    h.close()
+    st["x"] = xs
+    if hist:
+        st["hist"] = host(hh)[:st["iters"] + 1]
+    return st
+
+
+def _err(x, xs):
+    return np.linalg.norm(x - xs) / np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_uniform_fp64_iterations(B, name):
+    pr, b, P = _problem(name)
+    ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000)
+    got = _gpu_solve(B, pr, b, select=B.SELECT_UNIFORM, hist=True)
+    assert ref["converged"] and got["converged"]
+    assert abs(got["iters"] - ref["iters"]) <= 2
+    assert got["true_relres"] <= TOL
+    assert abs(_err(got["x"], pr.x_star) - _err(ref["x"], pr.x_star)) <= 10 * _err(ref["x"], pr.x_star) + 1e-12
+    k = min(got["iters"], ref["iters"], 20)
+    assert np.allclose(got["hist"][:k], ref["hist"][:k], rtol=1e-6)
+    assert got["high_applies"] > 0 and got["low_applies"] == 0
+
+
+@pytest.mark.parametrize("fmt", [1, 2, 3])
+@pytest.mark.parametrize("name", ["poisson2d_bs8", "subcube24_bs32", "subcube24_bs64", "voronoi24_uneven",
+                                  "aniso27_12_bs64"])
+def test_fmp_iterations(B, name, fmt):
+    pr, b, P = _problem(name)
+    P.set_formats(fmt)
+    ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000, policy=O.POLICY_FMP, mode=1)
+    got = _gpu_solve(B, pr, b, select=B.SELECT_FIXED, fixed_fmt=fmt)
+    assert got["converged"] and got["true_relres"] <= TOL
+    if ref["converged"]:
+        assert abs(got["iters"] - ref["iters"]) <= max(3, 0.05 * ref["iters"])
+    assert got["blocks_per_fmt"][fmt] == P.nb
+
+
+@pytest.mark.parametrize("temporal,adp,limit", [(1, 1e-30, "uniform"), (1, 1e30, "fmp"),
+                                                (2, 1e30, "uniform"), (2, 1e-30, "fmp")])
+def test_amp_limits(B, temporal, adp, limit):
+    # Section 4.3.2: hl -> uniform (adp_tol -> 0) and fMP (adp_tol -> inf); lh the reverse
+    pr, b, P = _problem("subcube24_bs32")
+    uni = _gpu_solve(B, pr, b, select=B.SELECT_UNIFORM)
+    fmp = _gpu_solve(B, pr, b, select=B.SELECT_FIXED, fixed_fmt=B.BF16)
+    got = _gpu_solve(B, pr, b, select=B.SELECT_FIXED, fixed_fmt=B.BF16, temporal=temporal, adp_tol=adp)
+    ref = uni if limit == "uniform" else fmp
+    assert abs(got["iters"] - ref["iters"]) <= 1
+    assert got["converged"]
+    if limit == "uniform":
+        assert got["low_applies"] == 0
+    else:
+        assert got["high_applies"] == 0
+
+
+@pytest.mark.parametrize("temporal,adp", [(1, 10.0), (1, 1e-4), (2, 1e-5), (2, 1e-2)])
+def test_amp_against_oracle(B, temporal, adp):
+    pr, b, P = _problem("subcube24_bs64")
+    P.set_formats(O.BF16)
+    pol = O.POLICY_HL if temporal == 1 else O.POLICY_LH
+    ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000, policy=pol, adp_tol=adp, mode=1)
+    got = _gpu_solve(B, pr, b, hist=True, select=B.SELECT_FIXED, fixed_fmt=B.BF16, temporal=temporal, adp_tol=adp)
+    assert got["converged"] and got["true_relres"] <= TOL
+    assert abs(got["iters"] - ref["iters"]) <= max(3, 0.05 * ref["iters"])
+    assert abs(got["low_applies"] - ref["low_applies"]) <= 3
+    # the switch follows the relres of the residual being preconditioned: applications happen
+    # after iterations 0 .. iters-1 (none after the converging one)
+    if got["restarts"] == 0:
+        h = got["hist"][:got["iters"]]
+        expect_low = int(np.sum(h < adp)) if temporal == 1 else int(np.sum(h >= adp))
+        assert got["low_applies"] == expect_low
+        assert got["low_applies"] + got["high_applies"] == got["iters"]
+
+
+def test_rule_and_fallback(B):
+    pr, b, P = _problem("voronoi24_uneven")
+    got = _gpu_solve(B, pr, b, select=B.SELECT_RULE, fp64_fallback=True)
+    assert got["converged"] and got["true_relres"] <= TOL
+    assert sum(got["blocks_per_fmt"]) == P.nb
+
+
+def test_zero_rhs_and_maxit(B):
+    pr, b, P = _problem("poisson2d_bs8")
+    dA = B.DeviceCSR(pr.A)
+    h = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    x = torch.ones(pr.A.n, dtype=torch.float64, device="cuda")
+    st = h.solve(torch.zeros(pr.A.n, dtype=torch.float64, device="cuda"), x)
+    assert st["status"] == 0 and st["iters"] == 0 and torch.all(x == 0)
+    x.zero_()
+    st = h.solve(cuda(b), x, maxit=5)
+    assert st["status"] == B.NOT_CONVERGED and st["iters"] == 5 and not st["converged"]
+    # warm start from the exact solution: nothing to do
+    x = cuda(pr.x_star)
+    st = h.solve(cuda(b), x)
+    assert st["iters"] <= 1
+    h.close()
+
+
+def test_repeat_solves_identical(B):
+    pr, b, P = _problem("subcube24_bs32")
+    dA = B.DeviceCSR(pr.A)
+    h = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=B.FP16S)
+    xs = []
+    for _ in range(3):
+        x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+        st = h.solve(cuda(b), x)
+        xs.append((st["iters"], host(x)))
+    h.close()
+    assert xs[0][0] == xs[1][0] == xs[2][0]
+    assert np.array_equal(xs[0][1], xs[1][1]) and np.array_equal(xs[0][1], xs[2][1])
