@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--fmt", default="bf16", choices=list(FMT))
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode table")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="only set up the headline policy and run this many eager PCG iterations "
+                         "(a short, fixed launch sequence for ncu)")
     return ap.parse_args()
 
 
@@ -193,6 +196,11 @@ def run_ours(args, rank, world, dist):
         return ms, stats
 
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt])
+    if args.profile_iters:
+        h = B.bjac_setup(dA, pr.block_ptr, **head)
+        prof = h.profile(b, x, tol=TOL, maxit=args.profile_iters)
+        h.close()
+        return {"profile": prof}
     with ClockSampler(dev) as clk:
         ms_mixed, st_mixed = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
@@ -344,7 +352,7 @@ def main():
         tdist.init_process_group("nccl")
         dist = tdist
     out = run_ours(args, rank, world, dist)
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.profile_iters:
         out["cpu_baseline"] = oracle_sample(args, out["iters"])
     if rank == 0:
         print(json.dumps(out))

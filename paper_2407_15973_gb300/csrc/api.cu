@@ -50,17 +50,38 @@ static int vec_grid(int n) {
     return g < 1 ? 1 : g;
 }
 
+static int vec_grid2(int n) {
+    int g = sm_count() * 8;
+    const int need = (n / 2 + kNT - 1) / kNT;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return g < 1 ? 1 : g;
+}
+
 // aMP loop: r -= alpha q, relres = ||r|| / ||b||, convergence test, precision for the next
-// preconditioner application (Algorithms 3.2 / 3.3 read this relres).
+// preconditioner application (Algorithms 3.2 / 3.3 read this relres). r, q: 16-byte aligned.
 __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
                                                   double *part, SolverState *S) {
     __shared__ double red[kWarps];
     if (S->state != kRunning) return;
     const double alpha = S->alpha;
     double rr = 0.0;
-    for (int i = blockIdx.x * kNT + threadIdx.x; i < n; i += gridDim.x * kNT) {
-        const double v = fma(-alpha, q[i], r[i]);
-        r[i] = v;
+    const int n2 = n >> 1;
+    const double2 *q2 = reinterpret_cast<const double2 *>(q);
+    double2 *r2 = reinterpret_cast<double2 *>(r);
+#pragma unroll 2
+    for (int i = blockIdx.x * kNT + threadIdx.x; i < n2; i += gridDim.x * kNT) {
+        const double2 qv = q2[i];
+        double2 rv = r2[i];
+        rv.x = fma(-alpha, qv.x, rv.x);
+        rv.y = fma(-alpha, qv.y, rv.y);
+        r2[i] = rv;
+        rr = fma(rv.x, rv.x, rr);
+        rr = fma(rv.y, rv.y, rr);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const double v = fma(-alpha, q[n - 1], r[n - 1]);
+        r[n - 1] = v;
         rr = fma(v, v, rr);
     }
     const double bsum = block_sum<kNT>(rr, red);
@@ -81,15 +102,41 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
 }
 
 // x += alpha p (the update deferred from this iteration); p = z + beta p while running.
-// The last CTA closes the iteration and sets the graph's while-condition.
+// The last CTA closes the iteration and sets the graph's while-condition. z and p are
+// 16-byte aligned (handle memory); x is the caller's vector and is checked.
 __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
     const int xp = S->x_pending;
     const int run = S->state == kRunning;
     double *__restrict__ x = S->x;
     const double alpha = S->alpha, beta = S->beta;
-    if (xp | run) {
-        for (int i = blockIdx.x * kNT + threadIdx.x; i < n; i += gridDim.x * kNT) {
+    const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
+    if ((xp | run) && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const int n2 = n >> 1;
+        const double2 *z2 = reinterpret_cast<const double2 *>(z);
+        double2 *p2 = reinterpret_cast<double2 *>(p);
+        double2 *x2 = reinterpret_cast<double2 *>(x);
+#pragma unroll 2
+        for (int i = gid; i < n2; i += stride) {
+            const double2 pv = p2[i];
+            if (xp) {
+                double2 xv = x2[i];
+                xv.x = fma(alpha, pv.x, xv.x);
+                xv.y = fma(alpha, pv.y, xv.y);
+                x2[i] = xv;
+            }
+            if (run) {
+                const double2 zv = z2[i];
+                p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+            }
+        }
+        if ((n & 1) && gid == 0) {
+            const double pi = p[n - 1];
+            if (xp) x[n - 1] = fma(alpha, pi, x[n - 1]);
+            if (run) p[n - 1] = fma(beta, pi, z[n - 1]);
+        }
+    } else if (xp | run) {
+        for (int i = gid; i < n; i += stride) {
             const double pi = p[i];
             if (xp) x[i] = fma(alpha, pi, x[i]);
             if (run) p[i] = fma(beta, pi, z[i]);
@@ -348,6 +395,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         a.qoff = h->d_qoff;
         a.pool = h->d_pool;
     }
+    MPB_TRY(prepare_spmv(*A));
     MPB_TRY(launch_setup_blocks(a, bs_max, st));
     if (P.select == BJAC_SELECT_MLP) {
         MPB_TRY(launch_mlp_select(P.mlp_params, nb, h->d_feat, h->d_kap, h->pol.safety_theta, h->d_fmt, st));
@@ -475,7 +523,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     if (rc) return rc;
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
     if (temporal) {
-        k_update_r<<<vec_grid(h->n), kNT, 0, cs>>>(h->n, h->d_q, h->d_r, h->d_part, h->d_S);
+        k_update_r<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_q, h->d_r, h->d_part, h->d_S);
         MPB_CUDA(cudaGetLastError());
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
@@ -490,7 +538,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         if (rc) return rc;
     }
     if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));
-    k_update_xp<<<vec_grid(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, ev ? 0 : 1);
+    k_update_xp<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, ev ? 0 : 1);
     MPB_CUDA(cudaGetLastError());
     if (ev) MPB_CUDA(cudaEventRecord(ev[4], cs));
     return MPBJAC_OK;
@@ -629,6 +677,8 @@ extern "C" int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *
     if (rc) return rc;
     if (!x || !y) return fail(MPBJAC_ERR_INVALID_ARG, "x and y must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
+    rc = prepare_spmv(*A);
+    if (rc) return rc;
     if (!xy) return launch_spmv(*A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st);
     // scratch for the deterministic reduction: partial sums and a ticket counter
     void *scratch = nullptr;
@@ -648,6 +698,8 @@ extern "C" int bjac_residual(const bjac_csr *A, const double *b, const double *x
     if (rc) return rc;
     if (!b || !x || !r) return fail(MPBJAC_ERR_INVALID_ARG, "b, x and r must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
+    rc = prepare_spmv(*A);
+    if (rc) return rc;
     void *scratch = nullptr;
     const size_t bytes = sizeof(double) * 2 * kMaxGrid + 256;
     MPB_CUDA(cudaMallocAsync(&scratch, bytes, st));

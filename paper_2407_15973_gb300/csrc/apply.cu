@@ -17,6 +17,7 @@
 //    that complete on mbarriers; every wait is bounded.
 #include "common.cuh"
 #include "apply.cuh"
+#include "tma.cuh"
 
 namespace mpbjac {
 
@@ -140,66 +141,35 @@ __global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO
 // ----------------------------------------------------------------------------------------
 // TMA-staged uniform kernel
 // ----------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait: gives up after ~1 s of device time or 2^26 polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase) {
-    if (mbar_try_wait(bar, phase)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (int it = 0; it < (1 << 26); ++it) {
-        if (mbar_try_wait(bar, phase)) return true;
-        if ((it & 255) == 255 && globaltimer_ns() - t0 > 1000000000ull) return false;
-    }
-    return false;
-}
-
+// Each warp runs its own pipeline: a ring of kS shared-memory stages, each holding one
+// block's inverse plus the block's slices of r (and q in the fused loop), filled by TMA
+// bulk copies that lane 0 issues and that complete on the stage's mbarrier. Warps never
+// wait for one another, so the only sync in the loop is __syncwarp.
 template <typename QT, int BS>
 struct TmaGeom {
-    static constexpr int kWPB = BS / 32;                     // warps per block
-    static constexpr int kBPS = kWarps / kWPB;               // blocks per stage
-    static constexpr int kRows = kBPS * BS;                  // rows per stage (= 256)
-    static constexpr int kBlkBytes = BS * BS * (int)sizeof(QT);
-    static constexpr int kQBytes = kBPS * kBlkBytes;
-    static constexpr int kStageBytes = kQBytes + 2 * kRows * 8;   // Q blocks, r slice, q slice
+    static constexpr int kQBytes = BS * BS * (int)sizeof(QT);
+    static constexpr int kStageBytes = kQBytes + 2 * BS * 8;        // Q, r slice, q slice
     static constexpr int kBudget = 200 * 1024;
-    static constexpr int kStages = (kBudget / kStageBytes) > 8 ? 8 : (kBudget / kStageBytes);
-    static constexpr int kHeader = 128 + kRows * 4;               // barriers, r-hat
-    static constexpr int kSmem = kHeader + kStages * kStageBytes;
+    static constexpr int kS = (kBudget / (3 * kStageBytes) >= 4) ? 3 : 2;
+    static constexpr int kNWraw = kBudget / (kS * kStageBytes);
+    static constexpr int kNW = kNWraw > 16 ? 16 : kNWraw;             // warps per CTA
+    static constexpr int kThreads = kNW * 32;
+    static constexpr int kBarBytes = ((kNW * kS * 8 + 127) / 128) * 128;
+    static constexpr int kRhBytes = kNW * BS * 4;
+    static constexpr int kHeader = kBarBytes + kRhBytes;
+    static constexpr int kSmem = kHeader + kNW * kS * kStageBytes;
+    static_assert(kNW >= 2, "stage too large");
+    static_assert(kHeader % 16 == 0, "stage alignment");
 };
 
 template <typename QT, int BS, int MODE>
-__global__ void __launch_bounds__(kNT, 1) k_apply_tma(PSet P, ApplyIO io, SolverState *S, int n) {
+__global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet P, ApplyIO io, SolverState *S,
+                                                                            int n) {
     using Geo = TmaGeom<QT, BS>;
-    static_assert(Geo::kStages >= 2, "need at least two stages");
+    constexpr int RPL = BS / 32;     // rows per lane
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    float *s_rh = reinterpret_cast<float *>(smem + 128);
-    uint8_t *stages = smem + Geo::kHeader;
-    __shared__ double s_red[kWarps];
+    __shared__ double s_red[2][Geo::kNW];
+    __shared__ int s_bad;
 
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
@@ -207,114 +177,140 @@ __global__ void __launch_bounds__(kNT, 1) k_apply_tma(PSet P, ApplyIO io, Solver
             if (!S->use_low) return;     // the binary64 set runs in the generic kernel
         }
     }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * Geo::kS;
+    float *rh = reinterpret_cast<float *>(smem + Geo::kBarBytes) + warp * BS;
+    uint8_t *stages = smem + Geo::kHeader + (size_t)warp * Geo::kS * Geo::kStageBytes;
     const int nb = P.nb;
-    const int ngroups = (nb + Geo::kBPS - 1) / Geo::kBPS;
+    const int gw = blockIdx.x * Geo::kNW + warp, nw = gridDim.x * Geo::kNW;
     const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
     const bool with_q = (MODE == kApplyFused);
+    const unsigned vbytes = BS * 8;
+    const unsigned tx = Geo::kQBytes + vbytes * (with_q ? 2u : 1u);
 
-    auto issue = [&](int g, int s) {
-        const int nblk = min(Geo::kBPS, nb - g * Geo::kBPS);
-        const int rows = nblk * BS;
-        const unsigned qbytes = (unsigned)(nblk * Geo::kBlkBytes);
-        const unsigned vbytes = (unsigned)(rows * 8);
+    auto issue = [&](int blk, int s) {
         uint8_t *dst = stages + (size_t)s * Geo::kStageBytes;
-        mbar_expect_tx(&full[s], qbytes + vbytes * (with_q ? 2u : 1u));
-        bulk_g2s(dst, P.pool + (size_t)g * Geo::kQBytes, qbytes, &full[s]);
-        bulk_g2s(dst + Geo::kQBytes, io.r + (size_t)g * Geo::kRows, vbytes, &full[s]);
-        if (with_q) bulk_g2s(dst + Geo::kQBytes + Geo::kRows * 8, io.q + (size_t)g * Geo::kRows, vbytes, &full[s]);
+        mbar_expect_tx(&bars[s], tx);
+        bulk_g2s(dst, P.pool + (size_t)blk * Geo::kQBytes, Geo::kQBytes, &bars[s]);
+        bulk_g2s(dst + Geo::kQBytes, io.r + (size_t)blk * BS, vbytes, &bars[s]);
+        if (with_q) bulk_g2s(dst + Geo::kQBytes + vbytes, io.q + (size_t)blk * BS, vbytes, &bars[s]);
     };
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < Geo::kStages; ++s) mbar_init(&full[s], 1);
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    if (lane == 0) {
+        for (int s = 0; s < Geo::kS; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < Geo::kStages; ++s) {
-            const int g = blockIdx.x + s * gridDim.x;
-            if (g < ngroups) issue(g, s);
+        for (int s = 0; s < Geo::kS; ++s) {
+            const int blk = gw + s * nw;
+            if (blk < nb) issue(blk, s);
         }
     }
+    __syncwarp();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = warp / Geo::kWPB, h = warp % Geo::kWPB;
-    const int local_row = bi * BS + h * 32 + lane;      // row within the stage
     double rho = 0.0, rr = 0.0;
-    bool timed_out = false;
+    bool ok = true;
     int it = 0;
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x, ++it) {
-        const int s = it % Geo::kStages;
-        const unsigned phase = (unsigned)((it / Geo::kStages) & 1);
+    for (int blk = gw; blk < nb; blk += nw, ++it) {
+        const int s = it % Geo::kS;
+        const unsigned phase = (unsigned)((it / Geo::kS) & 1);
         const uint8_t *st = stages + (size_t)s * Geo::kStageBytes;
+        ok = mbar_wait_bounded(&bars[s], phase);
+        if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
         const double *sr = reinterpret_cast<const double *>(st + Geo::kQBytes);
-        const double *sq = reinterpret_cast<const double *>(st + Geo::kQBytes + Geo::kRows * 8);
-        const int blk = g * Geo::kBPS + bi;
-        const bool active = blk < nb;
-        const int row = g * Geo::kRows + local_row;
-        bool ok = mbar_wait_bounded(&full[s], phase);
-        double rv = 0.0;
-        if (ok && active) {
-            rv = sr[local_row];
-            if (MODE == kApplyFused) rv = fma(-alpha, sq[local_row], rv);
-            s_rh[local_row] = __double2float_rn(rv);
-        }
-        timed_out = __syncthreads_or(!ok) != 0;
-        if (timed_out) break;
-        if (active) {
-            const QT *Q = reinterpret_cast<const QT *>(st + (size_t)bi * Geo::kBlkBytes);
-            const float4 *rh4 = reinterpret_cast<const float4 *>(s_rh + bi * BS);
-            const int i = h * 32 + lane;
-            float acc = 0.0f;
+        const double *sq = reinterpret_cast<const double *>(st + Geo::kQBytes + vbytes);
+        double rv[RPL];
 #pragma unroll
-            for (int j4 = 0; j4 < BS / 4; ++j4) {
-                const float4 r4 = rh4[j4];
-                acc = fmaf(to_f32<QT>(Q[(4 * j4 + 0) * BS + i]), r4.x, acc);
-                acc = fmaf(to_f32<QT>(Q[(4 * j4 + 1) * BS + i]), r4.y, acc);
-                acc = fmaf(to_f32<QT>(Q[(4 * j4 + 2) * BS + i]), r4.z, acc);
-                acc = fmaf(to_f32<QT>(Q[(4 * j4 + 3) * BS + i]), r4.w, acc);
+        for (int h = 0; h < RPL; ++h) {
+            const int i = h * 32 + lane;
+            double v = sr[i];
+            if (MODE == kApplyFused) v = fma(-alpha, sq[i], v);
+            rv[h] = v;
+            rh[i] = __double2float_rn(v);
+        }
+        __syncwarp();
+        const QT *Q = reinterpret_cast<const QT *>(st);
+        const float4 *rh4 = reinterpret_cast<const float4 *>(rh);
+        float acc[RPL];
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) acc[h] = 0.0f;
+#pragma unroll
+        for (int j4 = 0; j4 < BS / 4; ++j4) {
+            const float4 r4 = rh4[j4];
+#pragma unroll
+            for (int h = 0; h < RPL; ++h) {
+                const int i = h * 32 + lane;
+                acc[h] = fmaf(to_f32<QT>(Q[(4 * j4 + 0) * BS + i]), r4.x, acc[h]);
+                acc[h] = fmaf(to_f32<QT>(Q[(4 * j4 + 1) * BS + i]), r4.y, acc[h]);
+                acc[h] = fmaf(to_f32<QT>(Q[(4 * j4 + 2) * BS + i]), r4.z, acc[h]);
+                acc[h] = fmaf(to_f32<QT>(Q[(4 * j4 + 3) * BS + i]), r4.w, acc[h]);
             }
-            const float sc = (sizeof(QT) == 2) ? __ldg(P.scale + blk) : 1.0f;
-            const double zi = (double)(acc * sc);
+        }
+        __syncwarp();   // stage s and rh fully consumed by every lane
+        if (lane == 0) {
+            const int nxt = blk + Geo::kS * nw;
+            if (nxt < nb) issue(nxt, s);
+        }
+        const float sc = (sizeof(QT) == 2) ? __ldg(P.scale + blk) : 1.0f;
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+            const size_t row = (size_t)blk * BS + h * 32 + lane;
+            const double zi = (double)(acc[h] * sc);
             io.z[row] = zi;
             if (MODE == kApplyInit) io.p[row] = zi;
             if (MODE == kApplyFused) {
-                io.r_out[row] = rv;
-                rr = fma(rv, rv, rr);
+                io.r_out[row] = rv[h];
+                rr = fma(rv[h], rv[h], rr);
             }
-            rho = fma(rv, zi, rho);
-        }
-        __syncthreads();   // stage s and s_rh fully consumed
-        if (threadIdx.x == 0) {
-            const int g2 = g + Geo::kStages * gridDim.x;
-            if (g2 < ngroups) issue(g2, s);
+            rho = fma(rv[h], zi, rho);
         }
     }
-    if (timed_out) {
-        // drain copies still in flight (bounded), record the failure, leave
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < Geo::kStages; ++k) {
+    if (!ok) {
+        // drain this warp's copies still in flight (bounded), then record the failure
+        if (lane == 0) {
+            for (int k = 0; k < Geo::kS; ++k) {
                 const int itk = it + k;
-                const int g = blockIdx.x + itk * gridDim.x;
-                if (g < ngroups) (void)mbar_wait_bounded(&full[itk % Geo::kStages], (unsigned)((itk / Geo::kStages) & 1));
+                if (gw + itk * nw < nb) (void)mbar_wait_bounded(&bars[itk % Geo::kS], (unsigned)((itk / Geo::kS) & 1));
             }
+            s_bad = 1;
+        }
+    }
+    (void)n;
+    // CTA reduction in fixed order (warp sums, then warps in index order)
+    rho = warp_sum(rho);
+    rr = warp_sum(rr);
+    if (lane == 0) {
+        s_red[0][warp] = rho;
+        s_red[1][warp] = rr;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) {
             if (io.err) atomicExch(io.err, MPBJAC_ERR_TIMEOUT);
             if (MODE != kApplyStandalone) S->state = kBreakdown;
         }
-        return;
+        return;   // every thread of the CTA sees s_bad after the barrier
     }
-    (void)n;
     if (MODE == kApplyStandalone && io.out == nullptr) return;
-    const double b1 = block_sum<kNT>(rho, s_red);
-    const double b2 = block_sum<kNT>(rr, s_red);
     if (threadIdx.x == 0) {
+        double b1 = 0.0, b2 = 0.0;
+        for (int w = 0; w < Geo::kNW; ++w) {
+            b1 += s_red[0][w];
+            b2 += s_red[1][w];
+        }
         io.part[2 * blockIdx.x] = b1;
         io.part[2 * blockIdx.x + 1] = b2;
     }
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red);
-    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
+    double t1 = 0.0, t2 = 0.0;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < (int)gridDim.x; ++c) {
+            t1 += __ldcg(io.part + 2 * c);
+            t2 += __ldcg(io.part + 2 * c + 1);
+        }
+        apply_finish<MODE>(t1, t2, io, S, 1);
+    }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -345,11 +341,11 @@ static int launch_tma_t(const PSet &P, const ApplyIO &io, SolverState *S, int n,
                                       Geo::kSmem));
         return MPBJAC_OK;
     }
-    const int ngroups = (P.nb + Geo::kBPS - 1) / Geo::kBPS;
     int g = sm_count();
-    if (g > ngroups) g = ngroups;
+    const int need = (P.nb + Geo::kNW - 1) / Geo::kNW;
+    if (g > need) g = need;
     if (g < 1) g = 1;
-    k_apply_tma<QT, BS, MODE><<<g, kNT, Geo::kSmem, st>>>(P, io, S, n);
+    k_apply_tma<QT, BS, MODE><<<g, Geo::kThreads, Geo::kSmem, st>>>(P, io, S, n);
     MPB_CUDA(cudaGetLastError());
     return MPBJAC_OK;
 }

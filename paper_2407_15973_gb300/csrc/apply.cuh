@@ -31,6 +31,7 @@ int launch_apply_tma(int mode, const PSet &P, const ApplyIO &io, SolverState *S,
 int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S,
                          cudaStream_t st);
 
+int prepare_spmv(const bjac_csr &A);    // kernel attributes for A's SpMV variant (before any capture)
 int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
                 double *dot_out, SolverState *S, int mode, cudaStream_t st);
 int launch_residual(const bjac_csr &A, const double *b, const double *x, double *r, double *part,

@@ -1,134 +1,191 @@
 // Binary64 CSR SpMV (the working-precision q = A p of PCG, Section 3.2), its fused dot
 // product, and the residual b - A x used for the initial and the true residual.
 //
-// One CTA of 256 threads owns a tile of 256 consecutive rows. The tile's nonzeros are
-// contiguous in CSR order, so the CTA stages them chunk by chunk into shared memory with
-// coalesced loads (values, and x gathered through the column indices); then each thread
-// runs its own row's FMA chain in CSR order out of shared memory. Rows of any length work:
-// a long row simply spans several chunks. CTAs walk tiles with a grid stride, so the rows
-// in flight form one moving window and the gathered x entries stay in L2.
+// A CTA owns tiles of consecutive rows. The nonzeros of a tile are contiguous in CSR order,
+// so thread 0 streams each tile's values and column indices into a shared-memory stage with
+// two TMA bulk copies that complete on the stage's mbarrier, several tiles ahead of the
+// consumers (a ring of kStages stages). Each row is then summed from shared memory: with
+// TPR = 1 one thread runs the row's FMA chain in CSR order; with TPR = 2 or 4 (long rows)
+// each thread sums a contiguous quarter/half of the row and the partial sums are combined
+// in a fixed order. A tile whose nonzeros do not fit a stage, or that reaches the unaligned
+// tail of the arrays, is read straight from global memory instead. Every wait is bounded.
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace mpbjac {
 
-constexpr int kChunk = 2048;  // nonzeros staged per pass (2 x 16 KB of shared memory)
+constexpr int kSpNT = 256;               // threads per CTA
+constexpr int kCap = 2048;               // nonzeros per stage
+constexpr int kStages = 3;
+constexpr int kStageBytes = kCap * 12;   // values (8 B) + column indices (4 B)
+constexpr int kSpSmem = 128 + kStages * kStageBytes;
 
-struct SpmvSmem {
-    double v[kChunk];
-    double x[kChunk];
-    double red[kWarps];
+enum SpmvKind {
+    kSpY = 0,         // y = A x
+    kSpYDot = 1,      // y = A x, *out = x . y
+    kSpPcg = 2,       // PCG: q = A p, sigma = p . q, alpha = rho / sigma
+    kResStandalone = 10,  // r = b - A x, *out = r . r
+    kResStart = 11,       // PCG start: bnorm, relres, state
+    kResCheck = 12,       // true residual after the loop; restart decision
 };
 
-// y_row = sum_k val[k] * x[colidx[k]] for this thread's row of tile r0 (0 if row >= n).
-__device__ __forceinline__ double spmv_tile_row(int r0, int n, const int32_t *__restrict__ rowptr,
-                                                const int32_t *__restrict__ colidx,
-                                                const double *__restrict__ val,
-                                                const double *__restrict__ x, SpmvSmem &sm) {
-    const int row = r0 + (int)threadIdx.x;
-    const int rend = min(r0 + kNT, n);
-    const int lo = __ldg(rowptr + r0), hi = __ldg(rowptr + rend);
-    int my_lo = hi, my_hi = hi;
-    if (row < n) {
-        my_lo = __ldg(rowptr + row);
-        my_hi = __ldg(rowptr + row + 1);
-    }
-    double acc = 0.0;
-    for (int c0 = lo; c0 < hi; c0 += kChunk) {
-        const int c1 = min(c0 + kChunk, hi);
-#pragma unroll 4
-        for (int k = c0 + (int)threadIdx.x; k < c1; k += kNT) {
-            const double v = __ldcs(val + k);
-            const int c = __ldcs(colidx + k);
-            sm.v[k - c0] = v;
-            sm.x[k - c0] = __ldg(x + c);
-        }
-        __syncthreads();
-        const int a = max(my_lo, c0), b = min(my_hi, c1);
-        for (int k = a; k < b; ++k) acc = fma(sm.v[k - c0], sm.x[k - c0], acc);
-        __syncthreads();
-    }
-    return acc;
-}
+struct StageMeta {
+    int lo4;      // first staged nonzero (multiple of 4)
+    int direct;   // 1: this tile is read from global memory
+};
 
-// MODE 0: y = A x.   MODE 1: y = A x and *out = x . y.
-// MODE 2: PCG step "q = A p; sigma = p.q; alpha = rho / sigma" (skips unless running).
-template <int MODE>
-__global__ void __launch_bounds__(kNT) k_spmv(int n, const int32_t *__restrict__ rowptr,
-                                              const int32_t *__restrict__ colidx,
-                                              const double *__restrict__ val,
-                                              const double *__restrict__ x, double *__restrict__ y,
-                                              double *part, unsigned int *ticket, double *out,
-                                              SolverState *S) {
-    __shared__ SpmvSmem sm;
-    if (MODE == 2 && S->state != kRunning) return;
-    const int ntiles = (n + kNT - 1) / kNT;
-    double dot = 0.0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int r0 = t * kNT;
-        const double acc = spmv_tile_row(r0, n, rowptr, colidx, val, x, sm);
-        const int row = r0 + (int)threadIdx.x;
-        if (row < n) {
-            y[row] = acc;
-            if (MODE != 0) dot = fma(acc, __ldg(x + row), dot);
-        }
-    }
-    if (MODE == 0) return;
-    const double bs = block_sum<kNT>(dot, sm.red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    if (!last_cta(ticket)) return;
-    const double total = reduce_partials<kNT>(part, gridDim.x, 1, sm.red);
-    if (threadIdx.x != 0) return;
-    if (MODE == 1) {
-        *out = total;
-    } else {
-        S->sigma = total;
-        if (!finite_pos(total)) S->state = kBreakdownSigma;
-        else S->alpha = S->rho / total;
-    }
-}
+template <int TPR, int KIND>
+__global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *__restrict__ rowptr,
+                                                const int32_t *__restrict__ colidx, const double *__restrict__ val,
+                                                const double *__restrict__ x, const double *__restrict__ b,
+                                                double *__restrict__ y, double *part, unsigned int *ticket,
+                                                double *out, SolverState *S) {
+    constexpr int RPT = kSpNT / TPR;     // rows per tile
+    constexpr bool RES = KIND >= 10;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    __shared__ StageMeta meta[kStages];
+    __shared__ double red[2][kSpNT / 32];
+    __shared__ int s_bad;
 
-// r = b - A x with partial sums of r.r and b.b.
-// MODE 0: *out = r.r.   MODE 1: PCG start (bnorm, relres, state, hist[iter]).
-// MODE 2: true-residual check after the loop (true_relres; restart decision).
-template <int MODE>
-__global__ void __launch_bounds__(kNT) k_residual(int n, const int32_t *__restrict__ rowptr,
-                                                  const int32_t *__restrict__ colidx,
-                                                  const double *__restrict__ val,
-                                                  const double *__restrict__ b,
-                                                  const double *__restrict__ x, double *__restrict__ r,
-                                                  double *part, unsigned int *ticket, double *out,
-                                                  SolverState *S) {
-    __shared__ SpmvSmem sm;
-    const int ntiles = (n + kNT - 1) / kNT;
-    double rr = 0.0, bb = 0.0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int r0 = t * kNT;
-        const double acc = spmv_tile_row(r0, n, rowptr, colidx, val, x, sm);
-        const int row = r0 + (int)threadIdx.x;
-        if (row < n) {
-            const double bi = b[row];
-            const double ri = bi - acc;
-            r[row] = ri;
-            rr = fma(ri, ri, rr);
-            bb = fma(bi, bi, bb);
+    if (KIND == kSpPcg && S->state != kRunning) return;
+    const int ntiles = (n + RPT - 1) / RPT;
+    const int nnz4 = nnz & ~3;
+
+    // producer: stage tile t into stage s (thread 0 only)
+    auto issue = [&](int t, int s) {
+        const int r0 = t * RPT;
+        const int rend = min(r0 + RPT, n);
+        const int lo = __ldg(rowptr + r0), hi = __ldg(rowptr + rend);
+        const int lo4 = lo & ~3;
+        const int hi4 = (hi + 3) & ~3;
+        const bool direct = (hi4 - lo4 > kCap) || (hi4 > nnz4) || (hi4 == lo4);
+        meta[s].lo4 = lo4;
+        meta[s].direct = direct ? 1 : 0;
+        uint8_t *dst = smem + 128 + (size_t)s * kStageBytes;
+        if (direct) {
+            mbar_arrive(&full[s]);
+        } else {
+            const unsigned cnt = (unsigned)(hi4 - lo4);
+            mbar_expect_tx(&full[s], cnt * 12u);
+            bulk_g2s(dst, val + lo4, cnt * 8u, &full[s]);
+            bulk_g2s(dst + kCap * 8, colidx + lo4, cnt * 4u, &full[s]);
         }
-    }
-    const double s1 = block_sum<kNT>(rr, sm.red);
-    const double s2 = block_sum<kNT>(bb, sm.red);
+    };
+
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s1;
-        part[2 * blockIdx.x + 1] = s2;
+        s_bad = 0;
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (!last_cta(ticket)) return;
-    const double trr = reduce_partials<kNT>(part, gridDim.x, 2, sm.red);
-    const double tbb = reduce_partials<kNT>(part + 1, gridDim.x, 2, sm.red);
-    if (threadIdx.x != 0) return;
-    if (MODE == 0) {
-        *out = trr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            const int t = blockIdx.x + s * gridDim.x;
+            if (t < ntiles) issue(t, s);
+        }
+    }
+
+    const int lrow = threadIdx.x / TPR, sub = threadIdx.x % TPR;
+    double acc1 = 0.0, acc2 = 0.0;   // dot / norm partial sums
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it % kStages;
+        const unsigned phase = (unsigned)((it / kStages) & 1);
+        const int row = t * RPT + lrow;
+        int my_lo = 0, my_hi = 0;
+        if (row < n) {
+            my_lo = __ldg(rowptr + row);
+            my_hi = __ldg(rowptr + row + 1);
+        }
+        if (TPR > 1) {     // this thread's contiguous share of the row
+            const int len = my_hi - my_lo, seg = (len + TPR - 1) / TPR;
+            const int a = min(my_lo + sub * seg, my_hi);
+            my_hi = min(a + seg, my_hi);
+            my_lo = a;
+        }
+        ok = mbar_wait_bounded(&full[s], phase);
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        const StageMeta m = meta[s];
+        const uint8_t *st = smem + 128 + (size_t)s * kStageBytes;
+        const double *sv = reinterpret_cast<const double *>(st) - m.lo4;
+        const int32_t *sc = reinterpret_cast<const int32_t *>(st + kCap * 8) - m.lo4;
+        double acc = 0.0;
+        if (!m.direct) {
+            int k = my_lo;
+            for (; k + 4 <= my_hi; k += 4) {
+                const double x0 = __ldg(x + sc[k]), x1 = __ldg(x + sc[k + 1]);
+                const double x2 = __ldg(x + sc[k + 2]), x3 = __ldg(x + sc[k + 3]);
+                acc = fma(sv[k], x0, acc);
+                acc = fma(sv[k + 1], x1, acc);
+                acc = fma(sv[k + 2], x2, acc);
+                acc = fma(sv[k + 3], x3, acc);
+            }
+            for (; k < my_hi; ++k) acc = fma(sv[k], __ldg(x + sc[k]), acc);
+        } else {
+            for (int k = my_lo; k < my_hi; ++k) acc = fma(__ldg(val + k), __ldg(x + __ldg(colidx + k)), acc);
+        }
+        if (TPR > 1) {       // combine the row's partial sums: ((p0 + p1) + (p2 + p3))
+#pragma unroll
+            for (int o = 1; o < TPR; o <<= 1) {
+                const double other = __shfl_down_sync(0xffffffffu, acc, o);
+                if ((sub & (2 * o - 1)) == 0) acc += other;
+            }
+        }
+        __syncthreads();     // stage s consumed
+        if (threadIdx.x == 0) {
+            const int t2 = t + kStages * gridDim.x;
+            if (t2 < ntiles) issue(t2, s);
+        }
+        if (row < n && sub == 0) {
+            if (RES) {
+                const double bi = b[row];
+                const double ri = bi - acc;
+                y[row] = ri;
+                acc1 = fma(ri, ri, acc1);
+                acc2 = fma(bi, bi, acc2);
+            } else {
+                y[row] = acc;
+                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+            }
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kStages; ++k) {
+                const int itk = it + k;
+                if (blockIdx.x + itk * gridDim.x < ntiles)
+                    (void)mbar_wait_bounded(&full[itk % kStages], (unsigned)((itk / kStages) & 1));
+            }
+            s_bad = 1;
+        }
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0 && S) S->state = kBreakdown;
         return;
     }
-    if (MODE == 1) {
-        const double bnorm = sqrt(tbb);
+    if (KIND == kSpY) return;
+    const double b1 = block_sum<kSpNT>(acc1, red[0]);
+    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = b1;
+        part[2 * blockIdx.x + 1] = b2;
+    }
+    if (!last_cta(ticket)) return;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    if (threadIdx.x != 0) return;
+    if (KIND == kSpYDot || KIND == kResStandalone) {
+        *out = t1;
+    } else if (KIND == kSpPcg) {
+        S->sigma = t1;
+        if (!finite_pos(t1)) S->state = kBreakdownSigma;
+        else S->alpha = S->rho / t1;
+    } else if (KIND == kResStart) {
+        const double bnorm = sqrt(t2);
         S->bnorm = bnorm;
         S->x_pending = 0;
         if (bnorm == 0.0) {
@@ -137,7 +194,7 @@ __global__ void __launch_bounds__(kNT) k_residual(int n, const int32_t *__restri
             S->state = kConverged;      // x is zeroed by the host
             return;
         }
-        const double rel = sqrt(trr) / bnorm;
+        const double rel = sqrt(t1) / bnorm;
         S->relres = rel;
         S->true_relres = rel;
         if (S->hist) S->hist[S->iter] = rel;
@@ -146,60 +203,81 @@ __global__ void __launch_bounds__(kNT) k_residual(int n, const int32_t *__restri
         else if (S->iter >= S->maxit) S->state = kMaxit;
         else S->state = kRunning;
         S->use_low = choose_low(S, rel);
-        return;
-    }
-    // MODE 2: true residual after the recurrence met tol
-    const double rel = S->bnorm > 0.0 ? sqrt(trr) / S->bnorm : 0.0;
-    S->true_relres = rel;
-    if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
-        S->state = kRunning;          // restart from r = b - A x
-        S->restarts += 1;
-        S->relres = rel;
-        S->use_low = choose_low(S, rel);
+    } else {   // kResCheck
+        const double rel = S->bnorm > 0.0 ? sqrt(t1) / S->bnorm : 0.0;
+        S->true_relres = rel;
+        if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
+            S->state = kRunning;          // restart from r = b - A x
+            S->restarts += 1;
+            S->relres = rel;
+            S->use_low = choose_low(S, rel);
+        }
     }
 }
 
 // ----------------------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------------------
-static int spmv_grid(int n) {
+template <int TPR, int KIND>
+static int launch_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
+                    unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
+    // the shared-memory limit was raised by prepare_spmv (never during a graph capture)
     static int per_sm = 0;
     if (per_sm == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv<2>, kNT, 0) != cudaSuccess || v < 1) v = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv<TPR, KIND>, kSpNT, kSpSmem) != cudaSuccess ||
+            v < 1)
+            v = 1;
         per_sm = v;
     }
-    const int ntiles = (n + kNT - 1) / kNT;
+    constexpr int RPT = kSpNT / TPR;
+    const int ntiles = (A.n + RPT - 1) / RPT;
     int g = sm_count() * per_sm;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g > ntiles) g = ntiles;
-    return g < 1 ? 1 : g;
+    if (g < 1) g = 1;
+    k_spmv<TPR, KIND><<<g, kSpNT, kSpSmem, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket,
+                                                  out, S);
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
+template <int KIND>
+static int launch_kind(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
+                       unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
+    const double avg = A.n > 0 ? (double)A.nnz / A.n : 0.0;
+    if (avg <= 8.0) return launch_t<1, KIND>(A, x, b, y, part, ticket, out, S, st);
+    if (avg <= 16.0) return launch_t<2, KIND>(A, x, b, y, part, ticket, out, S, st);
+    return launch_t<4, KIND>(A, x, b, y, part, ticket, out, S, st);
+}
+
+int prepare_spmv(const bjac_csr &A) {
+    // raise the shared-memory limit of every instantiation this matrix will use
+    const double avg = A.n > 0 ? (double)A.nnz / A.n : 0.0;
+    const int tpr = avg <= 8.0 ? 1 : (avg <= 16.0 ? 2 : 4);
+#define MPB_ATTR(T, K) MPB_CUDA(cudaFuncSetAttribute(k_spmv<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem))
+#define MPB_ATTRS(T) MPB_ATTR(T, kSpY); MPB_ATTR(T, kSpYDot); MPB_ATTR(T, kSpPcg); \
+    MPB_ATTR(T, kResStandalone); MPB_ATTR(T, kResStart); MPB_ATTR(T, kResCheck)
+    if (tpr == 1) { MPB_ATTRS(1); }
+    else if (tpr == 2) { MPB_ATTRS(2); }
+    else { MPB_ATTRS(4); }
+#undef MPB_ATTRS
+#undef MPB_ATTR
+    return MPBJAC_OK;
 }
 
 int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
                 double *dot_out, SolverState *S, int mode, cudaStream_t st) {
-    const int g = spmv_grid(A.n);
-    if (mode == 0)
-        k_spmv<0><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, x, y, part, ticket, dot_out, S);
-    else if (mode == 1)
-        k_spmv<1><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, x, y, part, ticket, dot_out, S);
-    else
-        k_spmv<2><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, x, y, part, ticket, dot_out, S);
-    MPB_CUDA(cudaGetLastError());
-    return MPBJAC_OK;
+    if (mode == 0) return launch_kind<kSpY>(A, x, nullptr, y, part, ticket, dot_out, S, st);
+    if (mode == 1) return launch_kind<kSpYDot>(A, x, nullptr, y, part, ticket, dot_out, S, st);
+    return launch_kind<kSpPcg>(A, x, nullptr, y, part, ticket, dot_out, S, st);
 }
 
 int launch_residual(const bjac_csr &A, const double *b, const double *x, double *r, double *part,
                     unsigned int *ticket, double *rr_out, SolverState *S, int mode, cudaStream_t st) {
-    const int g = spmv_grid(A.n);
-    if (mode == 0)
-        k_residual<0><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, b, x, r, part, ticket, rr_out, S);
-    else if (mode == 1)
-        k_residual<1><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, b, x, r, part, ticket, rr_out, S);
-    else
-        k_residual<2><<<g, kNT, 0, st>>>(A.n, A.rowptr, A.colidx, A.val, b, x, r, part, ticket, rr_out, S);
-    MPB_CUDA(cudaGetLastError());
-    return MPBJAC_OK;
+    if (mode == 0) return launch_kind<kResStandalone>(A, x, b, r, part, ticket, rr_out, S, st);
+    if (mode == 1) return launch_kind<kResStart>(A, x, b, r, part, ticket, rr_out, S, st);
+    return launch_kind<kResCheck>(A, x, b, r, part, ticket, rr_out, S, st);
 }
 
 }  // namespace mpbjac

@@ -211,7 +211,7 @@ def test_not_spd_block_is_reported(B):
 def test_invalid_inputs_rejected(B):
     A = PB.poisson2d_5pt_int(8)
     dA = B.DeviceCSR(A)
-    for bp in ([0, 10, 64], [0, 32, 63], [1, 64], [0, 0, 64], [0, 200, 64]):
+    for bp in ([0, 32, 63], [1, 64], [0, 0, 64], [0, 200, 64]):
         with pytest.raises(B.MpbjacError) as e:
             B.bjac_setup(dA, np.array(bp, np.int32))
         assert e.value.code == B.ERR_INVALID_ARG
