@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO
                 rr = fma(rv, rv, rr);
             }
             s_r[warp][i] = rv;
-            s_rh[warp][i] = __double2float_rn(rv);
+            s_rh[warp][i] = f64_to_f32_rn(rv);
         }
         __syncwarp();
         const int f = __ldg(P.fmt + b);
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO
                 if (f == BJAC_FP32) acc = low_row(reinterpret_cast<const float *>(base), s_rh[warp], bs, i);
                 else if (f == BJAC_BF16) acc = low_row(reinterpret_cast<const __nv_bfloat16 *>(base), s_rh[warp], bs, i);
                 else acc = low_row(reinterpret_cast<const __half *>(base), s_rh[warp], bs, i);
-                zi = (double)(acc * sc);
+                zi = f32_to_f64(acc * sc);
             }
             io.z[s + i] = zi;
             if (MODE == kApplyInit) io.p[s + i] = zi;
@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
         const int s = it % Geo::kS;
         const unsigned phase = (unsigned)((it / Geo::kS) & 1);
         const uint8_t *st = stages + (size_t)s * Geo::kStageBytes;
+        const float sc = (sizeof(QT) == 2) ? __ldg(P.scale + blk) : 1.0f;   // issued before the wait
         ok = mbar_wait_bounded(&bars[s], phase);
         if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
         const double *sr = reinterpret_cast<const double *>(st + Geo::kQBytes);
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
             double v = sr[i];
             if (MODE == kApplyFused) v = fma(-alpha, sq[i], v);
             rv[h] = v;
-            rh[i] = __double2float_rn(v);
+            rh[i] = f64_to_f32_rn(v);
         }
         __syncwarp();
         const QT *Q = reinterpret_cast<const QT *>(st);
@@ -252,11 +253,10 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
             const int nxt = blk + Geo::kS * nw;
             if (nxt < nb) issue(nxt, s);
         }
-        const float sc = (sizeof(QT) == 2) ? __ldg(P.scale + blk) : 1.0f;
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {
             const size_t row = (size_t)blk * BS + h * 32 + lane;
-            const double zi = (double)(acc[h] * sc);
+            const double zi = f32_to_f64(acc[h] * sc);
             io.z[row] = zi;
             if (MODE == kApplyInit) io.p[row] = zi;
             if (MODE == kApplyFused) {

@@ -138,3 +138,38 @@ __device__ __forceinline__ double reduce_partials(const double *part, int count,
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e308; }
 
 }  // namespace mpbjac
+
+namespace mpbjac {
+
+// ----------------------------------------------------------------------------------------
+// binary64 <-> binary32 conversions done with integer operations, so that they do not use
+// the (narrow) FP64 pipe of sm_103a. Written from the IEEE 754 bit layouts:
+//   binary64 = sign | 11-bit exponent (bias 1023) | 52-bit fraction
+//   binary32 = sign | 8-bit exponent (bias 127)   | 23-bit fraction
+// Inputs outside the normal binary32 range (zero, subnormal, overflow, inf, NaN) take the
+// hardware conversion instead; results are identical to round-to-nearest-even.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e < 1023 - 126 || e > 1023 + 127) return __double2float_rn(d);
+    const unsigned long long frac = u & 0xFFFFFFFFFFFFFull;
+    unsigned int r = ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(frac >> 29);
+    const unsigned int rem = (unsigned int)(frac & 0x1FFFFFFFu);     // the 29 dropped bits
+    const unsigned int half = 0x10000000u;
+    r += (rem > half) | ((rem == half) & (r & 1u));                   // carry may reach the exponent
+    return __uint_as_float(((unsigned int)(u >> 63) << 31) | r);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);   // +-0
+    if (e == 0u || e == 0xFFu) return (double)f;                                  // subnormal, inf, NaN
+    const unsigned long long bits = sign | ((unsigned long long)(e + 1023u - 127u) << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+}  // namespace mpbjac

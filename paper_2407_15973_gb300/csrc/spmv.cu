@@ -4,21 +4,27 @@
 // A CTA owns tiles of consecutive rows. The nonzeros of a tile are contiguous in CSR order,
 // so thread 0 streams each tile's values and column indices into a shared-memory stage with
 // two TMA bulk copies that complete on the stage's mbarrier, several tiles ahead of the
-// consumers (a ring of kStages stages). Each row is then summed from shared memory: with
-// TPR = 1 one thread runs the row's FMA chain in CSR order; with TPR = 2 or 4 (long rows)
-// each thread sums a contiguous quarter/half of the row and the partial sums are combined
-// in a fixed order. A tile whose nonzeros do not fit a stage, or that reaches the unaligned
-// tail of the arrays, is read straight from global memory instead. Every wait is bounded.
+// consumers (a ring of NST stages). Each row is then summed from shared memory by one
+// thread, as an FMA chain in CSR order. Matrices with long rows (mean > 8 nonzeros) use
+// fewer, larger stages. A tile whose nonzeros do not fit a stage, or that reaches the
+// unaligned tail of the arrays, is read straight from global memory instead. Every wait
+// is bounded.
 #include "common.cuh"
 #include "tma.cuh"
 
 namespace mpbjac {
 
-constexpr int kSpNT = 256;               // threads per CTA
-constexpr int kCap = 2048;               // nonzeros per stage
-constexpr int kStages = 3;
-constexpr int kStageBytes = kCap * 12;   // values (8 B) + column indices (4 B)
-constexpr int kSpSmem = 128 + kStages * kStageBytes;
+constexpr int kSpNT = 256;               // threads per CTA = rows per tile
+
+template <int CAP, int NST>
+struct SpGeo {
+    static constexpr int kCap = CAP;                // nonzeros per stage
+    static constexpr int kStages = NST;
+    static constexpr int kStageBytes = CAP * 12;    // values (8 B) + column indices (4 B)
+    static constexpr int kSmem = 128 + NST * kStageBytes;
+};
+using SpShort = SpGeo<2048, 3>;   // rows of up to ~8 nonzeros
+using SpLong = SpGeo<8192, 2>;    // longer rows (27-point stencils)
 
 enum SpmvKind {
     kSpY = 0,         // y = A x
@@ -34,13 +40,14 @@ struct StageMeta {
     int direct;   // 1: this tile is read from global memory
 };
 
-template <int TPR, int KIND>
+template <int CAP, int NST, int KIND>
 __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *__restrict__ rowptr,
                                                 const int32_t *__restrict__ colidx, const double *__restrict__ val,
                                                 const double *__restrict__ x, const double *__restrict__ b,
                                                 double *__restrict__ y, double *part, unsigned int *ticket,
                                                 double *out, SolverState *S) {
-    constexpr int RPT = kSpNT / TPR;     // rows per tile
+    constexpr int RPT = kSpNT;           // rows per tile
+    constexpr int kCap = CAP, kStages = NST, kStageBytes = CAP * 12;
     constexpr bool RES = KIND >= 10;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         }
     }
 
-    const int lrow = threadIdx.x / TPR, sub = threadIdx.x % TPR;
+    const int lrow = threadIdx.x;
     double acc1 = 0.0, acc2 = 0.0;   // dot / norm partial sums
     int it = 0;
     bool ok = true;
@@ -100,12 +107,6 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
             my_lo = __ldg(rowptr + row);
             my_hi = __ldg(rowptr + row + 1);
         }
-        if (TPR > 1) {     // this thread's contiguous share of the row
-            const int len = my_hi - my_lo, seg = (len + TPR - 1) / TPR;
-            const int a = min(my_lo + sub * seg, my_hi);
-            my_hi = min(a + seg, my_hi);
-            my_lo = a;
-        }
         ok = mbar_wait_bounded(&full[s], phase);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         const StageMeta m = meta[s];
@@ -114,32 +115,28 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         const int32_t *sc = reinterpret_cast<const int32_t *>(st + kCap * 8) - m.lo4;
         double acc = 0.0;
         if (!m.direct) {
-            int k = my_lo;
-            for (; k + 4 <= my_hi; k += 4) {
-                const double x0 = __ldg(x + sc[k]), x1 = __ldg(x + sc[k + 1]);
-                const double x2 = __ldg(x + sc[k + 2]), x3 = __ldg(x + sc[k + 3]);
-                acc = fma(sv[k], x0, acc);
-                acc = fma(sv[k + 1], x1, acc);
-                acc = fma(sv[k + 2], x2, acc);
-                acc = fma(sv[k + 3], x3, acc);
+            // gather up to 8 x entries of the row at once (predicated), then the FMA chain
+            for (int k0 = my_lo; k0 < my_hi; k0 += 8) {
+                double xv[8], vv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool in = k0 + j < my_hi;
+                    xv[j] = in ? __ldg(x + sc[k0 + j]) : 0.0;
+                    vv[j] = in ? sv[k0 + j] : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (k0 + j < my_hi) acc = fma(vv[j], xv[j], acc);
             }
-            for (; k < my_hi; ++k) acc = fma(sv[k], __ldg(x + sc[k]), acc);
         } else {
             for (int k = my_lo; k < my_hi; ++k) acc = fma(__ldg(val + k), __ldg(x + __ldg(colidx + k)), acc);
-        }
-        if (TPR > 1) {       // combine the row's partial sums: ((p0 + p1) + (p2 + p3))
-#pragma unroll
-            for (int o = 1; o < TPR; o <<= 1) {
-                const double other = __shfl_down_sync(0xffffffffu, acc, o);
-                if ((sub & (2 * o - 1)) == 0) acc += other;
-            }
         }
         __syncthreads();     // stage s consumed
         if (threadIdx.x == 0) {
             const int t2 = t + kStages * gridDim.x;
             if (t2 < ntiles) issue(t2, s);
         }
-        if (row < n && sub == 0) {
+        if (row < n) {
             if (RES) {
                 const double bi = b[row];
                 const double ri = bi - acc;
@@ -218,26 +215,27 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
 // ----------------------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------------------
-template <int TPR, int KIND>
+static bool long_rows(const bjac_csr &A) { return A.n > 0 && (double)A.nnz / A.n > 8.0; }
+
+template <typename G, int KIND>
 static int launch_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
                     unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
     // the shared-memory limit was raised by prepare_spmv (never during a graph capture)
     static int per_sm = 0;
     if (per_sm == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv<TPR, KIND>, kSpNT, kSpSmem) != cudaSuccess ||
-            v < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv<G::kCap, G::kStages, KIND>, kSpNT, G::kSmem) !=
+                cudaSuccess || v < 1)
             v = 1;
         per_sm = v;
     }
-    constexpr int RPT = kSpNT / TPR;
-    const int ntiles = (A.n + RPT - 1) / RPT;
+    const int ntiles = (A.n + kSpNT - 1) / kSpNT;
     int g = sm_count() * per_sm;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g > ntiles) g = ntiles;
     if (g < 1) g = 1;
-    k_spmv<TPR, KIND><<<g, kSpNT, kSpSmem, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket,
-                                                  out, S);
+    k_spmv<G::kCap, G::kStages, KIND><<<g, kSpNT, G::kSmem, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y,
+                                                                  part, ticket, out, S);
     MPB_CUDA(cudaGetLastError());
     return MPBJAC_OK;
 }
@@ -245,22 +243,18 @@ static int launch_t(const bjac_csr &A, const double *x, const double *b, double 
 template <int KIND>
 static int launch_kind(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
                        unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
-    const double avg = A.n > 0 ? (double)A.nnz / A.n : 0.0;
-    if (avg <= 8.0) return launch_t<1, KIND>(A, x, b, y, part, ticket, out, S, st);
-    if (avg <= 16.0) return launch_t<2, KIND>(A, x, b, y, part, ticket, out, S, st);
-    return launch_t<4, KIND>(A, x, b, y, part, ticket, out, S, st);
+    if (long_rows(A)) return launch_t<SpLong, KIND>(A, x, b, y, part, ticket, out, S, st);
+    return launch_t<SpShort, KIND>(A, x, b, y, part, ticket, out, S, st);
 }
 
 int prepare_spmv(const bjac_csr &A) {
     // raise the shared-memory limit of every instantiation this matrix will use
-    const double avg = A.n > 0 ? (double)A.nnz / A.n : 0.0;
-    const int tpr = avg <= 8.0 ? 1 : (avg <= 16.0 ? 2 : 4);
-#define MPB_ATTR(T, K) MPB_CUDA(cudaFuncSetAttribute(k_spmv<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem))
-#define MPB_ATTRS(T) MPB_ATTR(T, kSpY); MPB_ATTR(T, kSpYDot); MPB_ATTR(T, kSpPcg); \
-    MPB_ATTR(T, kResStandalone); MPB_ATTR(T, kResStart); MPB_ATTR(T, kResCheck)
-    if (tpr == 1) { MPB_ATTRS(1); }
-    else if (tpr == 2) { MPB_ATTRS(2); }
-    else { MPB_ATTRS(4); }
+#define MPB_ATTR(G, K) \
+    MPB_CUDA(cudaFuncSetAttribute(k_spmv<G::kCap, G::kStages, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem))
+#define MPB_ATTRS(G) MPB_ATTR(G, kSpY); MPB_ATTR(G, kSpYDot); MPB_ATTR(G, kSpPcg); \
+    MPB_ATTR(G, kResStandalone); MPB_ATTR(G, kResStart); MPB_ATTR(G, kResCheck)
+    if (long_rows(A)) { MPB_ATTRS(SpLong); }
+    else { MPB_ATTRS(SpShort); }
 #undef MPB_ATTRS
 #undef MPB_ATTR
     return MPBJAC_OK;
