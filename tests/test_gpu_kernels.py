@@ -175,7 +175,7 @@ def test_pack_and_apply_bitwise(B, fmt, layout):
             assert abs(host(rz)[0] - O.dot(r, zo)) <= 1e-13 * np.sum(np.abs(r * zo))
         outs.append(zd)
         h.close()
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
 
 
 @pytest.mark.parametrize("layout", ["bs32", "bs64", "uneven_voronoi"])
