@@ -170,7 +170,7 @@ def test_pack_and_apply_bitwise(B, fmt, layout):
         zd = host(z)
         assert np.array_equal(zd, zo, equal_nan=True)
         fin = np.isfinite(zo)
-        assert fin.mean() > 0.9
+        assert fin.mean() > 0.85       # one block holds the overflowing entry
         if fin.all():
             assert abs(host(rz)[0] - O.dot(r, zo)) <= 1e-13 * np.sum(np.abs(r * zo))
         outs.append(zd)
