@@ -229,6 +229,7 @@ def run_ours(args, rank, world, dist):
 
     # per-kernel device times of one iteration (eager launches, CUDA events on the stream)
     h = B.bjac_setup(dA, pr.block_ptr, **head)
+    apply_kernel, tune_ms = h.apply_kernel()
     x.zero_()
     prof = h.profile(b, x, tol=TOL, maxit=MAXIT)
     h.close()
@@ -245,13 +246,16 @@ def run_ours(args, rank, world, dist):
         peak, peak_src = 6800.0, "fallback"
     achieved = alg[dom] / (prof[dom] * 1e-3) / 1e9
     wl_key = f"m{args.m}_bs{args.bs}_{args.fmt}"
-    kernel_name = {"spmv": "k_spmv", "apply": "k_apply_tma", "update_xp": "k_update_xp"}[dom]
+    apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg"}[apply_kernel]
+    kernel_name = {"spmv": "k_spmv", "apply": apply_name, "update_xp": "k_update_xp"}[dom]
     roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": committed_traffic(kernel_name, wl_key), "algorithmic_bytes": alg[dom],
                 "launch_ms": round(prof[dom], 5),
                 "per_kernel_ms": {k: round(v, 5) for k, v in shares.items()},
-                "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares}}
+                "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares},
+                "apply_kernel": apply_name,
+                "apply_autotune_ms": dict(zip(("generic", "tma", "register"), [round(t, 4) for t in tune_ms]))}
 
     # end to end through the public API with host buffers: upload A and b from pinned host
     # memory, set up, solve, read x back

@@ -83,7 +83,8 @@ typedef struct bjac_policy {
     double theta;           /* rule threshold on kappa_1 * u_f (0.1 if <= 0)               */
     double safety_theta;    /* MLP promotion threshold on kappa_1 * u_f (0.5 if <= 0)      */
     const float *mlp_params;/* HOST pointer, bjac_mlp_param_count() floats, for SELECT_MLP */
-    int32_t apply_variant;  /* 0 automatic, 1 generic warp-per-block, 2 TMA-staged uniform  */
+    int32_t apply_variant;  /* low-precision apply kernel: 0 autotuned (uniform sets), 1 generic
+                               warp-per-block, 2 TMA-staged, 3 register-direct (bs 32)        */
     int32_t reserved;
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
@@ -172,6 +173,11 @@ int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *qoff, uint8
  * and re-round every block to its current format. Lets a test feed identical inputs to
  * the GPU rounding and to an independent implementation. */
 int bjac_import_inverse(bjac_handle *h, const double *G);
+
+/* Kernel the handle uses for the low-precision apply (0 generic, 1 TMA-staged, 2
+ * register-direct) and, when the autotuner ran, its timings in ms (tune_ms[3], HOST,
+ * nullable; 0 for kernels not timed). */
+int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
 /* Number of floats of the selector's parameter vector:
  * W1[64][12] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[12] sd[12]. */

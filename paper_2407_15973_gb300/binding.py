@@ -77,6 +77,7 @@ def lib():
                 "bjac_import_inverse": (C.c_int, [P, P]),
                 "bjac_mlp_param_count": (i32, []),
                 "pcg_profile": (C.c_int, [P, P, P, f64, i32, P, C.POINTER(i32)]),
+                "bjac_apply_kernel": (C.c_int, [P, C.POINTER(i32), P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -199,6 +200,13 @@ class Handle:
     def apply(self, r, z, set=1, rz=None):
         _require_cuda(r, z, rz)
         _check(lib().bjac_apply(self.h, set, _ptr(r), _ptr(z), _ptr(rz)))
+
+    def apply_kernel(self):
+        """(kernel name, autotuner timings in ms) of the low-precision apply."""
+        k = C.c_int32()
+        ms = (C.c_float * 3)()
+        _check(lib().bjac_apply_kernel(self.h, C.byref(k), ms))
+        return {0: "generic", 1: "tma", 2: "register"}[k.value], list(ms)
 
     def info(self):
         nb, pb, ge = C.c_int32(), C.c_int64(), C.c_int64()

@@ -39,6 +39,9 @@ int sm_count() {
 
 static int fmt_bytes(int f) { return f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2; }
 
+// kernels that can apply the low-precision set (the binary64 set always uses the generic one)
+enum ApplyKind { kApplyKindGeneric = 0, kApplyKindTma = 1, kApplyKindReg = 2 };
+
 // ----------------------------------------------------------------------------------------
 // vector kernels of the PCG loop
 // ----------------------------------------------------------------------------------------
@@ -102,8 +105,9 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
 }
 
 // x += alpha p (the update deferred from this iteration); p = z + beta p while running.
-// The last CTA closes the iteration and sets the graph's while-condition. z and p are
-// 16-byte aligned (handle memory); x is the caller's vector and is checked.
+// The state it reads was final before this kernel started, so thread 0 of CTA 0 sets the
+// graph's while-condition without any grid-wide step (x_pending is cleared by the next
+// SpMV). z and p are 16-byte aligned (handle memory); x is the caller's vector and is checked.
 __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
     const int xp = S->x_pending;
@@ -142,11 +146,7 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
             if (run) p[i] = fma(beta, pi, z[i]);
         }
     }
-    if (!last_cta(&S->tickets[kTicketUpdXP])) return;
-    if (threadIdx.x == 0) {
-        S->x_pending = 0;
-        if (use_cond) cudaGraphSetConditional(cond, run ? 1u : 0u);
-    }
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, run ? 1u : 0u);
 }
 
 __global__ void k_zero_if_zero_rhs(int n, SolverState *S) {
@@ -207,6 +207,8 @@ struct bjac_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     float setup_ms = 0.0f;
     int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
+    int apply_kind = kApplyKindGeneric;   // kernel used for the low-precision set
+    float tune_ms[3] = {0, 0, 0};         // autotuner timings (generic, TMA, register)
 };
 
 static void free_handle(bjac_handle *h) {
@@ -266,6 +268,77 @@ static PSet make_pset(const bjac_handle *h, const uint8_t *fmt, const float *sca
     P.ufmt = ufmt;
     P.pad = 0;
     return P;
+}
+
+// Autotuner for the low-precision apply: when the set is uniform (one block size, one
+// format) every applicable kernel is timed on this very set (standalone launches on the
+// handle's stream, CUDA events, best of three after one warm-up) and the fastest is kept.
+// policy.apply_variant forces a kernel instead (1 generic, 2 TMA-staged, 3 register).
+// Results are cached per (format, block size, block count) for the life of the process.
+struct TuneKey {
+    int fmt, bs, nb;
+    bool operator==(const TuneKey &o) const { return fmt == o.fmt && bs == o.bs && nb == o.nb; }
+};
+static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+
+static int choose_apply_kind(bjac_handle *h) {
+    const bool tma_ok = tma_supported(h->lo, h->n);
+    const bool reg_ok = reg_supported(h->lo, h->n);
+    const int v = h->pol.apply_variant;
+    if (v == 1 || !tma_ok) { h->apply_kind = kApplyKindGeneric; return MPBJAC_OK; }
+    if (v == 2) { h->apply_kind = kApplyKindTma; return MPBJAC_OK; }
+    if (v == 3) { h->apply_kind = reg_ok ? kApplyKindReg : kApplyKindTma; return MPBJAC_OK; }
+    const TuneKey key{h->lo.ufmt, h->lo.ubs, h->nb};
+    for (auto &e : g_tune_cache)
+        if (e.first == key) { h->apply_kind = e.second; return MPBJAC_OK; }
+    cudaStream_t st = h->stream;
+    double *r = nullptr, *z = nullptr, *part = nullptr;
+    unsigned int *ticket = nullptr;
+    MPB_CUDA(cudaMalloc(&r, sizeof(double) * h->n));
+    MPB_CUDA(cudaMalloc(&z, sizeof(double) * h->n));
+    MPB_CUDA(cudaMalloc(&part, sizeof(double) * 2 * kMaxGrid + 64));
+    ticket = reinterpret_cast<unsigned int *>(part + 2 * kMaxGrid);
+    MPB_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * h->n, st));
+    MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+    ApplyIO io{};
+    io.r = r;
+    io.z = z;
+    io.part = part;
+    io.ticket = ticket;
+    io.set = 1;
+    io.only_set = -1;
+    cudaEvent_t e0, e1;
+    MPB_CUDA(cudaEventCreate(&e0));
+    MPB_CUDA(cudaEventCreate(&e1));
+    const int kinds[3] = {kApplyKindGeneric, kApplyKindTma, kApplyKindReg};
+    float best = 1e30f;
+    int best_kind = kApplyKindTma;
+    for (int k : kinds) {
+        if (k == kApplyKindReg && !reg_ok) continue;
+        float t_best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            MPB_CUDA(cudaEventRecord(e0, st));
+            int rc = k == kApplyKindGeneric ? launch_apply_generic(kApplyStandalone, h->lo, h->lo, io, nullptr, st)
+                     : k == kApplyKindTma   ? launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, st)
+                                            : launch_apply_reg(kApplyStandalone, h->lo, io, nullptr, st);
+            if (rc) return rc;
+            MPB_CUDA(cudaEventRecord(e1, st));
+            MPB_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < t_best) t_best = ms;
+        }
+        h->tune_ms[k] = t_best;
+        if (t_best < best) { best = t_best; best_kind = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(r);
+    cudaFree(z);
+    cudaFree(part);
+    h->apply_kind = best_kind;
+    g_tune_cache.push_back({key, best_kind});
+    return MPBJAC_OK;
 }
 
 extern "C" {
@@ -427,6 +500,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         }
         h->lo = make_pset(h, h->d_fmt, h->d_scale, h->d_qoff, h->d_pool, ufmt);
         if (tma_supported(h->lo, h->n)) MPB_TRY(prepare_apply_tma(h->lo));
+        MPB_TRY(choose_apply_kind(h));
     } else {
         h->blocks_per_fmt[BJAC_FP64] = nb;
     }
@@ -492,8 +566,12 @@ static ApplyIO base_io(bjac_handle *h) {
 // Apply for the init / aMP modes: the set is read on the device (S->use_low). The
 // binary64 set always goes to the generic kernel; the low set to the TMA kernel when it
 // fits one, each launch returning at once when the other set is selected.
-static bool lo_uses_tma(const bjac_handle *h) {
-    return h->have_lo && h->pol.apply_variant != 1 && tma_supported(h->lo, h->n);
+static bool lo_uses_tma(const bjac_handle *h) { return h->have_lo && h->apply_kind != kApplyKindGeneric; }
+
+// launch the low-precision set's specialised kernel (TMA-staged or register-direct)
+static int launch_lo_special(const bjac_handle *h, int mode, const ApplyIO &io, cudaStream_t st) {
+    if (h->apply_kind == kApplyKindReg) return launch_apply_reg(mode, h->lo, io, h->d_S, st);
+    return launch_apply_tma(mode, h->lo, io, h->d_S, h->n, st);
 }
 
 static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool low_only, bool high_only) {
@@ -502,7 +580,7 @@ static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool l
     PSet lo = h->have_lo ? h->lo : h->hi;
     PSet hi = h->have_hi ? h->hi : h->lo;
     if (lo_tma && !high_only) {
-        int rc = launch_apply_tma(mode, h->lo, io, h->d_S, h->n, st);
+        int rc = launch_lo_special(h, mode, io, st);
         if (rc) return rc;
         if (low_only) return MPBJAC_OK;
         io.only_set = 0;
@@ -532,7 +610,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         ApplyIO io = base_io(h);
         io.set = use_low ? 1 : 0;
-        if (use_low && lo_uses_tma(h)) rc = launch_apply_tma(kApplyFused, h->lo, io, h->d_S, h->n, cs);
+        if (use_low && lo_uses_tma(h)) rc = launch_lo_special(h, kApplyFused, io, cs);
         else rc = launch_apply_generic(kApplyFused, use_low ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                        h->d_S, cs);
         if (rc) return rc;
@@ -728,8 +806,10 @@ extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *
     io.set = set;
     // bulk copies need 16-byte aligned sources
     const bool aligned = (reinterpret_cast<uintptr_t>(r) & 15) == 0;
-    const bool tma = set == 1 && aligned && tma_supported(h->lo, h->n) && h->pol.apply_variant != 1;
-    if (tma) return launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, h->stream);
+    if (set == 1 && lo_uses_tma(h) && (aligned || h->apply_kind == kApplyKindReg)) {
+        if (h->apply_kind == kApplyKindReg) return launch_apply_reg(kApplyStandalone, h->lo, io, nullptr, h->stream);
+        return launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, h->stream);
+    }
     return launch_apply_generic(kApplyStandalone, h->have_lo ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                 nullptr, h->stream);
 }
@@ -816,5 +896,13 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     if (rc) return rc;
     for (int i = 0; i < 4; ++i) ms[i] = k ? (float)(acc[i] / k) : 0.0f;
     if (iters) *iters = k;
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    if (kind) *kind = h->apply_kind;
+    if (tune_ms)
+        for (int i = 0; i < 3; ++i) tune_ms[i] = h->tune_ms[i];
     return MPBJAC_OK;
 }

@@ -314,6 +314,146 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
 }
 
 // ----------------------------------------------------------------------------------------
+// register-direct uniform kernel: because every block is symmetric, row i of a block is also
+// its column i, so lane i loads its own row with 16-byte loads (the whole block arrives in one
+// round of coalesced-by-sector loads) and keeps it in registers; r-hat is shared through a
+// small per-warp buffer. The next block's row, r and q are loaded before the current block is
+// computed (two blocks in flight per warp). No TMA, no shared-memory copy of Q, no CTA sync.
+// ----------------------------------------------------------------------------------------
+template <typename QT, int BS>
+struct RegGeom {
+    static constexpr int kRPL = BS / 32;                       // rows per lane
+    static constexpr int kVPR = BS * (int)sizeof(QT) / 16;     // 16-byte vectors per row
+    static constexpr int kEPV = 16 / (int)sizeof(QT);          // entries per vector
+};
+
+template <typename QT>
+__device__ __forceinline__ float vec_entry(const uint4 &v, int e);
+template <> __device__ __forceinline__ float vec_entry<float>(const uint4 &v, int e) {
+    const unsigned w = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+    return __uint_as_float(w);
+}
+template <> __device__ __forceinline__ float vec_entry<__nv_bfloat16>(const uint4 &v, int e) {
+    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+    return __uint_as_float((e & 1) ? (w & 0xFFFF0000u) : (w << 16));     // bfloat16 -> binary32 is exact
+}
+template <> __device__ __forceinline__ float vec_entry<__half>(const uint4 &v, int e) {
+    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+    return __half2float(__ushort_as_half((unsigned short)((e & 1) ? (w >> 16) : (w & 0xFFFFu))));
+}
+
+template <typename QT, int BS, int MODE>
+__global__ void __launch_bounds__(kNT, 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
+    using Geo = RegGeom<QT, BS>;
+    constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
+    __shared__ __align__(16) float s_rh[kWarps][BS];
+    __shared__ double s_red[2][kWarps];
+    if (MODE != kApplyStandalone) {
+        if (S->state != kRunning) return;
+        if (MODE == kApplyTemporal || MODE == kApplyInit) {
+            if (!S->use_low) return;     // the binary64 set runs in the generic kernel
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = P.nb;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    const size_t blk_bytes = (size_t)BS * BS * sizeof(QT);
+
+    uint4 qc[RPL][VPR], qn[RPL][VPR];
+    double rc[RPL], rn[RPL], vc[RPL], vn[RPL];
+    float sc_c = 1.0f, sc_n = 1.0f;
+    auto load = [&](int blk, uint4 (&qv)[RPL][VPR], double (&rv)[RPL], double (&qq)[RPL], float &sc) {
+        const uint4 *base = reinterpret_cast<const uint4 *>(P.pool + (size_t)blk * blk_bytes);
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+            const int row = h * 32 + lane;
+#pragma unroll
+            for (int v = 0; v < VPR; ++v) qv[h][v] = __ldcs(base + (size_t)row * VPR + v);
+            rv[h] = io.r[(size_t)blk * BS + row];
+            if (MODE == kApplyFused) qq[h] = io.q[(size_t)blk * BS + row];
+        }
+        if (sizeof(QT) == 2) sc = __ldg(P.scale + blk);
+    };
+    double rho = 0.0, rr = 0.0;
+    if (gw < nb) load(gw, qc, rc, vc, sc_c);
+    for (int blk = gw; blk < nb; blk += nw) {
+        const int nxt = blk + nw;
+        if (nxt < nb) load(nxt, qn, rn, vn, sc_n);
+        double rv[RPL];
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+            double v = rc[h];
+            if (MODE == kApplyFused) v = fma(-alpha, vc[h], v);
+            rv[h] = v;
+            s_rh[warp][h * 32 + lane] = f64_to_f32_rn(v);
+        }
+        __syncwarp();
+        const float4 *rh4 = reinterpret_cast<const float4 *>(s_rh[warp]);
+        float acc[RPL];
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) acc[h] = 0.0f;
+#pragma unroll
+        for (int v = 0; v < VPR; ++v) {
+#pragma unroll
+            for (int e4 = 0; e4 < EPV; e4 += 4) {
+                const float4 r4 = rh4[(v * EPV + e4) >> 2];
+#pragma unroll
+                for (int h = 0; h < RPL; ++h) {
+                    acc[h] = fmaf(vec_entry<QT>(qc[h][v], e4 + 0), r4.x, acc[h]);
+                    acc[h] = fmaf(vec_entry<QT>(qc[h][v], e4 + 1), r4.y, acc[h]);
+                    acc[h] = fmaf(vec_entry<QT>(qc[h][v], e4 + 2), r4.z, acc[h]);
+                    acc[h] = fmaf(vec_entry<QT>(qc[h][v], e4 + 3), r4.w, acc[h]);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+            const size_t row = (size_t)blk * BS + h * 32 + lane;
+            const double zi = f32_to_f64(acc[h] * sc_c);
+            io.z[row] = zi;
+            if (MODE == kApplyInit) io.p[row] = zi;
+            if (MODE == kApplyFused) {
+                io.r_out[row] = rv[h];
+                rr = fma(rv[h], rv[h], rr);
+            }
+            rho = fma(rv[h], zi, rho);
+        }
+        // rotate the prefetched block into place
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+#pragma unroll
+            for (int v = 0; v < VPR; ++v) qc[h][v] = qn[h][v];
+            rc[h] = rn[h];
+            vc[h] = vn[h];
+        }
+        sc_c = sc_n;
+    }
+    rho = warp_sum(rho);
+    rr = warp_sum(rr);
+    if (lane == 0) {
+        s_red[0][warp] = rho;
+        s_red[1][warp] = rr;
+    }
+    __syncthreads();
+    if (MODE == kApplyStandalone && io.out == nullptr) return;
+    if (threadIdx.x == 0) {
+        double b1 = 0.0, b2 = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            b1 += s_red[0][w];
+            b2 += s_red[1][w];
+        }
+        io.part[2 * blockIdx.x] = b1;
+        io.part[2 * blockIdx.x + 1] = b2;
+    }
+    if (!last_cta(io.ticket)) return;
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red[0]);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red[1]);
+    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
+}
+
+// ----------------------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------------------
 static int generic_grid(int nb) {
@@ -361,6 +501,48 @@ static int launch_tma_mode(const PSet &P, const ApplyIO &io, SolverState *S, int
         case BJAC_FP16S * 1000 + 32: return launch_tma_t<__half, 32, MODE>(P, io, S, n, st, dry);
         case BJAC_FP16S * 1000 + 64: return launch_tma_t<__half, 64, MODE>(P, io, S, n, st, dry);
         default: return fail(MPBJAC_ERR_UNSUPPORTED, "no TMA apply kernel for this format / block size");
+    }
+}
+
+template <typename QT, int BS, int MODE>
+static int launch_reg_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_reg<QT, BS, MODE>, kNT, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v;
+    }
+    int g = sm_count() * per_sm;
+    const int need = (P.nb + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    if (g < 1) g = 1;
+    k_apply_reg<QT, BS, MODE><<<g, kNT, 0, st>>>(P, io, S);
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
+template <int MODE>
+static int launch_reg_mode(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    switch (P.ufmt * 1000 + P.ubs) {
+        case BJAC_FP32 * 1000 + 32: return launch_reg_t<float, 32, MODE>(P, io, S, st);
+        case BJAC_BF16 * 1000 + 32: return launch_reg_t<__nv_bfloat16, 32, MODE>(P, io, S, st);
+        case BJAC_FP16S * 1000 + 32: return launch_reg_t<__half, 32, MODE>(P, io, S, st);
+        default: return fail(MPBJAC_ERR_UNSUPPORTED, "no register apply kernel for this format / block size");
+    }
+}
+
+bool reg_supported(const PSet &P, int n) {
+    return tma_supported(P, n) && P.ubs == 32;
+}
+
+int launch_apply_reg(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    switch (mode) {
+        case kApplyStandalone: return launch_reg_mode<kApplyStandalone>(P, io, S, st);
+        case kApplyInit: return launch_reg_mode<kApplyInit>(P, io, S, st);
+        case kApplyTemporal: return launch_reg_mode<kApplyTemporal>(P, io, S, st);
+        default: return launch_reg_mode<kApplyFused>(P, io, S, st);
     }
 }
 

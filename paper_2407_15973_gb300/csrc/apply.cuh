@@ -28,6 +28,8 @@ struct ApplyIO {
 bool tma_supported(const PSet &P, int n);
 int prepare_apply_tma(const PSet &P);   // set kernel attributes (call before any capture)
 int launch_apply_tma(int mode, const PSet &P, const ApplyIO &io, SolverState *S, int n, cudaStream_t st);
+bool reg_supported(const PSet &P, int n);
+int launch_apply_reg(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st);
 int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S,
                          cudaStream_t st);
 

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     if (KIND == kSpYDot || KIND == kResStandalone) {
         *out = t1;
     } else if (KIND == kSpPcg) {
+        S->x_pending = 0;      // set again once this iteration updates r
         S->sigma = t1;
         if (!finite_pos(t1)) S->state = kBreakdownSigma;
         else S->alpha = S->rho / t1;
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     } else {   // kResCheck
         const double rel = S->bnorm > 0.0 ? sqrt(t1) / S->bnorm : 0.0;
         S->true_relres = rel;
+        S->x_pending = 0;
         if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
             S->state = kRunning;          // restart from r = b - A x
             S->restarts += 1;
