@@ -179,6 +179,12 @@ int bjac_import_inverse(bjac_handle *h, const double *G);
  * nullable; 0 for kernels not timed). */
 int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
+/* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):
+ * 0 = timed once per matrix shape at setup and the faster kept (default), 1 = TMA-staged
+ * CTA tiles, 2 = warp-cooperative. Rows longer on average always use the TMA kernel with
+ * large stages. Returns the previous setting, or INVALID_ARG. Not thread-safe. */
+int bjac_spmv_kernel(int32_t variant);
+
 /* Number of floats of the selector's parameter vector:
  * W1[64][12] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[12] sd[12]. */
 int32_t bjac_mlp_param_count(void);

@@ -78,6 +78,7 @@ def lib():
                 "bjac_mlp_param_count": (i32, []),
                 "pcg_profile": (C.c_int, [P, P, P, f64, i32, P, C.POINTER(i32)]),
                 "bjac_apply_kernel": (C.c_int, [P, C.POINTER(i32), P]),
+                "bjac_spmv_kernel": (C.c_int, [i32]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -124,6 +125,11 @@ def bjac_spmv(A: DeviceCSR, x, y, xy=None, stream=None):
     """y = A x (and xy[0] = x . y when a one-element float64 CUDA tensor xy is given)."""
     _require_cuda(x, y, xy)
     _check(lib().bjac_spmv(C.byref(A.c), _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
+
+
+def bjac_spmv_kernel(variant: int) -> int:
+    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative. Returns the old value."""
+    return _check(lib().bjac_spmv_kernel(int(variant)), allow_positive=True)
 
 
 def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):

@@ -12,6 +12,8 @@
 #include "common.cuh"
 #include "tma.cuh"
 
+#include <vector>
+
 namespace mpbjac {
 
 constexpr int kSpNT = 256;               // threads per CTA = rows per tile
@@ -39,6 +41,47 @@ struct StageMeta {
     int lo4;      // first staged nonzero (multiple of 4)
     int direct;   // 1: this tile is read from global memory
 };
+
+template <int KIND>
+__device__ __forceinline__ void spmv_finish(double t1, double t2, double *out, SolverState *S) {
+    if (KIND == kSpYDot || KIND == kResStandalone) {
+        *out = t1;
+    } else if (KIND == kSpPcg) {
+        S->x_pending = 0;      // set again once this iteration updates r
+        S->sigma = t1;
+        if (!finite_pos(t1)) S->state = kBreakdownSigma;
+        else S->alpha = S->rho / t1;
+    } else if (KIND == kResStart) {
+        const double bnorm = sqrt(t2);
+        S->bnorm = bnorm;
+        S->x_pending = 0;
+        if (bnorm == 0.0) {
+            S->relres = 0.0;
+            S->true_relres = 0.0;
+            S->state = kConverged;      // x is zeroed by the host
+            return;
+        }
+        const double rel = sqrt(t1) / bnorm;
+        S->relres = rel;
+        S->true_relres = rel;
+        if (S->hist) S->hist[S->iter] = rel;
+        if (!(rel < 1.0e308)) S->state = kBreakdown;
+        else if (rel <= S->tol) S->state = kConverged;
+        else if (S->iter >= S->maxit) S->state = kMaxit;
+        else S->state = kRunning;
+        S->use_low = choose_low(S, rel);
+    } else {   // kResCheck
+        const double rel = S->bnorm > 0.0 ? sqrt(t1) / S->bnorm : 0.0;
+        S->true_relres = rel;
+        S->x_pending = 0;
+        if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
+            S->state = kRunning;          // restart from r = b - A x
+            S->restarts += 1;
+            S->relres = rel;
+            S->use_low = choose_low(S, rel);
+        }
+    }
+}
 
 template <int CAP, int NST, int KIND>
 __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *__restrict__ rowptr,
@@ -174,50 +217,174 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     if (!last_cta(ticket)) return;
     const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
     const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
-    if (threadIdx.x != 0) return;
-    if (KIND == kSpYDot || KIND == kResStandalone) {
-        *out = t1;
-    } else if (KIND == kSpPcg) {
-        S->x_pending = 0;      // set again once this iteration updates r
-        S->sigma = t1;
-        if (!finite_pos(t1)) S->state = kBreakdownSigma;
-        else S->alpha = S->rho / t1;
-    } else if (KIND == kResStart) {
-        const double bnorm = sqrt(t2);
-        S->bnorm = bnorm;
-        S->x_pending = 0;
-        if (bnorm == 0.0) {
-            S->relres = 0.0;
-            S->true_relres = 0.0;
-            S->state = kConverged;      // x is zeroed by the host
-            return;
+    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+}
+
+// ----------------------------------------------------------------------------------------
+// warp-cooperative variant: a warp owns 32 consecutive rows. Their nonzeros are loaded with
+// coalesced loads (lane k takes entries c0 + k + 32 m) into registers, parked in a
+// warp-private shared buffer, and each lane then runs its own row's FMA chain in CSR order
+// from that buffer. The next chunk is loaded into registers before the current chunk is
+// summed, so every warp keeps a chunk in flight; there is no CTA-wide barrier at all.
+// ----------------------------------------------------------------------------------------
+template <int K, int KIND>
+__global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ colidx,
+                                                     const double *__restrict__ val, const double *__restrict__ x,
+                                                     const double *__restrict__ b, double *__restrict__ y,
+                                                     double *part, unsigned int *ticket, double *out, SolverState *S) {
+    constexpr int CH = 32 * K;          // nonzeros per chunk
+    constexpr int NW = kSpNT / 32;
+    constexpr bool RES = KIND >= 10;
+    __shared__ double s_v[NW][CH];
+    __shared__ int32_t s_c[NW][CH];
+    __shared__ double red[2][NW];
+    if (KIND == kSpPcg && S->state != kRunning) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (n + 31) >> 5;
+    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
+    double *sv = s_v[warp];
+    int32_t *sc = s_c[warp];
+    double acc1 = 0.0, acc2 = 0.0;
+
+    double pv[K];
+    int32_t pc[K];
+    auto fetch = [&](int c0, int hi) {
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            const int k = c0 + lane + 32 * m;
+            const bool in = k < hi;
+            pv[m] = in ? __ldcs(val + k) : 0.0;
+            pc[m] = in ? __ldcs(colidx + k) : 0;
         }
-        const double rel = sqrt(t1) / bnorm;
-        S->relres = rel;
-        S->true_relres = rel;
-        if (S->hist) S->hist[S->iter] = rel;
-        if (!(rel < 1.0e308)) S->state = kBreakdown;
-        else if (rel <= S->tol) S->state = kConverged;
-        else if (S->iter >= S->maxit) S->state = kMaxit;
-        else S->state = kRunning;
-        S->use_low = choose_low(S, rel);
-    } else {   // kResCheck
-        const double rel = S->bnorm > 0.0 ? sqrt(t1) / S->bnorm : 0.0;
-        S->true_relres = rel;
-        S->x_pending = 0;
-        if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
-            S->state = kRunning;          // restart from r = b - A x
-            S->restarts += 1;
-            S->relres = rel;
-            S->use_low = choose_low(S, rel);
+    };
+    // first chunk of the first tile
+    int t = gw;
+    int row = (t << 5) + lane;
+    int my_lo = 0, my_hi = 0, lo = 0, hi = 0;
+    if (t < ntiles) {
+        const int rr = min(row, n);
+        my_lo = __ldg(rowptr + rr);
+        my_hi = row < n ? __ldg(rowptr + row + 1) : my_lo;
+        lo = __shfl_sync(0xffffffffu, my_lo, 0);
+        hi = __shfl_sync(0xffffffffu, my_hi, 31);
+        fetch(lo, hi);
+    }
+    while (t < ntiles) {
+        double acc = 0.0;
+        for (int c0 = lo; c0 < hi; c0 += CH) {
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+                sv[lane + 32 * m] = pv[m];
+                sc[lane + 32 * m] = pc[m];
+            }
+            __syncwarp();
+            // prefetch: the rest of this tile, else the first chunk of the next tile
+            const int c1 = c0 + CH;
+            int nt = t, nrow = row, nlo = my_lo, nhi = my_hi, tlo = lo, thi = hi;
+            if (c1 < hi) {
+                fetch(c1, hi);
+            } else {
+                nt = t + nw;
+                if (nt < ntiles) {
+                    nrow = (nt << 5) + lane;
+                    const int rr = min(nrow, n);
+                    nlo = __ldg(rowptr + rr);
+                    nhi = nrow < n ? __ldg(rowptr + nrow + 1) : nlo;
+                    tlo = __shfl_sync(0xffffffffu, nlo, 0);
+                    thi = __shfl_sync(0xffffffffu, nhi, 31);
+                    fetch(tlo, thi);
+                }
+            }
+            const int a = max(my_lo, c0), e = min(my_hi, c1);
+            for (int k0 = a; k0 < e; k0 += 8) {
+                double xv[8], vv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool in = k0 + j < e;
+                    xv[j] = in ? __ldg(x + sc[k0 + j - c0]) : 0.0;
+                    vv[j] = in ? sv[k0 + j - c0] : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (k0 + j < e) acc = fma(vv[j], xv[j], acc);
+            }
+            if (c1 >= hi) {   // tile finished: emit the row, move to the next tile
+                if (row < n) {
+                    if (RES) {
+                        const double bi = b[row];
+                        const double ri = bi - acc;
+                        y[row] = ri;
+                        acc1 = fma(ri, ri, acc1);
+                        acc2 = fma(bi, bi, acc2);
+                    } else {
+                        y[row] = acc;
+                        if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+                    }
+                }
+                t = nt; row = nrow; my_lo = nlo; my_hi = nhi; lo = tlo; hi = thi;
+                break;
+            }
+        }
+        if (lo >= hi && t < ntiles) {   // a tile with no nonzeros
+            if (row < n) {
+                if (RES) {
+                    const double bi = b[row];
+                    y[row] = bi;
+                    acc1 = fma(bi, bi, acc1);
+                    acc2 = fma(bi, bi, acc2);
+                } else {
+                    y[row] = 0.0;
+                }
+            }
+            t += nw;
+            if (t < ntiles) {
+                row = (t << 5) + lane;
+                const int rr = min(row, n);
+                my_lo = __ldg(rowptr + rr);
+                my_hi = row < n ? __ldg(rowptr + row + 1) : my_lo;
+                lo = __shfl_sync(0xffffffffu, my_lo, 0);
+                hi = __shfl_sync(0xffffffffu, my_hi, 31);
+                fetch(lo, hi);
+            }
         }
     }
+    if (KIND == kSpY) return;
+    const double b1 = block_sum<kSpNT>(acc1, red[0]);
+    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = b1;
+        part[2 * blockIdx.x + 1] = b2;
+    }
+    if (!last_cta(ticket)) return;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
 }
 
 // ----------------------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------------------
 static bool long_rows(const bjac_csr &A) { return A.n > 0 && (double)A.nnz / A.n > 8.0; }
+
+// SpMV kernel choice per matrix shape, made once by timing (see prepare_spmv)
+enum SpmvVariant { kSpVarTma = 0, kSpVarWarp = 1 };
+struct SpTune {
+    int n, nnz, variant;
+};
+static std::vector<SpTune> g_sp_tune;
+
+static int g_sp_force = 0;   // 0 timed choice, 1 TMA-staged, 2 warp-cooperative
+
+static int spmv_variant(const bjac_csr &A) {
+    if (long_rows(A)) return kSpVarTma;
+    if (g_sp_force == 1) return kSpVarTma;
+    if (g_sp_force == 2) return kSpVarWarp;
+    for (const SpTune &t : g_sp_tune)
+        if (t.n == A.n && t.nnz == A.nnz) return t.variant;
+    return kSpVarWarp;
+}
 
 template <typename G, int KIND>
 static int launch_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
@@ -243,24 +410,90 @@ static int launch_t(const bjac_csr &A, const double *x, const double *b, double 
 }
 
 template <int KIND>
+static int launch_warp_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
+                         unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv_warp<8, KIND>, kSpNT, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v;
+    }
+    const int ntiles = (A.n + 31) / 32;
+    int g = sm_count() * per_sm;
+    if (g > kMaxGrid) g = kMaxGrid;
+    const int need = (ntiles + kSpNT / 32 - 1) / (kSpNT / 32);
+    if (g > need) g = need;
+    if (g < 1) g = 1;
+    k_spmv_warp<8, KIND><<<g, kSpNT, 0, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket, out, S);
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
+template <int KIND>
 static int launch_kind(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
                        unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
     if (long_rows(A)) return launch_t<SpLong, KIND>(A, x, b, y, part, ticket, out, S, st);
+    if (spmv_variant(A) == kSpVarWarp) return launch_warp_t<KIND>(A, x, b, y, part, ticket, out, S, st);
     return launch_t<SpShort, KIND>(A, x, b, y, part, ticket, out, S, st);
 }
 
+// Raise the shared-memory limit of every instantiation this matrix will use and, for short
+// rows, time the TMA-staged and the warp-cooperative kernels once on A (y = A x with x = 0,
+// best of three after a warm-up) and remember the faster for this (n, nnz).
 int prepare_spmv(const bjac_csr &A) {
-    // raise the shared-memory limit of every instantiation this matrix will use
 #define MPB_ATTR(G, K) \
     MPB_CUDA(cudaFuncSetAttribute(k_spmv<G::kCap, G::kStages, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem))
 #define MPB_ATTRS(G) MPB_ATTR(G, kSpY); MPB_ATTR(G, kSpYDot); MPB_ATTR(G, kSpPcg); \
     MPB_ATTR(G, kResStandalone); MPB_ATTR(G, kResStart); MPB_ATTR(G, kResCheck)
-    if (long_rows(A)) { MPB_ATTRS(SpLong); }
-    else { MPB_ATTRS(SpShort); }
+    if (long_rows(A)) {
+        MPB_ATTRS(SpLong);
+        return MPBJAC_OK;
+    }
+    MPB_ATTRS(SpShort);
 #undef MPB_ATTRS
 #undef MPB_ATTR
+    for (const SpTune &t : g_sp_tune)
+        if (t.n == A.n && t.nnz == A.nnz) return MPBJAC_OK;
+    double *x = nullptr, *y = nullptr;
+    MPB_CUDA(cudaMalloc(&x, sizeof(double) * A.n));
+    MPB_CUDA(cudaMalloc(&y, sizeof(double) * A.n));
+    MPB_CUDA(cudaMemset(x, 0, sizeof(double) * A.n));
+    cudaEvent_t e0, e1;
+    MPB_CUDA(cudaEventCreate(&e0));
+    MPB_CUDA(cudaEventCreate(&e1));
+    float best[2] = {1e30f, 1e30f};
+    for (int v = 0; v < 2; ++v) {
+        for (int rep = 0; rep < 4; ++rep) {
+            MPB_CUDA(cudaEventRecord(e0, 0));
+            int rc = v == kSpVarTma ? launch_t<SpShort, kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0)
+                                    : launch_warp_t<kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0);
+            if (rc) return rc;
+            MPB_CUDA(cudaEventRecord(e1, 0));
+            MPB_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best[v]) best[v] = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    g_sp_tune.push_back({A.n, A.nnz, best[kSpVarWarp] <= best[kSpVarTma] ? kSpVarWarp : kSpVarTma});
     return MPBJAC_OK;
 }
+
+}  // namespace mpbjac
+
+extern "C" int bjac_spmv_kernel(int32_t variant) {
+    if (variant < 0 || variant > 2) return mpbjac::fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    const int old = mpbjac::g_sp_force;
+    mpbjac::g_sp_force = variant;
+    return old;
+}
+
+namespace mpbjac {
 
 int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
                 double *dot_out, SolverState *S, int mode, cudaStream_t st) {

@@ -57,18 +57,27 @@ def test_spmv_integer_exact(B):
     assert host(xy)[0] == float(np.dot(x, ref))    # integers below 2^53: exact in any order
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("case", list(SPMV_CASES))
-def test_spmv_parity(B, case):
+def test_spmv_parity(B, case, variant):
     A = SPMV_CASES[case]()
     x = PB.solution(A.n, 17)
     dA = B.DeviceCSR(A)
     y = torch.empty(A.n, dtype=torch.float64, device="cuda")
     xy = torch.zeros(1, dtype=torch.float64, device="cuda")
-    B.bjac_spmv(dA, cuda(x), y, xy)
-    ref = O.spmv(A, x)
-    got = host(y)
+    old = B.bjac_spmv_kernel(variant)
+    try:
+        B.bjac_spmv(dA, cuda(x), y, xy)
+        ref = O.spmv(A, x)
+        got = host(y)
+        r = torch.empty(A.n, dtype=torch.float64, device="cuda")
+        B.bjac_residual(dA, cuda(ref), cuda(x), r)
+        res = host(r)
+    finally:
+        B.bjac_spmv_kernel(old)
     assert np.max(np.abs(got - ref)) <= spmv_tol(A, x)
     assert abs(host(xy)[0] - O.dot(x, ref)) <= 1e-14 * np.sum(np.abs(x * ref)) + 1e-300
+    assert np.max(np.abs(res)) <= spmv_tol(A, x)
 
 
 def test_residual_parity(B):
