@@ -247,6 +247,16 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     int32_t *sc = s_c[warp];
     double acc1 = 0.0, acc2 = 0.0;
 
+    // row range of this lane's row in tile tt (empty past the last row)
+    auto rows_of = [&](int tt, int &lo_r, int &hi_r) {
+        const int r = (tt << 5) + lane;
+        if (tt < ntiles) {
+            lo_r = __ldg(rowptr + min(r, n));
+            hi_r = r < n ? __ldg(rowptr + r + 1) : lo_r;
+        } else {
+            lo_r = hi_r = 0;
+        }
+    };
     double pv[K];
     int32_t pc[K];
     auto fetch = [&](int c0, int hi) {
@@ -258,21 +268,23 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
             pc[m] = in ? __ldcs(colidx + k) : 0;
         }
     };
-    // first chunk of the first tile
+    // pipeline: the row pointers of the next tile are loaded one tile ahead of its nonzeros,
+    // which are loaded one tile ahead of their use
     int t = gw;
-    int row = (t << 5) + lane;
-    int my_lo = 0, my_hi = 0, lo = 0, hi = 0;
-    if (t < ntiles) {
-        const int rr = min(row, n);
-        my_lo = __ldg(rowptr + rr);
-        my_hi = row < n ? __ldg(rowptr + row + 1) : my_lo;
-        lo = __shfl_sync(0xffffffffu, my_lo, 0);
-        hi = __shfl_sync(0xffffffffu, my_hi, 31);
-        fetch(lo, hi);
-    }
+    int my_lo, my_hi, nx_lo, nx_hi;
+    rows_of(t, my_lo, my_hi);
+    rows_of(t + nw, nx_lo, nx_hi);
+    int lo = __shfl_sync(0xffffffffu, my_lo, 0), hi = __shfl_sync(0xffffffffu, my_hi, 31);
+    if (t < ntiles) fetch(lo, hi);
     while (t < ntiles) {
+        const int row = (t << 5) + lane;
         double acc = 0.0;
-        for (int c0 = lo; c0 < hi; c0 += CH) {
+        int c0 = lo;
+        // row pointers two tiles ahead, issued before anything waits
+        int nn_lo, nn_hi;
+        rows_of(t + 2 * nw, nn_lo, nn_hi);
+        const int nlo = __shfl_sync(0xffffffffu, nx_lo, 0), nhi = __shfl_sync(0xffffffffu, nx_hi, 31);
+        do {
             __syncwarp();
 #pragma unroll
             for (int m = 0; m < K; ++m) {
@@ -280,75 +292,39 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
                 sc[lane + 32 * m] = pc[m];
             }
             __syncwarp();
-            // prefetch: the rest of this tile, else the first chunk of the next tile
             const int c1 = c0 + CH;
-            int nt = t, nrow = row, nlo = my_lo, nhi = my_hi, tlo = lo, thi = hi;
-            if (c1 < hi) {
-                fetch(c1, hi);
-            } else {
-                nt = t + nw;
-                if (nt < ntiles) {
-                    nrow = (nt << 5) + lane;
-                    const int rr = min(nrow, n);
-                    nlo = __ldg(rowptr + rr);
-                    nhi = nrow < n ? __ldg(rowptr + nrow + 1) : nlo;
-                    tlo = __shfl_sync(0xffffffffu, nlo, 0);
-                    thi = __shfl_sync(0xffffffffu, nhi, 31);
-                    fetch(tlo, thi);
-                }
-            }
+            if (c1 < hi) fetch(c1, hi);                    // rest of this tile
+            else if (t + nw < ntiles) fetch(nlo, nhi);     // first chunk of the next tile
             const int a = max(my_lo, c0), e = min(my_hi, c1);
             for (int k0 = a; k0 < e; k0 += 8) {
                 double xv[8], vv[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const bool in = k0 + j < e;
-                    xv[j] = in ? __ldg(x + sc[k0 + j - c0]) : 0.0;
-                    vv[j] = in ? sv[k0 + j - c0] : 0.0;
+                for (int jj = 0; jj < 8; ++jj) {
+                    const bool in = k0 + jj < e;
+                    xv[jj] = in ? __ldg(x + sc[k0 + jj - c0]) : 0.0;
+                    vv[jj] = in ? sv[k0 + jj - c0] : 0.0;
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (k0 + j < e) acc = fma(vv[j], xv[j], acc);
+                for (int jj = 0; jj < 8; ++jj)
+                    if (k0 + jj < e) acc = fma(vv[jj], xv[jj], acc);
             }
-            if (c1 >= hi) {   // tile finished: emit the row, move to the next tile
-                if (row < n) {
-                    if (RES) {
-                        const double bi = b[row];
-                        const double ri = bi - acc;
-                        y[row] = ri;
-                        acc1 = fma(ri, ri, acc1);
-                        acc2 = fma(bi, bi, acc2);
-                    } else {
-                        y[row] = acc;
-                        if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
-                    }
-                }
-                t = nt; row = nrow; my_lo = nlo; my_hi = nhi; lo = tlo; hi = thi;
-                break;
+            c0 = c1;
+        } while (c0 < hi);
+        if (row < n) {
+            if (RES) {
+                const double bi = b[row];
+                const double ri = bi - acc;
+                y[row] = ri;
+                acc1 = fma(ri, ri, acc1);
+                acc2 = fma(bi, bi, acc2);
+            } else {
+                y[row] = acc;
+                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
             }
         }
-        if (lo >= hi && t < ntiles) {   // a tile with no nonzeros
-            if (row < n) {
-                if (RES) {
-                    const double bi = b[row];
-                    y[row] = bi;
-                    acc1 = fma(bi, bi, acc1);
-                    acc2 = fma(bi, bi, acc2);
-                } else {
-                    y[row] = 0.0;
-                }
-            }
-            t += nw;
-            if (t < ntiles) {
-                row = (t << 5) + lane;
-                const int rr = min(row, n);
-                my_lo = __ldg(rowptr + rr);
-                my_hi = row < n ? __ldg(rowptr + row + 1) : my_lo;
-                lo = __shfl_sync(0xffffffffu, my_lo, 0);
-                hi = __shfl_sync(0xffffffffu, my_hi, 31);
-                fetch(lo, hi);
-            }
-        }
+        t += nw;
+        my_lo = nx_lo; my_hi = nx_hi; lo = nlo; hi = nhi;
+        nx_lo = nn_lo; nx_hi = nn_hi;
     }
     if (KIND == kSpY) return;
     const double b1 = block_sum<kSpNT>(acc1, red[0]);
