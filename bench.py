@@ -246,6 +246,22 @@ def run_ours(args, rank, world, dist):
         peak, peak_src = 6800.0, "fallback"
     achieved = alg[dom] / (prof[dom] * 1e-3) / 1e9
     wl_key = f"m{args.m}_bs{args.bs}_{args.fmt}"
+    # both SpMV kernels on this matrix, y = A x with the dot (standalone launches)
+    spmv_var = {}
+    xy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    yv = torch.empty(n, dtype=torch.float64, device="cuda")
+    for v, name in ((1, "tma"), (2, "warp")):
+        old = B.bjac_spmv_kernel(v)
+        for _ in range(3):
+            B.bjac_spmv(dA, xs, yv, xy)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(20):
+            B.bjac_spmv(dA, xs, yv, xy)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        B.bjac_spmv_kernel(old)
+        spmv_var[name] = round(ev0.elapsed_time(ev1) / 20, 5)
     apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg"}[apply_kernel]
     kernel_name = {"spmv": "k_spmv", "apply": apply_name, "update_xp": "k_update_xp"}[dom]
     roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -255,6 +271,7 @@ def run_ours(args, rank, world, dist):
                 "per_kernel_ms": {k: round(v, 5) for k, v in shares.items()},
                 "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares},
                 "apply_kernel": apply_name,
+                "spmv_variant_ms": spmv_var,
                 "apply_autotune_ms": dict(zip(("generic", "tma", "register"), [round(t, 4) for t in tune_ms]))}
 
     # end to end through the public API with host buffers: upload A and b from pinned host
