@@ -250,7 +250,7 @@ def run_ours(args, rank, world, dist):
     spmv_var = {}
     xy = torch.zeros(1, dtype=torch.float64, device="cuda")
     yv = torch.empty(n, dtype=torch.float64, device="cuda")
-    for v, name in ((1, "tma"), (2, "warp")):
+    for v, name in ((1, "tma"), (2, "warp"), (3, "pipe")):
         old = B.bjac_spmv_kernel(v)
         for _ in range(3):
             B.bjac_spmv(dA, xs, yv, xy)

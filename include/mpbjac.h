@@ -180,8 +180,9 @@ int bjac_import_inverse(bjac_handle *h, const double *G);
 int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
 /* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):
- * 0 = timed once per matrix shape at setup and the faster kept (default), 1 = TMA-staged
- * CTA tiles, 2 = warp-cooperative. Rows longer on average always use the TMA kernel with
+ * 0 = timed once per matrix shape at setup and the fastest kept (default), 1 = TMA-staged
+ * CTA tiles, 2 = warp-cooperative, 3 = software-pipelined warp-cooperative. Rows longer on
+ * average always use the TMA kernel with
  * large stages. Returns the previous setting, or INVALID_ARG. Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 

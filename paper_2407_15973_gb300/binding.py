@@ -128,7 +128,8 @@ def bjac_spmv(A: DeviceCSR, x, y, xy=None, stream=None):
 
 
 def bjac_spmv_kernel(variant: int) -> int:
-    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative. Returns the old value."""
+    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 3: pipelined warp.
+    Returns the old value."""
     return _check(lib().bjac_spmv_kernel(int(variant)), allow_positive=True)
 
 

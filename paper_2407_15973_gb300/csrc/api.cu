@@ -279,7 +279,11 @@ struct TuneKey {
     int fmt, bs, nb;
     bool operator==(const TuneKey &o) const { return fmt == o.fmt && bs == o.bs && nb == o.nb; }
 };
-static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+struct TuneResult {
+    int kind;
+    float ms[3];
+};
+static std::vector<std::pair<TuneKey, TuneResult>> g_tune_cache;
 
 static int choose_apply_kind(bjac_handle *h) {
     const bool tma_ok = tma_supported(h->lo, h->n);
@@ -290,7 +294,11 @@ static int choose_apply_kind(bjac_handle *h) {
     if (v == 3) { h->apply_kind = reg_ok ? kApplyKindReg : kApplyKindTma; return MPBJAC_OK; }
     const TuneKey key{h->lo.ufmt, h->lo.ubs, h->nb};
     for (auto &e : g_tune_cache)
-        if (e.first == key) { h->apply_kind = e.second; return MPBJAC_OK; }
+        if (e.first == key) {
+            h->apply_kind = e.second.kind;
+            for (int i = 0; i < 3; ++i) h->tune_ms[i] = e.second.ms[i];
+            return MPBJAC_OK;
+        }
     cudaStream_t st = h->stream;
     double *r = nullptr, *z = nullptr, *part = nullptr;
     unsigned int *ticket = nullptr;
@@ -310,13 +318,12 @@ static int choose_apply_kind(bjac_handle *h) {
     cudaEvent_t e0, e1;
     MPB_CUDA(cudaEventCreate(&e0));
     MPB_CUDA(cudaEventCreate(&e1));
-    const int kinds[3] = {kApplyKindGeneric, kApplyKindTma, kApplyKindReg};
-    float best = 1e30f;
-    int best_kind = kApplyKindTma;
-    for (int k : kinds) {
-        if (k == kApplyKindReg && !reg_ok) continue;
-        float t_best = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
+    // interleaved rounds over the candidate kernels, median of 7 after a warm-up round
+    constexpr int kRounds = 8;
+    float t[3][kRounds] = {};
+    for (int rep = 0; rep < kRounds; ++rep) {
+        for (int k = 0; k < 3; ++k) {
+            if (k == kApplyKindReg && !reg_ok) continue;
             MPB_CUDA(cudaEventRecord(e0, st));
             int rc = k == kApplyKindGeneric ? launch_apply_generic(kApplyStandalone, h->lo, h->lo, io, nullptr, st)
                      : k == kApplyKindTma   ? launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, st)
@@ -324,12 +331,17 @@ static int choose_apply_kind(bjac_handle *h) {
             if (rc) return rc;
             MPB_CUDA(cudaEventRecord(e1, st));
             MPB_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0 && ms < t_best) t_best = ms;
+            cudaEventElapsedTime(&t[k][rep], e0, e1);
         }
-        h->tune_ms[k] = t_best;
-        if (t_best < best) { best = t_best; best_kind = k; }
+    }
+    float best = 1e30f;
+    int best_kind = kApplyKindTma;
+    for (int k = 0; k < 3; ++k) {
+        if (k == kApplyKindReg && !reg_ok) continue;
+        std::sort(t[k] + 1, t[k] + kRounds);
+        const float med = t[k][1 + (kRounds - 1) / 2];
+        h->tune_ms[k] = med;
+        if (med < best) { best = med; best_kind = k; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -337,7 +349,7 @@ static int choose_apply_kind(bjac_handle *h) {
     cudaFree(z);
     cudaFree(part);
     h->apply_kind = best_kind;
-    g_tune_cache.push_back({key, best_kind});
+    g_tune_cache.push_back({key, TuneResult{best_kind, {h->tune_ms[0], h->tune_ms[1], h->tune_ms[2]}}});
     return MPBJAC_OK;
 }
 
