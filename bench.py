@@ -272,6 +272,8 @@ def run_ours(args, rank, world, dist):
                 "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares},
                 "apply_kernel": apply_name,
                 "spmv_variant_ms": spmv_var,
+                "spmv_kernel": B.bjac_spmv_tuning(dA)[0],
+                "spmv_autotune_ms": dict(zip(("tma", "warp", "pipe"), [round(t, 4) for t in B.bjac_spmv_tuning(dA)[1]])),
                 "apply_autotune_ms": dict(zip(("generic", "tma", "register"), [round(t, 4) for t in tune_ms]))}
 
     # end to end through the public API with host buffers: upload A and b from pinned host

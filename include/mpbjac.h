@@ -186,6 +186,10 @@ int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
  * large stages. Returns the previous setting, or INVALID_ARG. Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 
+/* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined) and,
+ * if the timing ran for it, the three median times in ms (ms[3], HOST, nullable). */
+int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms);
+
 /* Number of floats of the selector's parameter vector:
  * W1[64][12] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[12] sd[12]. */
 int32_t bjac_mlp_param_count(void);

@@ -79,6 +79,7 @@ def lib():
                 "pcg_profile": (C.c_int, [P, P, P, f64, i32, P, C.POINTER(i32)]),
                 "bjac_apply_kernel": (C.c_int, [P, C.POINTER(i32), P]),
                 "bjac_spmv_kernel": (C.c_int, [i32]),
+                "bjac_spmv_tuning": (C.c_int, [C.POINTER(bjac_csr), C.POINTER(i32), P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -131,6 +132,14 @@ def bjac_spmv_kernel(variant: int) -> int:
     """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 3: pipelined warp.
     Returns the old value."""
     return _check(lib().bjac_spmv_kernel(int(variant)), allow_positive=True)
+
+
+def bjac_spmv_tuning(A: DeviceCSR):
+    """(kernel name in use for A, timed medians in ms for tma / warp / pipe)."""
+    v = C.c_int32()
+    ms = (C.c_float * 3)()
+    _check(lib().bjac_spmv_tuning(C.byref(A.c), C.byref(v), ms))
+    return {1: "tma", 2: "warp", 3: "pipe"}.get(v.value, "tma"), list(ms)
 
 
 def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
