@@ -147,13 +147,13 @@ int bjac_residual(const bjac_csr *A, const double *b, const double *x, double *r
  * Uses the handle's stream. Error UNSUPPORTED if the requested set was not kept. */
 int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *z, double *rz);
 
-/* Same iterations as pcg_solve (no restart, no fallback), launched kernel by kernel
- * without the graph and with CUDA events around each kernel of the loop body, to time
- * them. ms (HOST, 4 floats) receives the mean device milliseconds per iteration of:
- * [0] q = A p with p.q, [1] r -= alpha q with ||r|| (aMP only, else 0),
- * [2] z = M^-1 r with r.z (fused with the r update outside aMP), [3] x += alpha p, p = z + beta p.
- * iters (HOST, nullable) receives the iterations run. x: DEVICE x0 in / iterate out.
- * Synchronises the stream once per iteration. */
+/* The first min(maxit, 64) iterations of pcg_solve (no restart, no fallback), launched
+ * kernel by kernel without the graph, back to back, with CUDA events around each kernel of
+ * the loop body, to time them. ms (HOST, 4 floats) receives the mean device milliseconds
+ * per iteration of: [0] q = A p with p.q, [1] r -= alpha q with ||r|| (aMP only, else 0),
+ * [2] z = M^-1 r with r.z (fused with the r update outside aMP), [3] x += alpha p,
+ * p = z + beta p. iters (HOST, nullable) receives the iterations averaged (those run before
+ * convergence). x: DEVICE x0 in / iterate out. Synchronises the stream once. */
 int pcg_profile(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, float *ms,
                 int32_t *iters);
 

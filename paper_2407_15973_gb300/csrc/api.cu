@@ -866,10 +866,12 @@ extern "C" int bjac_import_inverse(bjac_handle *h, const double *G) {
     return MPBJAC_OK;
 }
 
-// Eager (graph-free) run of the same PCG iterations with CUDA events around every kernel
-// of the loop body; ms[0..3] receive the mean device time per iteration of: the SpMV step,
-// the residual-update step (aMP only; 0 otherwise), the preconditioner apply step, and the
-// x/p update step. iters receives the iterations run. x holds x0 on entry.
+// Eager (graph-free) run of up to min(maxit, 64) iterations of the same PCG loop, all
+// enqueued back to back with CUDA events around every kernel of the loop body and one
+// synchronisation at the end (so no host latency lands inside a timed interval). Iterations
+// after convergence, whose kernels return at once, are left out of the averages.
+// ms[0..3]: mean device time per iteration of the SpMV step, the residual-update step (aMP
+// only; 0 otherwise), the preconditioner apply step, and the x/p update step.
 extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, float *ms,
                            int32_t *iters) {
     if (!h || !b || !x || !ms) return fail(MPBJAC_ERR_INVALID_ARG, "NULL argument");
@@ -888,26 +890,25 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
     rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1, !temporal && hs.low_default == 0);
     if (rc) return rc;
-    cudaEvent_t ev[5];
-    for (int i = 0; i < 5; ++i) MPB_CUDA(cudaEventCreate(&ev[i]));
+    const int cap = maxit < 64 ? maxit : 64;
+    std::vector<cudaEvent_t> ev((size_t)cap * 5);
+    for (auto &e : ev) MPB_CUDA(cudaEventCreate(&e));
+    for (int k = 0; k < cap && rc == 0; ++k) rc = capture_body(h, 0, st, cudaGraphConditionalHandle{}, &ev[(size_t)k * 5]);
+    if (rc == 0) MPB_CUDA(cudaMemcpyAsync(&hs, h->d_S, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    if (rc == 0) MPB_CUDA(cudaStreamSynchronize(st));
+    const int ran = rc == 0 ? (hs.iter < cap ? hs.iter : cap) : 0;
     double acc[4] = {0, 0, 0, 0};
-    int k = 0;
-    int32_t state = kRunning;
-    while (k < maxit) {
-        rc = capture_body(h, 0, st, cudaGraphConditionalHandle{}, ev);
-        if (rc) break;
-        MPB_CUDA(cudaMemcpyAsync(&state, &h->d_S->state, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        MPB_CUDA(cudaStreamSynchronize(st));
-        float t[4];
-        for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
-        for (int i = 0; i < 4; ++i) acc[i] += t[i];
-        ++k;
-        if (state != kRunning) break;
+    for (int k = 0; k < ran; ++k) {
+        for (int i = 0; i < 4; ++i) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, ev[(size_t)k * 5 + i], ev[(size_t)k * 5 + i + 1]);
+            acc[i] += t;
+        }
     }
-    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    for (auto &e : ev) cudaEventDestroy(e);
     if (rc) return rc;
-    for (int i = 0; i < 4; ++i) ms[i] = k ? (float)(acc[i] / k) : 0.0f;
-    if (iters) *iters = k;
+    for (int i = 0; i < 4; ++i) ms[i] = ran ? (float)(acc[i] / ran) : 0.0f;
+    if (iters) *iters = ran;
     return MPBJAC_OK;
 }
 
