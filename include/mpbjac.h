@@ -138,6 +138,21 @@ const char *bjac_last_error(void);
  * written as well (deterministic two-stage reduction). */
 int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *stream);
 
+/* Allocation-free y = A x and *xy = x . y, for callers that cannot allocate device memory
+ * while they run (a fixed device-memory budget reserved up front, a hard memory cap, or code
+ * that must not let cudaFree synchronise the device). The paper has no counterpart: this is a
+ * deployment variant of bjac_spmv. Same arguments as bjac_spmv except that xy (DEVICE, one
+ * double) is required. Instead of allocating scratch for the partial sums of the dot product
+ * it uses a buffer in the library's static device memory: 65,536 partial-sum pairs (1 MiB),
+ * which every GPU that loads the library holds until the process exits, so n is limited to
+ * 16,777,216 rows (INVALID_ARG beyond, with a message naming the limit). The first call on a
+ * device looks up that buffer's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture. Every call shares the one buffer
+ * and finds there what the previous call left (the ticket counter is cleared each time):
+ * calls that overlap on the GPU (other streams, other threads) race and must not be made.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+int bjac_spmv_noalloc(const bjac_csr *A, const double *x, double *y, double *xy, void *stream);
+
 /* r = b - A x and, if rr (DEVICE, nullable) is given, *rr = r . r. */
 int bjac_residual(const bjac_csr *A, const double *b, const double *x, double *r, double *rr,
                   void *stream);

@@ -80,6 +80,7 @@ def lib():
                 "bjac_apply_kernel": (C.c_int, [P, C.POINTER(i32), P]),
                 "bjac_spmv_kernel": (C.c_int, [i32]),
                 "bjac_spmv_tuning": (C.c_int, [C.POINTER(bjac_csr), C.POINTER(i32), P]),
+                "bjac_spmv_noalloc": (C.c_int, [C.POINTER(bjac_csr), P, P, P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -126,6 +127,14 @@ def bjac_spmv(A: DeviceCSR, x, y, xy=None, stream=None):
     """y = A x (and xy[0] = x . y when a one-element float64 CUDA tensor xy is given)."""
     _require_cuda(x, y, xy)
     _check(lib().bjac_spmv(C.byref(A.c), _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
+
+
+def bjac_spmv_noalloc(A: DeviceCSR, x, y, xy, stream=None):
+    """y = A x and xy[0] = x . y without allocating any device memory (see include/mpbjac.h:
+    for callers that cannot allocate while they run; shares one static buffer, so calls must
+    not overlap on the GPU; at most 16,777,216 rows)."""
+    _require_cuda(x, y, xy)
+    _check(lib().bjac_spmv_noalloc(C.byref(A.c), _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
 
 
 def bjac_spmv_kernel(variant: int) -> int:

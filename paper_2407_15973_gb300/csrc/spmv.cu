@@ -654,6 +654,29 @@ extern "C" int bjac_spmv_kernel(int32_t variant) {
 
 namespace mpbjac {
 
+// y = A x and *out = x . y with one CTA per tile group (the grid grows with n instead of
+// being capped), reducing through the caller's partial-sum buffer (2 doubles per CTA) and
+// ticket. Used by the allocation-free entry point; refuses a grid above max_ctas.
+int launch_spmv_dot_grid(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
+                         double *out, cudaStream_t st, int max_ctas) {
+    if (long_rows(A)) {
+        const long long g = ((long long)A.n + kSpNT - 1) / kSpNT;
+        if (g > max_ctas) return fail(MPBJAC_ERR_INVALID_ARG, "matrix too large for the fixed scratch buffer");
+        MPB_CUDA(cudaFuncSetAttribute(k_spmv<SpLong::kCap, SpLong::kStages, kSpYDot>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SpLong::kSmem));
+        k_spmv<SpLong::kCap, SpLong::kStages, kSpYDot><<<(int)g, kSpNT, SpLong::kSmem, st>>>(
+            A.n, A.nnz, A.rowptr, A.colidx, A.val, x, nullptr, y, part, ticket, out, nullptr);
+    } else {
+        const long long tiles = ((long long)A.n + 31) / 32;
+        const long long g = (tiles + kSpNT / 32 - 1) / (kSpNT / 32);
+        if (g > max_ctas) return fail(MPBJAC_ERR_INVALID_ARG, "matrix too large for the fixed scratch buffer");
+        k_spmv_warp<8, kSpYDot><<<(int)g, kSpNT, 0, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, nullptr, y, part,
+                                                           ticket, out, nullptr);
+    }
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
 int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
                 double *dot_out, SolverState *S, int mode, cudaStream_t st) {
     if (mode == 0) return launch_kind<kSpY>(A, x, nullptr, y, part, ticket, dot_out, S, st);
