@@ -109,13 +109,14 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return t;
 }
 
-// Every CTA publishes its partials, then the last CTA to arrive (ticket) sees them all.
+// Every CTA publishes its partials (written by thread 0), then the last CTA to arrive
+// (ticket) sees them all. Only thread 0 fences: it wrote the partials and takes the ticket.
 // Returns true in every thread of that last CTA. The ticket counter is reset there.
 __device__ __forceinline__ bool last_cta(unsigned int *ticket) {
     __shared__ int s_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
         s_last = (t == gridDim.x - 1);
     }
