@@ -250,7 +250,7 @@ def run_ours(args, rank, world, dist):
     spmv_var = {}
     xy = torch.zeros(1, dtype=torch.float64, device="cuda")
     yv = torch.empty(n, dtype=torch.float64, device="cuda")
-    for v, name in ((1, "tma"), (2, "warp"), (3, "pipe")):
+    for v, name in ((1, "tma"), (2, "warp"), (3, "pipe"), (4, "wtma")):
         old = B.bjac_spmv_kernel(v)
         for _ in range(3):
             B.bjac_spmv(dA, xs, yv, xy)
@@ -273,7 +273,8 @@ def run_ours(args, rank, world, dist):
                 "apply_kernel": apply_name,
                 "spmv_variant_ms": spmv_var,
                 "spmv_kernel": B.bjac_spmv_tuning(dA)[0],
-                "spmv_autotune_ms": dict(zip(("tma", "warp", "pipe"), [round(t, 4) for t in B.bjac_spmv_tuning(dA)[1]])),
+                "spmv_autotune_ms": dict(zip(("tma", "warp", "pipe", "wtma"),
+                                             [round(t, 4) for t in B.bjac_spmv_tuning(dA)[1]])),
                 "apply_autotune_ms": dict(zip(("generic", "tma", "register"), [round(t, 4) for t in tune_ms]))}
 
     # end to end through the public API with host buffers: upload A and b from pinned host

@@ -196,13 +196,15 @@ int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
 /* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):
  * 0 = timed once per matrix shape at setup and the fastest kept (default), 1 = TMA-staged
- * CTA tiles, 2 = warp-cooperative, 3 = software-pipelined warp-cooperative. Rows longer on
+ * CTA tiles, 2 = warp-cooperative, 3 = software-pipelined warp-cooperative, 4 = per-warp
+ * TMA rings. Rows longer on
  * average always use the TMA kernel with
  * large stages. Returns the previous setting, or INVALID_ARG. Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 
-/* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined) and,
- * if the timing ran for it, the three median times in ms (ms[3], HOST, nullable). */
+/* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined, 4
+ * per-warp TMA) and, if the timing ran for it, the four median times in ms (ms[4], HOST,
+ * nullable). */
 int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms);
 
 /* Number of floats of the selector's parameter vector:

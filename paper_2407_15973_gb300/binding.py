@@ -138,17 +138,17 @@ def bjac_spmv_noalloc(A: DeviceCSR, x, y, xy, stream=None):
 
 
 def bjac_spmv_kernel(variant: int) -> int:
-    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 3: pipelined warp.
-    Returns the old value."""
+    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 3: pipelined warp,
+    4: per-warp TMA rings. Returns the old value."""
     return _check(lib().bjac_spmv_kernel(int(variant)), allow_positive=True)
 
 
 def bjac_spmv_tuning(A: DeviceCSR):
-    """(kernel name in use for A, timed medians in ms for tma / warp / pipe)."""
+    """(kernel name in use for A, timed medians in ms for tma / warp / pipe / wtma)."""
     v = C.c_int32()
-    ms = (C.c_float * 3)()
+    ms = (C.c_float * 4)()
     _check(lib().bjac_spmv_tuning(C.byref(A.c), C.byref(v), ms))
-    return {1: "tma", 2: "warp", 3: "pipe"}.get(v.value, "tma"), list(ms)
+    return {1: "tma", 2: "warp", 3: "pipe", 4: "wtma"}.get(v.value, "tma"), list(ms)
 
 
 def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):

@@ -57,7 +57,7 @@ def test_spmv_integer_exact(B):
     assert host(xy)[0] == float(np.dot(x, ref))    # integers below 2^53: exact in any order
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", list(SPMV_CASES))
 def test_spmv_parity(B, case, variant):
     A = SPMV_CASES[case]()
