@@ -146,6 +146,12 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         const int s = it % kStages;
         const unsigned phase = (unsigned)((it / kStages) & 1);
         const int row = t * RPT + lrow;
+        // operands of the row's epilogue, loaded before the sum so their latency is hidden
+        double xr = 0.0, bi = 0.0;
+        if (row < n) {
+            if (RES) bi = b[row];
+            else if (KIND != kSpY) xr = __ldg(x + row);
+        }
         int my_lo = 0, my_hi = 0;
         if (row < n) {
             my_lo = __ldg(rowptr + row);
@@ -182,14 +188,13 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         }
         if (row < n) {
             if (RES) {
-                const double bi = b[row];
                 const double ri = bi - acc;
                 y[row] = ri;
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
                 y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }
     }
@@ -279,6 +284,11 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     if (t < ntiles) fetch(lo, hi);
     while (t < ntiles) {
         const int row = (t << 5) + lane;
+        double xr = 0.0, bi = 0.0;
+        if (row < n) {
+            if (RES) bi = b[row];
+            else if (KIND != kSpY) xr = __ldg(x + row);
+        }
         double acc = 0.0;
         int c0 = lo;
         // row pointers two tiles ahead, issued before anything waits
@@ -313,14 +323,13 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
         } while (c0 < hi);
         if (row < n) {
             if (RES) {
-                const double bi = b[row];
                 const double ri = bi - acc;
                 y[row] = ri;
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
                 y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }
         t += nw;
@@ -438,6 +447,11 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
         __syncwarp();
         // sum this lane's row of T_i
         const int row = (t << 5) + lane;
+        double xr = 0.0, bi = 0.0;
+        if (row < n) {
+            if (RES) bi = b[row];
+            else if (KIND != kSpY) xr = __ldg(x + row);
+        }
         double acc = 0.0;
         if (!d0.big) {
             const double *sv = s_v[warp][buf] - d0.lo;
@@ -448,14 +462,13 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
         }
         if (row < n) {
             if (RES) {
-                const double bi = b[row];
                 const double ri = bi - acc;
                 y[row] = ri;
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
                 y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }
         __syncwarp();
@@ -549,9 +562,12 @@ __global__ void __launch_bounds__(kWThreads) k_spmv_wtma(int n, int nnz, const i
         const unsigned phase = (unsigned)((it / kWStages) & 1);
         const int row = (t << 5) + lane;
         int my_lo = 0, my_hi = 0;
+        double xr = 0.0, bi = 0.0;
         if (row < n) {
             my_lo = __ldg(rowptr + row);
             my_hi = __ldg(rowptr + row + 1);
+            if (RES) bi = b[row];
+            else if (KIND != kSpY) xr = __ldg(x + row);
         }
         ok = mbar_wait_bounded(&bars[s], phase);
         if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
@@ -581,14 +597,13 @@ __global__ void __launch_bounds__(kWThreads) k_spmv_wtma(int n, int nnz, const i
         if (lane == 0 && t + kWStages * nw < ntiles) issue(t + kWStages * nw, s);
         if (row < n) {
             if (RES) {
-                const double bi = b[row];
                 const double ri = bi - acc;
                 y[row] = ri;
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
                 y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, __ldg(x + row), acc1);
+                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }
     }
