@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--fmt", default="bf16", choices=list(FMT))
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode table")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
+    ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
+                    help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
+    ap.add_argument("--apply-kernel", default="auto", choices=["auto", "generic", "tma", "reg"],
+                    help="pin the low-precision apply kernel instead of the timed choice")
+    ap.add_argument("--eager", action="store_true",
+                    help="host-driven loop instead of the CUDA graph (the profiler sees every kernel)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only set up the headline policy and run this many eager PCG iterations "
                          "(a short, fixed launch sequence for ncu)")
@@ -160,7 +166,7 @@ def run_ours(args, rank, world, dist):
     dA = B.DeviceCSR(A)
     xs = torch.as_tensor(pr.x_star).cuda()
     b = torch.empty(n, dtype=torch.float64, device="cuda")
-    B.bjac_spmv(dA, xs, b)                       # input construction, not timed
+    B.bjac_spmv(dA, xs, b)                       # input construction, not timed (also times the SpMV kernels)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -195,7 +201,11 @@ def run_ours(args, rank, world, dist):
             ms = float(t.item())
         return ms, stats
 
-    head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt])
+    spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
+    B.bjac_spmv_kernel(spmv_pin)
+    apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3}[args.apply_kernel]
+    head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
+                graph_mode=1 if args.eager else 0)
     if args.profile_iters:
         h = B.bjac_setup(dA, pr.block_ptr, **head)
         prof = h.profile(b, x, tol=TOL, maxit=args.profile_iters)
@@ -204,7 +214,7 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(dev) as clk:
         ms_mixed, st_mixed = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
-    ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM), args.steps, args.warmup)
+    ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM, graph_mode=head["graph_mode"]), args.steps, args.warmup)
     sm = st_mixed[-1]
     s64 = st_fp64[-1]
     err_x = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))

@@ -85,7 +85,9 @@ typedef struct bjac_policy {
     const float *mlp_params;/* HOST pointer, bjac_mlp_param_count() floats, for SELECT_MLP */
     int32_t apply_variant;  /* low-precision apply kernel: 0 autotuned (uniform sets), 1 generic
                                warp-per-block, 2 TMA-staged, 3 register-direct (bs 32)        */
-    int32_t reserved;
+    int32_t graph_mode;     /* 0: each solve runs as one CUDA graph with a device-side while
+                               loop (default); 1: the host enqueues the same kernels in
+                               batches of 32 iterations and checks the state between batches */
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
 

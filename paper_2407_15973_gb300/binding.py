@@ -40,7 +40,7 @@ class bjac_policy(C.Structure):
     _fields_ = [("select", C.c_int32), ("fixed_fmt", C.c_int32), ("temporal", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("adp_tol", C.c_double), ("theta", C.c_double),
                 ("safety_theta", C.c_double), ("mlp_params", C.c_void_p), ("apply_variant", C.c_int32),
-                ("reserved", C.c_int32), ("stream", C.c_void_p)]
+                ("graph_mode", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pcg_stats(C.Structure):
@@ -157,12 +157,14 @@ def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
 
 
 def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp_tol=10.0, theta=0.1,
-                safety_theta=0.5, fp64_fallback=False, mlp_params=None, apply_variant=0, stream=None):
+                safety_theta=0.5, fp64_fallback=False, mlp_params=None, apply_variant=0, graph_mode=0,
+                stream=None):
     p = bjac_policy()
     p.select, p.fixed_fmt, p.temporal = select, fixed_fmt, temporal
     p.fp64_fallback = int(bool(fp64_fallback))
     p.adp_tol, p.theta, p.safety_theta = adp_tol, theta, safety_theta
     p.apply_variant = apply_variant
+    p.graph_mode = graph_mode
     p._mlp_keep = None
     if mlp_params is not None:
         arr = np.ascontiguousarray(mlp_params, dtype=np.float32)

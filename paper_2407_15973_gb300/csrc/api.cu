@@ -605,7 +605,7 @@ static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool l
 // One PCG iteration: captured into the body of a device-side while loop, or launched
 // eagerly by the profiler with an event between kernels (ev != nullptr: ev[0..4]).
 static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphConditionalHandle cond,
-                        cudaEvent_t *ev = nullptr) {
+                        cudaEvent_t *ev = nullptr, bool in_graph = true) {
     const bool temporal = (which == 0) && h->pol.temporal != BJAC_TEMPORAL_NONE;
     const bool use_low = (which == 0) && h->have_lo;
     if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
@@ -628,7 +628,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         if (rc) return rc;
     }
     if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));
-    k_update_xp<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, ev ? 0 : 1);
+    k_update_xp<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, (in_graph && !ev) ? 1 : 0);
     MPB_CUDA(cudaGetLastError());
     if (ev) MPB_CUDA(cudaEventRecord(ev[4], cs));
     return MPBJAC_OK;
@@ -687,7 +687,8 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;
     k_zero_if_zero_rhs<<<vec_grid(h->n), kNT, 0, st>>>(h->n, h->d_S);
-    if (!h->exec[which]) {
+    const bool eager = h->pol.graph_mode == 1;
+    if (!eager && !h->exec[which]) {
         rc = build_graph(h, which);
         if (rc) return rc;
     }
@@ -696,8 +697,22 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
         rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1,
                                  !temporal && hs.low_default == 0);
         if (rc) return rc;
-        MPB_CUDA(cudaGraphLaunch(h->exec[which], st));
-        *graph_launches += 1;
+        if (eager) {
+            // the same loop body, enqueued from the host in batches of 32 iterations; once the
+            // state leaves "running" every kernel returns at once
+            int32_t state = kRunning;
+            while (state == kRunning) {
+                for (int k = 0; k < 32; ++k) {
+                    rc = capture_body(h, which, st, cudaGraphConditionalHandle{}, nullptr, false);
+                    if (rc) return rc;
+                }
+                MPB_CUDA(cudaMemcpyAsync(&state, &h->d_S->state, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                MPB_CUDA(cudaStreamSynchronize(st));
+            }
+        } else {
+            MPB_CUDA(cudaGraphLaunch(h->exec[which], st));
+            *graph_launches += 1;
+        }
         rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 2, st);
         if (rc) return rc;
         MPB_CUDA(cudaMemcpyAsync(&hs, h->d_S, sizeof(SolverState), cudaMemcpyDeviceToHost, st));

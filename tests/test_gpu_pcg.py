@@ -155,3 +155,17 @@ def test_repeat_solves_identical(B):
     h.close()
     assert xs[0][0] == xs[1][0] == xs[2][0]
     assert np.array_equal(xs[0][1], xs[1][1]) and np.array_equal(xs[0][1], xs[2][1])
+
+
+@pytest.mark.parametrize("temporal", [0, 1])
+def test_eager_loop_matches_graph(B, temporal):
+    # the host-driven loop enqueues exactly the kernels of the graph's loop body
+    pr, b, P = _problem("subcube24_bs32")
+    outs = []
+    for mode in (0, 1):
+        st = _gpu_solve(B, pr, b, select=B.SELECT_FIXED, fixed_fmt=B.BF16, temporal=temporal, adp_tol=1e-3,
+                        graph_mode=mode)
+        outs.append(st)
+    assert outs[0]["iters"] == outs[1]["iters"] and outs[0]["converged"] and outs[1]["converged"]
+    assert np.array_equal(outs[0]["x"], outs[1]["x"])
+    assert outs[1]["graph_launches"] == 0
