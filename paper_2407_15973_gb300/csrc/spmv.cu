@@ -99,7 +99,12 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     __shared__ double red[2][kSpNT / 32];
     __shared__ int s_bad;
 
-    if (KIND == kSpPcg && S->state != kRunning) return;
+    if (KIND == kSpPcg) {
+        // the previous iteration's x update is done (stream order): clear its flag even when
+        // this iteration does not run, so a loop body after convergence changes nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
+        if (S->state != kRunning) return;
+    }
     const int ntiles = (n + RPT - 1) / RPT;
     const int nnz4 = nnz & ~3;
 
@@ -245,7 +250,12 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     __shared__ double s_v[NW][CH];
     __shared__ int32_t s_c[NW][CH];
     __shared__ double red[2][NW];
-    if (KIND == kSpPcg && S->state != kRunning) return;
+    if (KIND == kSpPcg) {
+        // the previous iteration's x update is done (stream order): clear its flag even when
+        // this iteration does not run, so a loop body after convergence changes nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
+        if (S->state != kRunning) return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = (n + 31) >> 5;
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
@@ -369,7 +379,12 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
     __shared__ double s_v[NW][2][CH];
     __shared__ double s_x[NW][2][CH];
     __shared__ double red[2][NW];
-    if (KIND == kSpPcg && S->state != kRunning) return;
+    if (KIND == kSpPcg) {
+        // the previous iteration's x update is done (stream order): clear its flag even when
+        // this iteration does not run, so a loop body after convergence changes nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
+        if (S->state != kRunning) return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = (n + 31) >> 5;
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
@@ -519,7 +534,12 @@ __global__ void __launch_bounds__(kWThreads) k_spmv_wtma(int n, int nnz, const i
     __shared__ int s_meta[kWWarps][kWStages][2];
     __shared__ double red[2][kWWarps];
     __shared__ int s_bad;
-    if (KIND == kSpPcg && S->state != kRunning) return;
+    if (KIND == kSpPcg) {
+        // the previous iteration's x update is done (stream order): clear its flag even when
+        // this iteration does not run, so a loop body after convergence changes nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
+        if (S->state != kRunning) return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * kWStages;
     uint8_t *stages = smem + kWWarps * (kWStages * 8 + 16) + (size_t)warp * kWStages * kWStageBytes;
