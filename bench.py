@@ -358,7 +358,17 @@ def oracle_sample(args, gpu_iters=None):
     t0 = time.perf_counter()
     O.pcg(pr.A, P, b, tol=TOL, maxit=k, policy=O.POLICY_FMP, mode=1)
     t_iter = (time.perf_counter() - t0) / k
-    iters = gpu_iters if gpu_iters else 150
+    if gpu_iters:
+        iters = gpu_iters
+    else:     # the oracle's own full-size count (oracle/reference_runs.py), else its sample's count
+        ref = os.path.join(ROOT, "oracle", "full_size_reference.json")
+        key = f"m{args.m}_bs{args.bs}_{args.fmt}"
+        iters = 0
+        if os.path.exists(ref):
+            with open(ref) as f:
+                iters = json.load(f).get(key, {}).get("iters", 0)
+        if not iters:
+            raise SystemExit(f"no oracle iteration count for {key}: run oracle/reference_runs.py")
     ms = (t_setup + t_iter * iters) * 1e3
     return {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
             "sample": f"full setup ({t_setup:.1f} s) + {k} PCG iterations ({t_iter*1e3:.0f} ms each) of the same "
