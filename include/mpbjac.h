@@ -128,6 +128,33 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
 int pcg_solve(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit,
               pcg_stats *stats, double *relres_hist);
 
+/* ---- batched solves: many independent systems in one persistent launch --------------- */
+typedef struct bjac_batch bjac_batch;
+
+/* Set up nsys independent systems A[s] (DEVICE CSR arrays, copied into one block-diagonal
+ * matrix owned by the batch) with contiguous blocks block_ptr[s] (HOST, nb[s]+1 entries,
+ * every block 1..32 rows). policy: select UNIFORM, FIXED or RULE (no aMP switching);
+ * policy.stream is used for every call. The setup also times the persistent kernel with 32-
+ * and 64-row work tiles on this batch (20 iterations each) and keeps the faster tile height.
+ * Errors: INVALID_ARG, UNSUPPORTED, NOT_SPD, CUDA, NO_MEMORY. */
+int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *const *block_ptr, const int32_t *nb,
+                     const bjac_policy *policy, bjac_batch **out);
+
+/* Solve all systems of the batch by PCG at once: one cooperative persistent kernel,
+ * captured once in a CUDA graph, in which every system has its own PCG scalars and stops at
+ * its own convergence (recurrence relres <= tol, then a true-residual check with up to two
+ * restarts). b[s], x[s]: DEVICE vectors of system s (x[s] holds x0 on entry). stats (HOST,
+ * nullable, nsys entries). Returns OK if all converged, else the worst status (errors < 0
+ * before NOT_CONVERGED); TIMEOUT if a grid barrier's bounded wait expired. Synchronises. */
+int pcg_solve_batched(bjac_batch *h, const double *const *b, double *const *x, double tol, int32_t maxit,
+                      pcg_stats *stats);
+
+/* Work tiles, tile height chosen by the setup's timing, grid size and the timings (ms[2]:
+ * 32-row and 64-row tiles) of a batch. All outputs HOST and nullable. */
+int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid, float *tune_ms);
+
+void bjac_batch_destroy(bjac_batch *h);
+
 /* Release everything the handle owns (synchronises its stream first). NULL is ignored. */
 void bjac_destroy(bjac_handle *h);
 

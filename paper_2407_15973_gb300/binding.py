@@ -81,6 +81,10 @@ def lib():
                 "bjac_spmv_kernel": (C.c_int, [i32]),
                 "bjac_spmv_tuning": (C.c_int, [C.POINTER(bjac_csr), C.POINTER(i32), P]),
                 "bjac_spmv_noalloc": (C.c_int, [C.POINTER(bjac_csr), P, P, P, P]),
+                "bjac_batch_setup": (C.c_int, [i32, P, P, P, C.POINTER(bjac_policy), C.POINTER(P)]),
+                "pcg_solve_batched": (C.c_int, [P, P, P, f64, i32, P]),
+                "bjac_batch_info": (C.c_int, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), P]),
+                "bjac_batch_destroy": (None, [P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -267,3 +271,52 @@ def pcg_solve(h: Handle, b, x, tol=1e-10, maxit=1000, hist=None):
 
 def bjac_mlp_param_count() -> int:
     return int(lib().bjac_mlp_param_count())
+
+
+class Batch:
+    """Many independent systems solved together (bjac_batch_setup / pcg_solve_batched)."""
+
+    def __init__(self, As, block_ptrs, policy: bjac_policy | None = None, **kw):
+        self.As = list(As)                       # DeviceCSR objects, borrowed during setup
+        self.bps = [np.ascontiguousarray(bp, dtype=np.int32) for bp in block_ptrs]
+        self.policy = policy if policy is not None else make_policy(**kw)
+        ns = len(self.As)
+        arr = (bjac_csr * ns)(*[a.c for a in self.As])
+        ptrs = (C.c_void_p * ns)(*[bp.ctypes.data for bp in self.bps])
+        nbs = (C.c_int32 * ns)(*[len(bp) - 1 for bp in self.bps])
+        h = C.c_void_p()
+        _check(lib().bjac_batch_setup(ns, C.cast(arr, C.c_void_p), C.cast(ptrs, C.c_void_p), C.cast(nbs, C.c_void_p),
+                                      C.byref(self.policy), C.byref(h)))
+        self.h = h
+        self.nsys = ns
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bjac_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        nt, tr, g = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = (C.c_float * 2)()
+        _check(lib().bjac_batch_info(self.h, C.byref(nt), C.byref(tr), C.byref(g), ms))
+        return dict(ntiles=nt.value, tile_rows=tr.value, grid=g.value, tune_ms=list(ms))
+
+    def solve(self, bs, xs, tol=1e-10, maxit=5000):
+        _require_cuda(*bs, *xs)
+        ns = self.nsys
+        bp = (C.c_void_p * ns)(*[b.data_ptr() for b in bs])
+        xp = (C.c_void_p * ns)(*[x.data_ptr() for x in xs])
+        st = (pcg_stats * ns)()
+        rc = lib().pcg_solve_batched(self.h, C.cast(bp, C.c_void_p), C.cast(xp, C.c_void_p), tol, maxit,
+                                     C.cast(st, C.c_void_p))
+        if rc < 0 and rc != ERR_BREAKDOWN:
+            _check(rc)
+        return rc, [dict(iters=s.iters, converged=bool(s.converged), status=s.status, restarts=s.restarts,
+                         relres=s.relres, true_relres=s.true_relres, solve_ms=s.solve_ms, setup_ms=s.setup_ms)
+                    for s in st]

@@ -1,0 +1,794 @@
+// Batched PCG: many independent systems of uneven size solved together in ONE persistent,
+// cooperative kernel launch (captured in a CUDA graph). The systems' CSR matrices are
+// concatenated into one block-diagonal matrix (global row / column numbering) and their
+// diagonal blocks into one block list, so the setup kernels of the single-system path build
+// the preconditioner unchanged. Every system keeps its own PCG scalars (alpha, beta, rho,
+// relres, iteration count, state) and converges on its own; the rows of finished systems are
+// skipped.
+//
+// Work is cut into tiles of TR rows that never cross a system (nor a diagonal block).
+// Per iteration the kernel runs five phases separated by grid barriers:
+//   A  q = A p on the tiles of running systems, per-tile partial of p.q
+//   B  per system: sigma = sum of its tiles' partials (fixed order), alpha = rho / sigma
+//   C  r -= alpha q, z = M^-1 r (Algorithm 3.1 for low blocks), per-tile partials r.r, r.z
+//   D  per system: relres, convergence / maxit, beta = rho' / rho
+//   E  x += alpha p, p = z + beta p
+// Grid barriers spin on a generation counter with a time bound; a timeout sets an error
+// word and every CTA leaves at its next barrier, so a stall can never hang the GPU.
+// Data one CTA writes and another reads later in the same launch (vectors gathered by the
+// SpMV, per-system scalars) is read with L1-bypassing loads; a tile is always handled by
+// the same warp, so its own rows need no such care.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "apply.cuh"
+#include "common.cuh"
+#include "setup.cuh"
+#include "tma.cuh"
+
+namespace mpbjac {
+
+struct BatchDev {
+    int n_tot, nsys, ntiles;
+    const int32_t *rowptr, *colidx;
+    const double *val;
+    const int32_t *block_ptr;
+    const uint8_t *fmt;
+    const float *scale;
+    const int64_t *qoff;
+    const uint8_t *pool;
+    const int32_t *tile_row;     // [ntiles+1] first row of each tile
+    const int32_t *tile_sys;     // [ntiles] owning system
+    const int32_t *tile_blk;     // [ntiles] first block of each tile
+    const int32_t *sys_tile;     // [nsys+1] first tile of each system
+    const double *b;
+    double *x, *r, *z, *p, *q;
+    double *part;                // [2 * ntiles]
+    // per-system state
+    double *bnorm, *rho, *alpha, *beta, *relres, *true_relres;
+    int32_t *iter, *state, *xpend, *restarts;
+    double tol;
+    int32_t maxit;
+    // barrier and control
+    unsigned int *bar_count, *bar_gen;
+    int32_t *err, *active;
+};
+
+__device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = d.bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(d.bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *d.bar_count = 0u;
+            __threadfence();
+            atomicAdd(d.bar_gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            int polls = 0;
+            while (*gen == g) {
+                if (((++polls) & 1023) == 0 && globaltimer_ns() - t0 > 2000000000ull) {
+                    atomicExch(d.err, MPBJAC_ERR_TIMEOUT);
+                    break;
+                }
+                if (*((volatile int32_t *)d.err) != 0) break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *((volatile int32_t *)d.err) == 0;
+}
+
+// q or r rows of a tile: each lane owns one row (TR = 32) or two rows (TR = 64)
+template <int TR>
+__device__ __forceinline__ void tile_spmv(const BatchDev &d, int t, const double *xin, int mode,
+                                          double &part_a, double &part_b) {
+    // mode 0: q = A p, part_a += p.q ; mode 1: r = b - A x, part_a += r.r, part_b += b.b
+    const int lane = threadIdx.x & 31;
+    const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
+#pragma unroll
+    for (int h = 0; h < TR / 32; ++h) {
+        const int row = r0 + h * 32 + lane;
+        if (row >= r1) continue;
+        double acc = 0.0;
+        const int lo = d.rowptr[row], hi = d.rowptr[row + 1];
+        for (int k = lo; k < hi; ++k) acc = fma(d.val[k], __ldcg(xin + d.colidx[k]), acc);
+        if (mode == 0) {
+            d.q[row] = acc;
+            part_a = fma(acc, __ldcg(xin + row), part_a);
+        } else {
+            const double bi = d.b[row];
+            const double ri = bi - acc;
+            d.r[row] = ri;
+            part_a = fma(ri, ri, part_a);
+            part_b = fma(bi, bi, part_b);
+        }
+    }
+}
+
+// z = M^-1 r on a tile (blocks lie inside tiles). mode 0: plain (with p = z when init);
+// mode 1: r -= alpha q first. part_a += r.z, part_b += r.r.
+template <int TR>
+__device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alpha, int fused, int init,
+                                           float *s_rh, double *s_r, double &part_a, double &part_b) {
+    const int lane = threadIdx.x & 31;
+    const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
+#pragma unroll
+    for (int h = 0; h < TR / 32; ++h) {
+        const int row = r0 + h * 32 + lane;
+        if (row < r1) {
+            double v = d.r[row];
+            if (fused) {
+                v = fma(-alpha, d.q[row], v);
+                d.r[row] = v;
+                part_b = fma(v, v, part_b);
+            }
+            s_r[h * 32 + lane] = v;
+            s_rh[h * 32 + lane] = f64_to_f32_rn(v);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < TR / 32; ++h) {
+        const int row = r0 + h * 32 + lane;
+        if (row < r1) {
+            // this row's block
+            int bk = d.tile_blk[t];
+            while (d.block_ptr[bk + 1] <= row) ++bk;
+            const int bs0 = d.block_ptr[bk], bs = d.block_ptr[bk + 1] - bs0;
+            const int i = row - bs0, off = bs0 - r0;
+            const int f = d.fmt[bk];
+            const uint8_t *base = d.pool + d.qoff[bk];
+            double zi;
+            if (f == BJAC_FP64) {
+                const double *G = reinterpret_cast<const double *>(base);
+                double acc = 0.0;
+                for (int j = 0; j < bs; ++j) acc = fma(G[(size_t)j * bs + i], s_r[off + j], acc);
+                zi = acc;
+            } else {
+                float acc = 0.0f;
+                if (f == BJAC_FP32) {
+                    const float *Q = reinterpret_cast<const float *>(base);
+                    for (int j = 0; j < bs; ++j) acc = fmaf(Q[(size_t)j * bs + i], s_rh[off + j], acc);
+                } else if (f == BJAC_BF16) {
+                    const __nv_bfloat16 *Q = reinterpret_cast<const __nv_bfloat16 *>(base);
+                    for (int j = 0; j < bs; ++j) acc = fmaf(__bfloat162float(Q[(size_t)j * bs + i]), s_rh[off + j], acc);
+                } else {
+                    const __half *Q = reinterpret_cast<const __half *>(base);
+                    for (int j = 0; j < bs; ++j) acc = fmaf(__half2float(Q[(size_t)j * bs + i]), s_rh[off + j], acc);
+                }
+                zi = f32_to_f64(acc * d.scale[bk]);
+            }
+            d.z[row] = zi;
+            if (init) d.p[row] = zi;
+            part_a = fma(s_r[h * 32 + lane], zi, part_a);
+        }
+    }
+    __syncwarp();
+}
+
+template <int TR>
+__global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
+    __shared__ float s_rh[kWarps][TR];
+    __shared__ double s_r[kWarps][TR];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+
+    auto per_tile = [&](auto &&fn) {
+        for (int t = gw; t < d.ntiles; t += nw) {
+            double a = 0.0, b2 = 0.0;
+            fn(t, a, b2);
+            a = warp_sum(a);
+            b2 = warp_sum(b2);
+            if (lane == 0) {
+                d.part[2 * t] = a;
+                d.part[2 * t + 1] = b2;
+            }
+        }
+    };
+    auto sys_sum = [&](int s, int which) {     // fixed-order sum of system s's tile partials
+        double v = 0.0;
+        for (int t = d.sys_tile[s] + lane; t < d.sys_tile[s + 1]; t += 32) v += __ldcg(d.part + 2 * t + which);
+        return warp_sum(v);
+    };
+
+    // ---- start: r = b - A x, relres, then z = M^-1 r, p = z, rho ----------------------
+    for (int restart = 0; restart < 3; ++restart) {
+        per_tile([&](int t, double &a, double &b2) {
+            const int s = d.tile_sys[t];
+            if (restart > 0 && __ldcg(d.state + s) != kRunning) return;
+            tile_spmv<TR>(d, t, d.x, 1, a, b2);
+        });
+        if (!grid_barrier(d)) return;
+        for (int s = gw; s < d.nsys; s += nw) {
+            if (restart > 0 && d.state[s] != kRunning) continue;
+            const double rr = sys_sum(s, 0), bb = sys_sum(s, 1);
+            if (lane == 0) {
+                if (restart == 0) {
+                    d.bnorm[s] = sqrt(bb);
+                    d.iter[s] = 0;
+                    d.restarts[s] = 0;
+                }
+                const double bn = d.bnorm[s];
+                const double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+                d.relres[s] = rel;
+                d.true_relres[s] = rel;
+                d.xpend[s] = 0;
+                if (bn == 0.0) d.state[s] = kConverged;
+                else if (!(rel < 1.0e308)) d.state[s] = kBreakdown;
+                else if (rel <= d.tol) d.state[s] = kConverged;
+                else if (d.iter[s] >= d.maxit) d.state[s] = kMaxit;
+                else d.state[s] = kRunning;
+            }
+        }
+        if (!grid_barrier(d)) return;
+        per_tile([&](int t, double &a, double &b2) {
+            if (__ldcg(d.state + d.tile_sys[t]) != kRunning) return;
+            tile_apply<TR>(d, t, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
+        });
+        if (!grid_barrier(d)) return;
+        for (int s = gw; s < d.nsys; s += nw) {
+            if (d.state[s] != kRunning) continue;
+            const double rz = sys_sum(s, 0);
+            if (lane == 0) {
+                d.rho[s] = rz;
+                if (!finite_pos(rz)) d.state[s] = kBreakdown;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 1;
+        if (!grid_barrier(d)) return;
+
+        // ---- iterations --------------------------------------------------------------
+        while (*((volatile int32_t *)d.active) != 0) {
+            // A: q = A p, p.q
+            per_tile([&](int t, double &a, double &b2) {
+                if (__ldcg(d.state + d.tile_sys[t]) != kRunning) return;
+                tile_spmv<TR>(d, t, d.p, 0, a, b2);
+            });
+            if (!grid_barrier(d)) return;
+            // B: alpha per system
+            for (int s = gw; s < d.nsys; s += nw) {
+                if (d.state[s] != kRunning) continue;
+                const double sigma = sys_sum(s, 0);
+                if (lane == 0) {
+                    if (!finite_pos(sigma)) d.state[s] = kBreakdownSigma;
+                    else d.alpha[s] = d.rho[s] / sigma;
+                }
+            }
+            if (!grid_barrier(d)) return;
+            // C: r -= alpha q, z = M^-1 r, r.r and r.z
+            per_tile([&](int t, double &a, double &b2) {
+                const int s = d.tile_sys[t];
+                if (__ldcg(d.state + s) != kRunning) return;
+                tile_apply<TR>(d, t, __ldcg(d.alpha + s), 1, 0, s_rh[warp], s_r[warp], a, b2);
+            });
+            if (!grid_barrier(d)) return;
+            // D: convergence and beta per system; count the systems still running
+            int my_active = 0;
+            for (int s = gw; s < d.nsys; s += nw) {
+                if (d.state[s] != kRunning) continue;
+                const double rz = sys_sum(s, 0), rr = sys_sum(s, 1);
+                if (lane == 0) {
+                    const int it = d.iter[s] + 1;
+                    d.iter[s] = it;
+                    d.xpend[s] = 1;
+                    const double rel = sqrt(rr) / d.bnorm[s];
+                    d.relres[s] = rel;
+                    if (!(rel < 1.0e308)) d.state[s] = kBreakdown;
+                    else if (rel <= d.tol) d.state[s] = kConverged;
+                    else if (it >= d.maxit) d.state[s] = kMaxit;
+                    else if (!finite_pos(rz)) d.state[s] = kBreakdown;
+                    else {
+                        d.beta[s] = rz / d.rho[s];
+                        d.rho[s] = rz;
+                        my_active = 1;
+                    }
+                }
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
+            if (!grid_barrier(d)) return;
+            if (lane == 0 && my_active) atomicOr(d.active, 1);
+            // E: x += alpha p, p = z + beta p
+            per_tile([&](int t, double &, double &) {
+                const int s = d.tile_sys[t];
+                const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
+                if (!xp && !run) return;
+                const double al = __ldcg(d.alpha + s), be = __ldcg(d.beta + s);
+                const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
+                for (int row = r0 + lane; row < r1; row += 32) {
+                    const double pi = d.p[row];
+                    if (xp) d.x[row] = fma(al, pi, d.x[row]);
+                    if (run) d.p[row] = fma(be, pi, d.z[row]);
+                }
+            });
+            if (!grid_barrier(d)) return;
+            for (int s = gw; s < d.nsys; s += nw)
+                if (lane == 0) d.xpend[s] = 0;
+            if (!grid_barrier(d)) return;
+        }
+        // ---- true residual of the converged systems; restart those that miss tol -----
+        per_tile([&](int t, double &a, double &b2) {
+            const int s = d.tile_sys[t];
+            if (__ldcg(d.state + s) != kConverged) return;
+            tile_spmv<TR>(d, t, d.x, 1, a, b2);
+        });
+        if (!grid_barrier(d)) return;
+        int again = 0;
+        for (int s = gw; s < d.nsys; s += nw) {
+            if (d.state[s] != kConverged) continue;
+            const double rr = sys_sum(s, 0);
+            if (lane == 0) {
+                const double rel = d.bnorm[s] > 0.0 ? sqrt(rr) / d.bnorm[s] : 0.0;
+                d.true_relres[s] = rel;
+                if (rel > d.tol && d.iter[s] < d.maxit && restart < 2) {
+                    d.state[s] = kRunning;
+                    d.restarts[s] += 1;
+                    again = 1;
+                }
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
+        if (!grid_barrier(d)) return;
+        if (lane == 0 && again) atomicOr(d.active, 1);
+        if (!grid_barrier(d)) return;
+        if (*((volatile int32_t *)d.active) == 0) return;
+    }
+}
+
+}  // namespace mpbjac
+
+using namespace mpbjac;
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+struct bjac_batch {
+    int nsys = 0, n_tot = 0, nnz_tot = 0, nb_tot = 0, ntiles = 0, tile_rows = 32;
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t> sys_row, sys_tile, sys_blk;
+    int32_t *rowptr = nullptr, *colidx = nullptr;
+    double *val = nullptr;
+    int32_t *block_ptr = nullptr;
+    int64_t *goff = nullptr;
+    uint8_t *fmt = nullptr;
+    float *scale = nullptr;
+    int64_t *qoff = nullptr;
+    uint8_t *pool = nullptr;
+    double *feat = nullptr, *kap = nullptr;
+    int *status = nullptr;
+    int32_t *tile_row = nullptr, *tile_sys = nullptr, *tile_blk = nullptr, *d_sys_tile = nullptr;
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
+    double *sd = nullptr;          // per-system doubles: bnorm rho alpha beta relres true_relres
+    int32_t *si = nullptr;         // per-system ints: iter state xpend restarts
+    unsigned int *ctl = nullptr;   // barrier count, generation, err, active
+    int grid = 0;
+    float tune_ms[2] = {0, 0};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double tol_cached = -1.0;
+    int maxit_cached = -1;
+    int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
+    float setup_ms = 0.0f;
+};
+
+static void free_batch(bjac_batch *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    void *ptrs[] = {h->rowptr, h->colidx, h->val, h->block_ptr, h->goff, h->fmt, h->scale, h->qoff, h->pool, h->feat,
+                    h->kap, h->status, h->tile_row, h->tile_sys, h->tile_blk, h->d_sys_tile, h->b, h->x, h->r, h->z,
+                    h->p, h->q, h->part, h->sd, h->si, h->ctl};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+__global__ void k_concat_csr(int rows, int row0, int nz0, const int32_t *rp, const int32_t *ci, const double *v,
+                             int32_t *rp_out, int32_t *ci_out, double *v_out) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < rows; i += stride) rp_out[row0 + i] = nz0 + rp[i];
+    const int nnz = rp[rows];
+    for (int k = tid; k < nnz; k += stride) {
+        ci_out[nz0 + k] = row0 + ci[k];
+        v_out[nz0 + k] = v[k];
+    }
+}
+
+static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
+    BatchDev d{};
+    d.n_tot = h->n_tot;
+    d.nsys = h->nsys;
+    d.ntiles = h->ntiles;
+    d.rowptr = h->rowptr;
+    d.colidx = h->colidx;
+    d.val = h->val;
+    d.block_ptr = h->block_ptr;
+    d.fmt = h->fmt;
+    d.scale = h->scale;
+    d.qoff = h->qoff;
+    d.pool = h->pool;
+    d.tile_row = h->tile_row;
+    d.tile_sys = h->tile_sys;
+    d.tile_blk = h->tile_blk;
+    d.sys_tile = h->d_sys_tile;
+    d.b = h->b;
+    d.x = h->x;
+    d.r = h->r;
+    d.z = h->z;
+    d.p = h->p;
+    d.q = h->q;
+    d.part = h->part;
+    const int S = h->nsys;
+    d.bnorm = h->sd;
+    d.rho = h->sd + S;
+    d.alpha = h->sd + 2 * S;
+    d.beta = h->sd + 3 * S;
+    d.relres = h->sd + 4 * S;
+    d.true_relres = h->sd + 5 * S;
+    d.iter = h->si;
+    d.state = h->si + S;
+    d.xpend = h->si + 2 * S;
+    d.restarts = h->si + 3 * S;
+    d.tol = tol;
+    d.maxit = maxit;
+    d.bar_count = h->ctl;
+    d.bar_gen = h->ctl + 1;
+    d.err = reinterpret_cast<int32_t *>(h->ctl + 2);
+    d.active = reinterpret_cast<int32_t *>(h->ctl + 3);
+    return d;
+}
+
+template <int TR>
+static int launch_batched(bjac_batch *h, const BatchDev &d, cudaStream_t st, int grid) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MPB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batched<TR>, d));
+    return MPBJAC_OK;
+}
+
+static int max_coresident(int tr) {
+    int per = 0;
+    cudaError_t e = tr == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<32>, kNT, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<64>, kNT, 0);
+    if (e != cudaSuccess || per < 1) per = 1;
+    return sm_count() * per;
+}
+
+static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
+    // tiles of at most tr rows, cut at system boundaries and at block boundaries
+    std::vector<int32_t> trow, tsys, tblk;
+    h->sys_tile.assign(h->nsys + 1, 0);
+    int bk = 0;
+    for (int s = 0; s < h->nsys; ++s) {
+        h->sys_tile[s] = (int)tsys.size();
+        int row = h->sys_row[s];
+        const int end = h->sys_row[s + 1];
+        while (row < end) {
+            while (bp[bk + 1] <= row) ++bk;
+            int stop = std::min(row + tr, end);
+            // do not split a block: end at the last block boundary inside [row, row + tr]
+            int k = bk;
+            int last = row;
+            while (k < h->nb_tot && bp[k + 1] <= stop) last = bp[++k];
+            if (last == row) last = bp[bk + 1];     // a block longer than tr (never with bs <= 32)
+            trow.push_back(row);
+            tsys.push_back(s);
+            tblk.push_back(bk);
+            row = last;
+        }
+    }
+    h->sys_tile[h->nsys] = (int)tsys.size();
+    trow.push_back(h->n_tot);
+    h->ntiles = (int)tsys.size();
+    cudaFree(h->tile_row);
+    cudaFree(h->tile_sys);
+    cudaFree(h->tile_blk);
+    MPB_CUDA(cudaMalloc(&h->tile_row, sizeof(int32_t) * trow.size()));
+    MPB_CUDA(cudaMalloc(&h->tile_sys, sizeof(int32_t) * tsys.size()));
+    MPB_CUDA(cudaMalloc(&h->tile_blk, sizeof(int32_t) * tblk.size()));
+    MPB_CUDA(cudaMemcpy(h->tile_row, trow.data(), sizeof(int32_t) * trow.size(), cudaMemcpyHostToDevice));
+    MPB_CUDA(cudaMemcpy(h->tile_sys, tsys.data(), sizeof(int32_t) * tsys.size(), cudaMemcpyHostToDevice));
+    MPB_CUDA(cudaMemcpy(h->tile_blk, tblk.data(), sizeof(int32_t) * tblk.size(), cudaMemcpyHostToDevice));
+    MPB_CUDA(cudaMemcpy(h->d_sys_tile, h->sys_tile.data(), sizeof(int32_t) * (h->nsys + 1), cudaMemcpyHostToDevice));
+    cudaFree(h->part);
+    MPB_CUDA(cudaMalloc(&h->part, sizeof(double) * 2 * h->ntiles));
+    h->tile_rows = tr;
+    return MPBJAC_OK;
+}
+
+static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bool use_graph) {
+    BatchDev d = batch_dev(h, tol, maxit);
+    MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 4 * sizeof(unsigned int), st));
+    if (!use_graph) return h->tile_rows == 32 ? launch_batched<32>(h, d, st, h->grid) : launch_batched<64>(h, d, st, h->grid);
+    if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit) {
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->exec = nullptr;
+        h->graph = nullptr;
+        cudaStream_t cs;
+        MPB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        MPB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = h->tile_rows == 32 ? launch_batched<32>(h, d, cs, h->grid) : launch_batched<64>(h, d, cs, h->grid);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "capture of the batched kernel");
+        e = cudaGraphInstantiate(&h->exec, g, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphInstantiate (batched)"); }
+        h->graph = g;
+        h->tol_cached = tol;
+        h->maxit_cached = maxit;
+    }
+    MPB_CUDA(cudaGraphLaunch(h->exec, st));
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *const *block_ptr, const int32_t *nb,
+                                const bjac_policy *policy, bjac_batch **out) {
+    if (!out) return fail(MPBJAC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nsys < 1 || !A || !block_ptr || !nb || !policy) return fail(MPBJAC_ERR_INVALID_ARG, "NULL argument or nsys < 1");
+    const bjac_policy &P = *policy;
+    if (P.select != BJAC_SELECT_UNIFORM && P.select != BJAC_SELECT_FIXED && P.select != BJAC_SELECT_RULE)
+        return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes uniform, fixed or rule selection");
+    if (P.temporal != BJAC_TEMPORAL_NONE) return fail(MPBJAC_ERR_UNSUPPORTED, "no aMP switching in the batched solver");
+    long long n_tot = 0, nnz_tot = 0, nb_tot = 0;
+    for (int s = 0; s < nsys; ++s) {
+        if (A[s].n <= 0 || A[s].nnz < 0 || !A[s].rowptr) return fail(MPBJAC_ERR_INVALID_ARG, "bad CSR in the batch");
+        if (!block_ptr[s] || nb[s] < 1 || block_ptr[s][0] != 0 || block_ptr[s][nb[s]] != A[s].n)
+            return fail(MPBJAC_ERR_INVALID_ARG, "bad block_ptr in the batch");
+        for (int k = 0; k < nb[s]; ++k) {
+            const int bs = block_ptr[s][k + 1] - block_ptr[s][k];
+            if (bs < 1 || bs > 32) return fail(MPBJAC_ERR_INVALID_ARG, "batched blocks need 1..32 rows");
+        }
+        n_tot += A[s].n;
+        nnz_tot += A[s].nnz;
+        nb_tot += nb[s];
+    }
+    if (n_tot >= (1ll << 31) || nnz_tot >= (1ll << 31)) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
+    bjac_batch *h = new bjac_batch();
+    auto bail = [&](int rc) { free_batch(h); return rc; };
+    h->nsys = nsys;
+    h->n_tot = (int)n_tot;
+    h->nnz_tot = (int)nnz_tot;
+    h->nb_tot = (int)nb_tot;
+    h->stream = (cudaStream_t)P.stream;
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    h->sys_row.assign(nsys + 1, 0);
+    h->sys_blk.assign(nsys + 1, 0);
+    std::vector<int32_t> bp(nb_tot + 1, 0);
+    std::vector<int64_t> goff(nb_tot + 1, 0);
+    {
+        int row = 0, blk = 0;
+        for (int s = 0; s < nsys; ++s) {
+            h->sys_row[s] = row;
+            h->sys_blk[s] = blk;
+            for (int k = 0; k < nb[s]; ++k) bp[blk + k] = row + block_ptr[s][k];
+            row += A[s].n;
+            blk += nb[s];
+        }
+        h->sys_row[nsys] = row;
+        h->sys_blk[nsys] = blk;
+        bp[nb_tot] = row;
+        for (long long k = 0; k < nb_tot; ++k) {
+            const int64_t bs = bp[k + 1] - bp[k];
+            goff[k + 1] = goff[k] + bs * bs;
+        }
+    }
+#define BTRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call)); } while (0)
+    BTRY(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n_tot + 1)));
+    BTRY(cudaMalloc(&h->colidx, sizeof(int32_t) * std::max(1ll, nnz_tot)));
+    BTRY(cudaMalloc(&h->val, sizeof(double) * std::max(1ll, nnz_tot)));
+    {
+        int row = 0, nz = 0;
+        for (int s = 0; s < nsys; ++s) {
+            k_concat_csr<<<std::max(1, std::min(sm_count() * 4, (A[s].nnz + 255) / 256)), 256, 0, st>>>(
+                A[s].n, row, nz, A[s].rowptr, A[s].colidx, A[s].val, h->rowptr, h->colidx, h->val);
+            row += A[s].n;
+            nz += A[s].nnz;
+        }
+        const int32_t last = nz;
+        BTRY(cudaMemcpyAsync(h->rowptr + n_tot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        BTRY(cudaStreamSynchronize(st));
+    }
+    BTRY(cudaMalloc(&h->block_ptr, sizeof(int32_t) * (nb_tot + 1)));
+    BTRY(cudaMalloc(&h->goff, sizeof(int64_t) * (nb_tot + 1)));
+    BTRY(cudaMalloc(&h->fmt, nb_tot));
+    BTRY(cudaMalloc(&h->scale, sizeof(float) * nb_tot));
+    BTRY(cudaMalloc(&h->qoff, sizeof(int64_t) * (nb_tot + 1)));
+    BTRY(cudaMalloc(&h->feat, sizeof(double) * 12 * nb_tot));
+    BTRY(cudaMalloc(&h->kap, sizeof(double) * 2 * nb_tot));
+    BTRY(cudaMalloc(&h->status, 2 * sizeof(int)));
+    BTRY(cudaMemcpy(h->block_ptr, bp.data(), sizeof(int32_t) * (nb_tot + 1), cudaMemcpyHostToDevice));
+    BTRY(cudaMemcpy(h->goff, goff.data(), sizeof(int64_t) * (nb_tot + 1), cudaMemcpyHostToDevice));
+    BTRY(cudaMemset(h->status, 0, 2 * sizeof(int)));
+    // pool: fixed format -> compact offsets now; rule -> the binary64 layout (room for any format)
+    const int ffmt = P.select == BJAC_SELECT_UNIFORM ? BJAC_FP64 : P.fixed_fmt;
+    std::vector<int64_t> qoff(nb_tot + 1, 0);
+    for (long long k = 0; k < nb_tot; ++k) {
+        const int64_t bs = bp[k + 1] - bp[k];
+        const int by = P.select == BJAC_SELECT_RULE ? 8 : (ffmt == BJAC_FP64 ? 8 : ffmt == BJAC_FP32 ? 4 : 2);
+        qoff[k + 1] = qoff[k] + ((bs * bs * by + 15) & ~int64_t(15));
+    }
+    BTRY(cudaMalloc(&h->pool, std::max<int64_t>(16, qoff[nb_tot])));
+    BTRY(cudaMemcpy(h->qoff, qoff.data(), sizeof(int64_t) * (nb_tot + 1), cudaMemcpyHostToDevice));
+    bjac_csr big{h->n_tot, h->nnz_tot, h->rowptr, h->colidx, h->val};
+    SetupArgs a{};
+    a.n = h->n_tot;
+    a.rowptr = h->rowptr;
+    a.colidx = h->colidx;
+    a.val = h->val;
+    a.block_ptr = h->block_ptr;
+    a.nb = h->nb_tot;
+    a.goff = h->goff;
+    a.G = nullptr;
+    a.select = P.select;
+    a.fixed_fmt = ffmt;
+    a.theta = P.theta > 0 ? P.theta : 0.1;
+    a.fmt = h->fmt;
+    a.scale = h->scale;
+    a.qoff = h->qoff;
+    a.pool = h->pool;       // the rule path writes each block in its chosen format at its slot
+    a.feat = h->feat;
+    a.kap = h->kap;
+    a.status = h->status;
+    int rc = launch_setup_blocks(a, 32, st);
+    if (rc) return bail(rc);
+    int hstat[2] = {0, 0};
+    BTRY(cudaMemcpyAsync(hstat, h->status, sizeof(hstat), cudaMemcpyDeviceToHost, st));
+    std::vector<uint8_t> hf(nb_tot);
+    BTRY(cudaMemcpyAsync(hf.data(), h->fmt, nb_tot, cudaMemcpyDeviceToHost, st));
+    BTRY(cudaStreamSynchronize(st));
+    if (hstat[0] != 0) return bail(fail(MPBJAC_ERR_NOT_SPD, "a diagonal block of the batch is not positive definite"));
+    for (uint8_t f : hf) h->blocks_per_fmt[f & 3] += 1;
+    (void)big;
+    // vectors and per-system state
+    BTRY(cudaMalloc(&h->b, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->x, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->r, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->z, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->p, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->q, sizeof(double) * n_tot));
+    BTRY(cudaMalloc(&h->sd, sizeof(double) * 6 * nsys));
+    BTRY(cudaMalloc(&h->si, sizeof(int32_t) * 4 * nsys));
+    BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 4));
+    BTRY(cudaMalloc(&h->d_sys_tile, sizeof(int32_t) * (nsys + 1)));
+    // autotuner: tile height (32 or 64 rows per warp task) timed on 20 iterations of this batch
+    {
+        BTRY(cudaMemsetAsync(h->b, 0, sizeof(double) * n_tot, st));
+        std::vector<double> ones(n_tot, 1.0);
+        BTRY(cudaMemcpy(h->b, ones.data(), sizeof(double) * n_tot, cudaMemcpyHostToDevice));
+        float best = 1e30f;
+        int best_tr = 32;
+        for (int tr : {32, 64}) {
+            rc = build_tiles(h, tr, bp);
+            if (rc) return bail(rc);
+            h->grid = max_coresident(tr);
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                BTRY(cudaMemsetAsync(h->x, 0, sizeof(double) * n_tot, st));
+                BTRY(cudaEventRecord(e1, st));
+                cudaEvent_t e2;
+                cudaEventCreate(&e2);
+                rc = run_batched(h, 0.0, 20, st, false);
+                if (rc) return bail(rc);
+                BTRY(cudaEventRecord(e2, st));
+                BTRY(cudaEventSynchronize(e2));
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e1, e2);
+                cudaEventDestroy(e2);
+                if (rep > 0) t = std::min(t, ms);
+            }
+            h->tune_ms[tr == 32 ? 0 : 1] = t;
+            if (t < best) { best = t; best_tr = tr; }
+        }
+        rc = build_tiles(h, best_tr, bp);
+        if (rc) return bail(rc);
+        h->grid = max_coresident(best_tr);
+    }
+#undef BTRY
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&h->setup_ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = h;
+    return MPBJAC_OK;
+}
+
+extern "C" int pcg_solve_batched(bjac_batch *h, const double *const *b, double *const *x, double tol, int32_t maxit,
+                                 pcg_stats *stats) {
+    if (!h || !b || !x) return fail(MPBJAC_ERR_INVALID_ARG, "NULL argument");
+    if (maxit < 0 || !(tol >= 0.0)) return fail(MPBJAC_ERR_INVALID_ARG, "need maxit >= 0 and tol >= 0");
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0, e1;
+    MPB_CUDA(cudaEventCreate(&e0));
+    MPB_CUDA(cudaEventCreate(&e1));
+    MPB_CUDA(cudaEventRecord(e0, st));
+    for (int s = 0; s < h->nsys; ++s) {
+        const size_t rows = (size_t)(h->sys_row[s + 1] - h->sys_row[s]);
+        MPB_CUDA(cudaMemcpyAsync(h->b + h->sys_row[s], b[s], rows * 8, cudaMemcpyDeviceToDevice, st));
+        MPB_CUDA(cudaMemcpyAsync(h->x + h->sys_row[s], x[s], rows * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    int rc = run_batched(h, tol, maxit, st, true);
+    if (rc) return rc;
+    for (int s = 0; s < h->nsys; ++s) {
+        const size_t rows = (size_t)(h->sys_row[s + 1] - h->sys_row[s]);
+        MPB_CUDA(cudaMemcpyAsync(x[s], h->x + h->sys_row[s], rows * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    MPB_CUDA(cudaEventRecord(e1, st));
+    MPB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int S = h->nsys;
+    std::vector<double> sd(6 * (size_t)S);
+    std::vector<int32_t> si(4 * (size_t)S);
+    unsigned int ctl[4];
+    MPB_CUDA(cudaMemcpy(sd.data(), h->sd, sizeof(double) * 6 * S, cudaMemcpyDeviceToHost));
+    MPB_CUDA(cudaMemcpy(si.data(), h->si, sizeof(int32_t) * 4 * S, cudaMemcpyDeviceToHost));
+    MPB_CUDA(cudaMemcpy(ctl, h->ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+    if ((int)ctl[2] != 0) return fail(MPBJAC_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
+    int worst = MPBJAC_OK;
+    for (int s = 0; s < S; ++s) {
+        const int state = si[S + s];
+        int status;
+        if (state == kBreakdown || state == kBreakdownSigma) status = MPBJAC_ERR_BREAKDOWN;
+        else if (state == kConverged && sd[5 * S + s] <= tol) status = MPBJAC_OK;
+        else status = MPBJAC_NOT_CONVERGED;
+        if (status < 0) worst = status;
+        else if (worst == MPBJAC_OK && status > 0) worst = status;
+        if (stats) {
+            pcg_stats &o = stats[s];
+            memset(&o, 0, sizeof(o));
+            o.iters = si[s];
+            o.converged = status == MPBJAC_OK;
+            o.status = status;
+            o.restarts = si[3 * S + s];
+            o.relres = sd[4 * S + s];
+            o.true_relres = sd[5 * S + s];
+            o.graph_launches = 1;
+            for (int i = 0; i < 4; ++i) o.blocks_per_fmt[i] = h->blocks_per_fmt[i];
+            o.setup_ms = h->setup_ms;
+            o.solve_ms = ms;
+        }
+    }
+    return worst;
+}
+
+extern "C" void bjac_batch_destroy(bjac_batch *h) { free_batch(h); }
+
+extern "C" int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid,
+                               float *tune_ms) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "batch is NULL");
+    if (ntiles) *ntiles = h->ntiles;
+    if (tile_rows) *tile_rows = h->tile_rows;
+    if (grid) *grid = h->grid;
+    if (tune_ms) {
+        tune_ms[0] = h->tune_ms[0];
+        tune_ms[1] = h->tune_ms[1];
+    }
+    return MPBJAC_OK;
+}

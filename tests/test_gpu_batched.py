@@ -1,0 +1,77 @@
+"""Batched solver (one persistent cooperative launch for many systems) against the
+single-system GPU solver and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2407_15973_gb300 import problems as PB
+from gpu_util import cuda, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def systems():
+    out = PB.batch2d(count=10, seed=3, side_lo=12, side_hi=48)
+    out.append(PB.make_problem("subcube3d", seed=4, m=12, bs=32))
+    out.append(PB.make_problem("poisson2d", m=20, bs=16))
+    return out
+
+
+def _solve_batch(B, systems, rhs, **pol):
+    dAs = [B.DeviceCSR(p.A) for p in systems]
+    bt = B.Batch(dAs, [p.block_ptr for p in systems], **pol)
+    bs = [cuda(b) for b in rhs]
+    xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in systems]
+    rc, st = bt.solve(bs, xs, tol=TOL, maxit=5000)
+    info = bt.info()
+    bt.close()
+    return rc, st, [host(x) for x in xs], info
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_batched_matches_single_and_oracle(B, systems, fmt):
+    rhs = [O.spmv(p.A, p.x_star) for p in systems]
+    pol = dict(select=B.SELECT_UNIFORM) if fmt == 0 else dict(select=B.SELECT_FIXED, fixed_fmt=fmt)
+    rc, st, xs, info = _solve_batch(B, systems, rhs, **pol)
+    assert rc == 0 and info["tile_rows"] in (32, 64) and info["ntiles"] > len(systems)
+    for p, b, s, x in zip(systems, rhs, st, xs):
+        assert s["converged"] and s["true_relres"] <= TOL
+        dA = B.DeviceCSR(p.A)
+        h = B.bjac_setup(dA, p.block_ptr, **pol)
+        xg = torch.zeros(p.A.n, dtype=torch.float64, device="cuda")
+        sg = h.solve(cuda(b), xg, tol=TOL, maxit=5000)
+        h.close()
+        assert abs(sg["iters"] - s["iters"]) <= 2, (p.name, sg["iters"], s["iters"])
+        P = O.Preconditioner(p.A, p.block_ptr, fmt=None if fmt == 0 else fmt)
+        ref = O.pcg(p.A, P, b, tol=TOL, maxit=5000, policy=O.POLICY_UNIFORM if fmt == 0 else O.POLICY_FMP, mode=1)
+        slack = 2 if fmt == 0 else max(3, 0.05 * ref["iters"])
+        assert abs(ref["iters"] - s["iters"]) <= slack, (p.name, ref["iters"], s["iters"])
+        err = np.linalg.norm(x - p.x_star) / np.linalg.norm(p.x_star)
+        ref_err = np.linalg.norm(ref["x"] - p.x_star) / np.linalg.norm(p.x_star)
+        assert err <= 10 * ref_err + 1e-12
+
+
+def test_batched_zero_rhs_and_rule(B, systems):
+    rhs = [O.spmv(p.A, p.x_star) for p in systems]
+    rhs[2] = np.zeros_like(rhs[2])           # this system is solved by x = 0
+    rc, st, xs, info = _solve_batch(B, systems, rhs, select=B.SELECT_RULE)
+    assert rc == 0
+    assert st[2]["iters"] == 0 and np.all(xs[2] == 0)
+    assert all(s["converged"] for s in st)
+
+
+def test_batched_repeatable(B, systems):
+    rhs = [O.spmv(p.A, p.x_star) for p in systems]
+    a = _solve_batch(B, systems, rhs, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    b = _solve_batch(B, systems, rhs, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    assert [s["iters"] for s in a[1]] == [s["iters"] for s in b[1]]
+    for x1, x2 in zip(a[2], b[2]):
+        assert np.array_equal(x1, x2)
