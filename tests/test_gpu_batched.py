@@ -69,9 +69,16 @@ def test_batched_zero_rhs_and_rule(B, systems):
 
 
 def test_batched_repeatable(B, systems):
+    # one batch solved twice gives bit-identical results (fixed tiles, fixed reduction order)
     rhs = [O.spmv(p.A, p.x_star) for p in systems]
-    a = _solve_batch(B, systems, rhs, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
-    b = _solve_batch(B, systems, rhs, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
-    assert [s["iters"] for s in a[1]] == [s["iters"] for s in b[1]]
-    for x1, x2 in zip(a[2], b[2]):
+    dAs = [B.DeviceCSR(p.A) for p in systems]
+    bt = B.Batch(dAs, [p.block_ptr for p in systems], select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    runs = []
+    for _ in range(2):
+        xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in systems]
+        rc, st = bt.solve([cuda(b) for b in rhs], xs, tol=TOL, maxit=5000)
+        runs.append(([s["iters"] for s in st], [host(x) for x in xs]))
+    bt.close()
+    assert runs[0][0] == runs[1][0]
+    for x1, x2 in zip(runs[0][1], runs[1][1]):
         assert np.array_equal(x1, x2)
