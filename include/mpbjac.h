@@ -55,6 +55,7 @@ extern "C" {
 #define BJAC_SELECT_RULE 2      /* cheapest f with kappa_1(B_b) u_f <= theta                 */
 #define BJAC_SELECT_MLP 3       /* learned 12-64-64-3 selector, then promoted until          */
                                 /* kappa_1 u_f <= safety_theta                               */
+#define BJAC_SELECT_GIVEN 4     /* every block the format policy.block_fmt[b] names          */
 
 /* ---- residual-driven switching (the paper's aMP-BJAC) ------------------------------- */
 #define BJAC_TEMPORAL_NONE 0
@@ -83,6 +84,7 @@ typedef struct bjac_policy {
     double theta;           /* rule threshold on kappa_1 * u_f (0.1 if <= 0)               */
     double safety_theta;    /* MLP promotion threshold on kappa_1 * u_f (0.5 if <= 0)      */
     const float *mlp_params;/* HOST pointer, bjac_mlp_param_count() floats, for SELECT_MLP */
+    const uint8_t *block_fmt;/* HOST pointer, nb formats, for SELECT_GIVEN                  */
     int32_t apply_variant;  /* low-precision apply kernel: 0 autotuned (uniform sets), 1 generic
                                warp-per-block, 2 TMA-staged, 3 register-direct (bs 32)        */
     int32_t graph_mode;     /* 0: each solve runs as one CUDA graph with a device-side while
@@ -235,6 +237,27 @@ int bjac_spmv_kernel(int32_t variant);
  * per-warp TMA) and, if the timing ran for it, the four median times in ms (ms[4], HOST,
  * nullable). */
 int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms);
+
+/* ---- the learned selector (training and inference on the GPU) ------------------------ */
+
+/* Gradient of the mean softmax cross-entropy of the 12-64-64-3 selector over N samples.
+ * params: HOST, bjac_mlp_param_count() floats (weights, then feature mean and standard
+ * deviation used to standardise the inputs). feat: DEVICE N x 12 doubles (raw features as
+ * bjac_export returns them); label: DEVICE N int32 classes (0 FP64, 1 FP32, 2 16-bit).
+ * bf16_weights: 1 to use the weights rounded to bfloat16 (as inference does), 0 for the
+ * binary32 values. grad: HOST, the first 5187 entries (weights only); loss: HOST. */
+int bjac_mlp_grad(const float *params, int32_t bf16_weights, const double *feat, const int32_t *label, int32_t N,
+                  float *grad, float *loss, void *stream);
+
+/* Full-batch Adam (beta 0.9 / 0.999) for `epochs` steps on the same loss with bfloat16
+ * forward weights and binary32 masters; params (HOST) is updated in place (the feature mean
+ * and deviation entries are left as given). loss_hist: HOST, epochs floats, nullable. */
+int bjac_mlp_train(float *params, const double *feat, const int32_t *label, int32_t N, int32_t epochs, float lr,
+                   float *loss_hist, void *stream);
+
+/* Logits (HOST, N x 3) of the selector for N feature rows (DEVICE). */
+int bjac_mlp_logits(const float *params, int32_t bf16_weights, const double *feat, int32_t N, float *logits,
+                    void *stream);
 
 /* Number of floats of the selector's parameter vector:
  * W1[64][12] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[12] sd[12]. */

@@ -17,7 +17,7 @@ from . import build as _build
 
 FP64, FP32, BF16, FP16S = 0, 1, 2, 3
 FORMAT_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", FP16S: "fp16s"}
-SELECT_UNIFORM, SELECT_FIXED, SELECT_RULE, SELECT_MLP = 0, 1, 2, 3
+SELECT_UNIFORM, SELECT_FIXED, SELECT_RULE, SELECT_MLP, SELECT_GIVEN = 0, 1, 2, 3, 4
 TEMPORAL_NONE, TEMPORAL_HL, TEMPORAL_LH = 0, 1, 2
 
 OK, NOT_CONVERGED = 0, 1
@@ -39,7 +39,8 @@ class bjac_csr(C.Structure):
 class bjac_policy(C.Structure):
     _fields_ = [("select", C.c_int32), ("fixed_fmt", C.c_int32), ("temporal", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("adp_tol", C.c_double), ("theta", C.c_double),
-                ("safety_theta", C.c_double), ("mlp_params", C.c_void_p), ("apply_variant", C.c_int32),
+                ("safety_theta", C.c_double), ("mlp_params", C.c_void_p), ("block_fmt", C.c_void_p),
+                ("apply_variant", C.c_int32),
                 ("graph_mode", C.c_int32), ("stream", C.c_void_p)]
 
 
@@ -85,6 +86,9 @@ def lib():
                 "pcg_solve_batched": (C.c_int, [P, P, P, f64, i32, P]),
                 "bjac_batch_info": (C.c_int, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), P]),
                 "bjac_batch_destroy": (None, [P]),
+                "bjac_mlp_grad": (C.c_int, [P, i32, P, P, i32, P, P, P]),
+                "bjac_mlp_train": (C.c_int, [P, P, P, i32, i32, C.c_float, P, P]),
+                "bjac_mlp_logits": (C.c_int, [P, i32, P, i32, P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -161,8 +165,8 @@ def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
 
 
 def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp_tol=10.0, theta=0.1,
-                safety_theta=0.5, fp64_fallback=False, mlp_params=None, apply_variant=0, graph_mode=0,
-                stream=None):
+                safety_theta=0.5, fp64_fallback=False, mlp_params=None, block_fmt=None, apply_variant=0,
+                graph_mode=0, stream=None):
     p = bjac_policy()
     p.select, p.fixed_fmt, p.temporal = select, fixed_fmt, temporal
     p.fp64_fallback = int(bool(fp64_fallback))
@@ -176,6 +180,11 @@ def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp
             raise ValueError("mlp_params has the wrong size")
         p._mlp_keep = arr
         p.mlp_params = arr.ctypes.data
+    p._fmt_keep = None
+    if block_fmt is not None:
+        fa = np.ascontiguousarray(block_fmt, dtype=np.uint8)
+        p._fmt_keep = fa
+        p.block_fmt = fa.ctypes.data
     p.stream = _stream(stream)
     return p
 
@@ -320,3 +329,33 @@ class Batch:
         return rc, [dict(iters=s.iters, converged=bool(s.converged), status=s.status, restarts=s.restarts,
                          relres=s.relres, true_relres=s.true_relres, solve_ms=s.solve_ms, setup_ms=s.setup_ms)
                     for s in st]
+
+
+def bjac_mlp_grad(params, feat, label, bf16_weights=True, stream=None):
+    """(loss, gradient of the 5187 weights) of the selector on DEVICE feat (N x 12) / label (N)."""
+    _require_cuda(feat, label)
+    pr = np.ascontiguousarray(params, dtype=np.float32)
+    g = np.zeros(5187, np.float32)
+    loss = C.c_float()
+    _check(lib().bjac_mlp_grad(pr.ctypes.data, int(bool(bf16_weights)), _ptr(feat), _ptr(label), feat.shape[0],
+                               g.ctypes.data, C.byref(loss), _stream(stream)))
+    return float(loss.value), g
+
+
+def bjac_mlp_train(params, feat, label, epochs=300, lr=3e-3, stream=None):
+    """Adam on the GPU; returns (new params, loss history)."""
+    _require_cuda(feat, label)
+    pr = np.array(params, dtype=np.float32, copy=True)
+    hist = np.zeros(epochs, np.float32)
+    _check(lib().bjac_mlp_train(pr.ctypes.data, _ptr(feat), _ptr(label), feat.shape[0], epochs, float(lr),
+                                hist.ctypes.data, _stream(stream)))
+    return pr, hist
+
+
+def bjac_mlp_logits(params, feat, bf16_weights=True, stream=None):
+    _require_cuda(feat)
+    pr = np.ascontiguousarray(params, dtype=np.float32)
+    out = np.zeros((feat.shape[0], 3), np.float32)
+    _check(lib().bjac_mlp_logits(pr.ctypes.data, int(bool(bf16_weights)), _ptr(feat), feat.shape[0],
+                                 out.ctypes.data, _stream(stream)))
+    return out

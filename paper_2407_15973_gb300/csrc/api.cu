@@ -377,8 +377,13 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         if (bs != ubs) ubs = 0;
     }
     const bjac_policy &P = *policy;
-    if (P.select < BJAC_SELECT_UNIFORM || P.select > BJAC_SELECT_MLP)
+    if (P.select < BJAC_SELECT_UNIFORM || P.select > BJAC_SELECT_GIVEN)
         return fail(MPBJAC_ERR_INVALID_ARG, "unknown select");
+    if (P.select == BJAC_SELECT_GIVEN) {
+        if (!P.block_fmt) return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_GIVEN needs block_fmt");
+        for (int b = 0; b < nb; ++b)
+            if (P.block_fmt[b] > BJAC_FP16S) return fail(MPBJAC_ERR_INVALID_ARG, "block_fmt entries must be 0..3");
+    }
     if (P.select == BJAC_SELECT_FIXED && (P.fixed_fmt < BJAC_FP64 || P.fixed_fmt > BJAC_FP16S))
         return fail(MPBJAC_ERR_INVALID_ARG, "unknown fixed_fmt");
     if (P.temporal < BJAC_TEMPORAL_NONE || P.temporal > BJAC_TEMPORAL_LH)
@@ -394,6 +399,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     if (h->pol.theta <= 0.0) h->pol.theta = 0.1;
     if (h->pol.safety_theta <= 0.0) h->pol.safety_theta = 0.5;
     h->pol.mlp_params = nullptr;   // not retained
+    h->pol.block_fmt = nullptr;
     h->stream = (cudaStream_t)P.stream;
     h->n = A->n;
     h->nb = nb;
@@ -412,7 +418,8 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         const int64_t bs = block_ptr[b + 1] - block_ptr[b];
         h->h_goff[b + 1] = h->h_goff[b] + bs * bs;
     }
-    const bool fixed_now = P.select == BJAC_SELECT_FIXED || P.select == BJAC_SELECT_UNIFORM;
+    const bool fixed_now = P.select == BJAC_SELECT_FIXED || P.select == BJAC_SELECT_UNIFORM ||
+                           P.select == BJAC_SELECT_GIVEN;
     h->have_hi = P.select == BJAC_SELECT_UNIFORM || P.temporal != BJAC_TEMPORAL_NONE || P.fp64_fallback ||
                  !fixed_now;
     h->have_lo = P.select != BJAC_SELECT_UNIFORM;
@@ -473,7 +480,15 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     a.kap = h->d_kap;
     a.status = h->d_status;
     if (h->have_lo && fixed_now) {
-        set_qoff({});
+        if (P.select == BJAC_SELECT_GIVEN) {
+            std::vector<uint8_t> given(P.block_fmt, P.block_fmt + nb);
+            set_qoff(given);
+            MPB_TRY(cudaMemcpyAsync(h->d_fmt, P.block_fmt, nb, cudaMemcpyHostToDevice, st) == cudaSuccess
+                        ? 0 : cuda_fail(cudaGetLastError(), "copy block_fmt"));
+            a.given = h->d_fmt;
+        } else {
+            set_qoff({});
+        }
         MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
         MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
                                 st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));

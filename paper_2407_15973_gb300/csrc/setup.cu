@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kSetupNT) k_setup_blocks(SetupArgs a, int bs_m
     if (a.select == BJAC_SELECT_UNIFORM) f = BJAC_FP64;
     else if (a.select == BJAC_SELECT_FIXED) f = a.fixed_fmt;
     else if (a.select == BJAC_SELECT_RULE) f = rule_format(lk, ldr, a.theta);
+    else if (a.select == BJAC_SELECT_GIVEN) f = a.given[b];
     else f = BJAC_FP64;   // the learned selector decides in a later pass
     const int ex = (f == BJAC_BF16 || f == BJAC_FP16S) ? scale_exp(gmax) : 0;
     if (tid == 0) {

@@ -23,6 +23,7 @@ struct SetupArgs {
     double *feat;            // [nb * 12] (nullable)
     double *kap;             // [2 nb]: log10 kappa_1, log10 dynamic range of G
     int *status;             // [2]: first error code, its block
+    const uint8_t *given;    // [nb] formats for BJAC_SELECT_GIVEN (device), else nullptr
 };
 
 size_t setup_smem_bytes(int bs_max);

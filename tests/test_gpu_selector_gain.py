@@ -1,0 +1,43 @@
+"""What the trained selector gains over the method without it (the condition-number rule),
+on held-out systems of the law it was trained on (27-point anisotropic diffusion)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2407_15973_gb300 import problems as PB
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+BYTES = {0: 8, 1: 4, 2: 2, 3: 2}
+
+
+def test_trained_selector_beats_rule_on_held_out_systems():
+    B = need_gpu()
+    from paper_2407_15973_gb300 import selector
+    if not os.path.exists(selector.DEFAULT_WEIGHTS):
+        pytest.fail("trained weights missing: run python -m paper_2407_15973_gb300.selector")
+    params = selector.load()
+    tot = {"rule": [0, 0], "mlp": [0, 0], "fp64": [0, 0]}
+    for seed in range(5):                         # held out: training used seeds >= 1000
+        pr = PB.make_problem("aniso27", seed=seed, m=20, bs=64)
+        dA = B.DeviceCSR(pr.A)
+        xs = torch.as_tensor(pr.x_star).cuda()
+        b = torch.empty(pr.A.n, dtype=torch.float64, device="cuda")
+        B.bjac_spmv(dA, xs, b)
+        for name, pol in (("fp64", dict(select=B.SELECT_UNIFORM)), ("rule", dict(select=B.SELECT_RULE)),
+                          ("mlp", dict(select=B.SELECT_MLP, mlp_params=params))):
+            h = B.bjac_setup(dA, pr.block_ptr, **pol)
+            fm = h.export()["fmt"]
+            x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+            st = h.solve(b, x, tol=1e-10, maxit=20000)
+            h.close()
+            assert st["converged"] and st["true_relres"] <= 1e-10, (name, seed)
+            bs = np.diff(pr.block_ptr)
+            tot[name][0] += int(np.sum(bs * bs * np.array([BYTES[int(f)] for f in fm])))
+            tot[name][1] += st["iters"]
+    # fewer preconditioner bytes per iteration than the rule, at (almost) the same iterations
+    assert tot["mlp"][0] < 0.8 * tot["rule"][0], tot
+    assert tot["mlp"][1] <= 1.03 * tot["rule"][1] + 5, tot
+    assert tot["mlp"][1] <= 1.05 * tot["fp64"][1] + 5, tot
