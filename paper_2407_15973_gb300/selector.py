@@ -4,8 +4,9 @@ Labels come from the method itself: for a training system, the blocks are split 
 groups by the octiles of their log10 condition number; for each group and each candidate
 class (FP32, 16-bit) only that group is demoted (all other blocks binary64) and the system
 is solved; the group's label is the cheapest class whose solve converges with a delay of
-at most max(2, 0.5 % of the all-binary64 count) iterations (class 0 = FP64 otherwise;
-rounding order alone moves these counts by a couple of iterations). The
+at most max(3, 1.5 % of the all-binary64 count) iterations (class 0 = FP64 otherwise). On
+these ill-conditioned systems any perturbation of the rounding moves the count by a few
+iterations, so a tighter bound would label noise. The
 12-64-64-3 MLP is then trained by the library's own forward/backward kernels (full-batch
 Adam, bfloat16 forward weights, binary32 masters).
 
@@ -72,7 +73,7 @@ def label_problem(pr, groups: int = 8, tol: float = 1e-10):
             fm = np.zeros(nb, np.uint8)
             fm[sel] = B.FP32 if cls == 1 else sixteen[sel]
             st = solve_given(dA, pr, b, fm, tol)
-            ok[cls] = st["converged"] and st["iters"] - base["iters"] <= max(2, 0.005 * base["iters"])
+            ok[cls] = st["converged"] and st["iters"] - base["iters"] <= max(3, 0.015 * base["iters"])
         if ok[2] and not ok[1]:
             monotone_violations += 1
         labels[sel] = 2 if ok[2] else (1 if ok[1] else 0)
