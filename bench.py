@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
     ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
                     help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
+    ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell"],
+                    help="pin the loop SpMV's matrix layout instead of the timed choice")
     ap.add_argument("--apply-kernel", default="auto", choices=["auto", "generic", "tma", "reg"],
                     help="pin the low-precision apply kernel instead of the timed choice")
     ap.add_argument("--eager", action="store_true",
@@ -204,8 +206,9 @@ def run_ours(args, rank, world, dist):
     spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
     B.bjac_spmv_kernel(spmv_pin)
     apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3}[args.apply_kernel]
+    layout_pin = {"auto": 0, "csr": 1, "sell": 2}[args.spmv_layout]
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
-                graph_mode=1 if args.eager else 0)
+                graph_mode=1 if args.eager else 0, spmv_format=layout_pin)
     if args.profile_iters:
         h = B.bjac_setup(dA, pr.block_ptr, **head)
         prof = h.profile(b, x, tol=TOL, maxit=args.profile_iters)
@@ -214,7 +217,8 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(dev) as clk:
         ms_mixed, st_mixed = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
-    ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM, graph_mode=head["graph_mode"]), args.steps, args.warmup)
+    ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM, graph_mode=head["graph_mode"],
+                                  spmv_format=layout_pin), args.steps, args.warmup)
     sm = st_mixed[-1]
     s64 = st_fp64[-1]
     err_x = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
@@ -230,6 +234,9 @@ def run_ours(args, rank, world, dist):
         table["amp-lh1e-5-bf16"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"], temporal=B.TEMPORAL_LH,
                                         adp_tol=1e-5)
         table["rule"] = dict(select=B.SELECT_RULE)
+        from paper_2407_15973_gb300 import selector as SEL
+        if os.path.exists(SEL.DEFAULT_WEIGHTS):
+            table["mlp"] = dict(select=B.SELECT_MLP, mlp_params=SEL.load())
         for name, pol in table.items():
             ms, sts = timed(pol, 2, 1)
             s = sts[-1]
@@ -240,6 +247,7 @@ def run_ours(args, rank, world, dist):
     # per-kernel device times of one iteration (eager launches, CUDA events on the stream)
     h = B.bjac_setup(dA, pr.block_ptr, **head)
     apply_kernel, tune_ms = h.apply_kernel()
+    layout = h.spmv_format()
     x.zero_()
     prof = h.profile(b, x, tol=TOL, maxit=MAXIT)
     h.close()
@@ -272,8 +280,25 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         B.bjac_spmv_kernel(old)
         spmv_var[name] = round(ev0.elapsed_time(ev1) / 20, 5)
+    # the loop SpMV in both layouts through handles (y = A x with the dot, standalone launches)
+    layout_ms = {}
+    for name, fmt_pin in (("csr", 1), ("sell32", 2)):
+        hl = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], spmv_format=fmt_pin)
+        for _ in range(3):
+            hl.spmv(xs, yv, xy)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(20):
+            hl.spmv(xs, yv, xy)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        hl.close()
+        layout_ms[name] = round(ev0.elapsed_time(ev1) / 20, 5)
     apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg"}[apply_kernel]
-    kernel_name = {"spmv": "k_spmv", "apply": apply_name, "update_xp": "k_update_xp"}[dom]
+    csr_name = {"tma": "k_spmv", "warp": "k_spmv_warp", "pipe": "k_spmv_pipe", "wtma": "k_spmv_wtma"}[
+        B.bjac_spmv_tuning(dA)[0]]
+    spmv_name = "k_spmv_sell" if layout["format"] == "sell32" else csr_name
+    kernel_name = {"spmv": spmv_name, "apply": apply_name, "update_xp": "k_update_xp"}[dom]
     roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": committed_traffic(kernel_name, wl_key), "algorithmic_bytes": alg[dom],
@@ -281,6 +306,11 @@ def run_ours(args, rank, world, dist):
                 "per_kernel_ms": {k: round(v, 5) for k, v in shares.items()},
                 "per_kernel_gbs": {k: round(alg[k] / (shares[k] * 1e-3) / 1e9, 1) for k in shares},
                 "apply_kernel": apply_name,
+                "spmv_kernel_name": spmv_name,
+                "spmv_layout": {"format": layout["format"], "stored_entries": layout["entries"],
+                                "setup_timing_ms": {"csr": round(layout["ms"][0], 4),
+                                                    "sell32": round(layout["ms"][1], 4)},
+                                "standalone_ms": layout_ms},
                 "spmv_variant_ms": spmv_var,
                 "spmv_kernel": B.bjac_spmv_tuning(dA)[0],
                 "spmv_autotune_ms": dict(zip(("tma", "warp", "pipe", "wtma"),
@@ -321,6 +351,7 @@ def run_ours(args, rank, world, dist):
     d2h = n * 8
 
     setup_kernels = 2 + (0 if head["select"] in (B.SELECT_FIXED, B.SELECT_UNIFORM) else 1)
+    setup_kernels += 3 if layout["format"] == "sell32" else 0       # slice lengths, scan, fill
     per_step = [setup_kernels + 3 + 3 * s["iters"] + 1 for s in st_mixed]
     out = {
         "metric": METRIC, "value": round(ms_mixed, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,

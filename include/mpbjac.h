@@ -90,6 +90,11 @@ typedef struct bjac_policy {
     int32_t graph_mode;     /* 0: each solve runs as one CUDA graph with a device-side while
                                loop (default); 1: the host enqueues the same kernels in
                                batches of 32 iterations and checks the state between batches */
+    int32_t spmv_format;    /* matrix layout of the loop SpMV q = A p: 0 chosen at setup (a
+                               SELL-32 copy is built when its padding stays under 1.5 nnz,
+                               both layouts are timed once per matrix shape and the faster is
+                               kept), 1 the caller's CSR arrays, 2 always the SELL-32 copy.
+                               Either layout sums every row in CSR order: same result bits. */
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
 
@@ -203,7 +208,27 @@ int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *z, double *
 int pcg_profile(bjac_handle *h, const double *b, double *x, double tol, int32_t maxit, float *ms,
                 int32_t *iters);
 
+/* y = A x with the layout the handle's PCG loop uses (see bjac_policy.spmv_format), on the
+ * handle's stream; *xy = x . y as well when xy (DEVICE, nullable) is given. x, y: DEVICE,
+ * n doubles. Uses the handle's reduction scratch: not concurrent with a solve on the same
+ * handle. */
+int bjac_handle_spmv(bjac_handle *h, const double *x, double *y, double *xy);
+
 /* ---- inspection (tests, tools) ------------------------------------------------------- */
+
+/* The library's binary64 <-> binary32 conversions, element-wise over n entries: f[i] = x[i]
+ * rounded to nearest even in binary32 (subnormals kept), w[i] = f[i] widened back. The apply
+ * kernels convert r and z with these integer-only routines instead of the hardware
+ * conversion (which would occupy the FP64 pipe); this entry lets a test compare them with
+ * the hardware and with an independent rounding. x: DEVICE; f, w: DEVICE, nullable. */
+int bjac_convert(const double *x, float *f, double *w, int32_t n, void *stream);
+
+/* Layout of the loop SpMV (HOST outputs, each nullable): *format 0 = CSR arrays of the
+ * caller, 1 = SELL-32 copy (slices of 32 rows padded to the slice's longest row, stored
+ * column-major); *entries = stored entries of the SELL-32 copy including padding (0 if none
+ * was kept); ms[2] = median times of one y = A x in the CSR and SELL-32 layouts when the
+ * setup timed them (else 0). */
+int bjac_spmv_format(const bjac_handle *h, int32_t *format, int64_t *entries, float *ms);
 
 /* Sizes: nb, bytes of the low-precision pool, entries of the binary64 pool (0 if not kept). */
 int bjac_info(const bjac_handle *h, int32_t *nb, int64_t *pool_bytes, int64_t *g_entries);
@@ -228,9 +253,10 @@ int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 /* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):
  * 0 = timed once per matrix shape at setup and the fastest kept (default), 1 = TMA-staged
  * CTA tiles, 2 = warp-cooperative, 3 = software-pipelined warp-cooperative, 4 = per-warp
- * TMA rings. Rows longer on
- * average always use the TMA kernel with
- * large stages. Returns the previous setting, or INVALID_ARG. Not thread-safe. */
+ * TMA rings, 5 = bjac_spmv and bjac_residual build a SELL-32 copy of A for the call and run
+ * the SELL-32 kernel (a test mode: it allocates and synchronises; handles are unaffected).
+ * Rows longer on average always use the TMA kernel with large stages. Returns the previous
+ * setting, or INVALID_ARG. Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 
 /* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined, 4

@@ -41,7 +41,7 @@ class bjac_policy(C.Structure):
                 ("fp64_fallback", C.c_int32), ("adp_tol", C.c_double), ("theta", C.c_double),
                 ("safety_theta", C.c_double), ("mlp_params", C.c_void_p), ("block_fmt", C.c_void_p),
                 ("apply_variant", C.c_int32),
-                ("graph_mode", C.c_int32), ("stream", C.c_void_p)]
+                ("graph_mode", C.c_int32), ("spmv_format", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pcg_stats(C.Structure):
@@ -89,6 +89,9 @@ def lib():
                 "bjac_mlp_grad": (C.c_int, [P, i32, P, P, i32, P, P, P]),
                 "bjac_mlp_train": (C.c_int, [P, P, P, i32, i32, C.c_float, P, P]),
                 "bjac_mlp_logits": (C.c_int, [P, i32, P, i32, P, P]),
+                "bjac_handle_spmv": (C.c_int, [P, P, P, P]),
+                "bjac_spmv_format": (C.c_int, [P, C.POINTER(i32), C.POINTER(i64), P]),
+                "bjac_convert": (C.c_int, [P, P, P, i32, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -166,13 +169,14 @@ def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
 
 def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp_tol=10.0, theta=0.1,
                 safety_theta=0.5, fp64_fallback=False, mlp_params=None, block_fmt=None, apply_variant=0,
-                graph_mode=0, stream=None):
+                graph_mode=0, spmv_format=0, stream=None):
     p = bjac_policy()
     p.select, p.fixed_fmt, p.temporal = select, fixed_fmt, temporal
     p.fp64_fallback = int(bool(fp64_fallback))
     p.adp_tol, p.theta, p.safety_theta = adp_tol, theta, safety_theta
     p.apply_variant = apply_variant
     p.graph_mode = graph_mode
+    p.spmv_format = spmv_format
     p._mlp_keep = None
     if mlp_params is not None:
         arr = np.ascontiguousarray(mlp_params, dtype=np.float32)
@@ -241,6 +245,19 @@ class Handle:
         _require_cuda(r, z, rz)
         _check(lib().bjac_apply(self.h, set, _ptr(r), _ptr(z), _ptr(rz)))
 
+    def spmv(self, x, y, xy=None):
+        """y = A x (and xy[0] = x . y) in the layout the handle's PCG loop uses."""
+        _require_cuda(x, y, xy)
+        _check(lib().bjac_handle_spmv(self.h, _ptr(x), _ptr(y), _ptr(xy)))
+
+    def spmv_format(self):
+        """Layout of the loop SpMV: dict(format 'csr' | 'sell32', stored SELL-32 entries,
+        timed ms of y = A x in the CSR and SELL-32 layouts)."""
+        f, e = C.c_int32(), C.c_int64()
+        ms = (C.c_float * 2)()
+        _check(lib().bjac_spmv_format(self.h, C.byref(f), C.byref(e), ms))
+        return dict(format="sell32" if f.value else "csr", entries=e.value, ms=list(ms))
+
     def apply_kernel(self):
         """(kernel name, autotuner timings in ms) of the low-precision apply."""
         k = C.c_int32()
@@ -276,6 +293,16 @@ def bjac_setup(A: DeviceCSR, block_ptr, policy=None, **kw) -> Handle:
 
 def pcg_solve(h: Handle, b, x, tol=1e-10, maxit=1000, hist=None):
     return h.solve(b, x, tol, maxit, hist)
+
+
+def bjac_convert(x, stream=None):
+    """(f, w): x (CUDA float64) rounded to binary32 by the library's integer routine, and f
+    widened back to binary64 the same way."""
+    _require_cuda(x)
+    f = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    w = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _check(lib().bjac_convert(_ptr(x), _ptr(f), _ptr(w), x.numel(), _stream(stream)))
+    return f, w
 
 
 def bjac_mlp_param_count() -> int:

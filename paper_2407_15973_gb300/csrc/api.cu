@@ -12,7 +12,9 @@
 #include "apply.cuh"
 #include "common.cuh"
 #include "mlp.cuh"
+#include "sell.cuh"
 #include "setup.cuh"
+#include "spmv.cuh"
 
 namespace mpbjac {
 
@@ -149,6 +151,16 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, run ? 1u : 0u);
 }
 
+// element-wise f = RNE binary32 of x and w = f widened back, both by the integer routines the
+// apply kernels use
+__global__ void k_convert(int n, const double *__restrict__ x, float *__restrict__ f, double *__restrict__ w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = f64_to_f32_rn(x[i]);
+        if (f) f[i] = v;
+        if (w) w[i] = f32_to_f64(v);
+    }
+}
+
 __global__ void k_zero_if_zero_rhs(int n, SolverState *S) {
     if (S->bnorm != 0.0) return;
     double *x = S->x;
@@ -209,6 +221,9 @@ struct bjac_handle {
     int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
     int apply_kind = kApplyKindGeneric;   // kernel used for the low-precision set
     float tune_ms[3] = {0, 0, 0};         // autotuner timings (generic, TMA, register)
+    SellMat sell{};                       // SELL-32 copy of A (val NULL if not kept)
+    int use_sell = 0;                     // loop SpMV on the SELL-32 copy
+    float spmv_ms[2] = {0, 0};            // timed y = A x: CSR, SELL-32
 };
 
 static void free_handle(bjac_handle *h) {
@@ -223,6 +238,7 @@ static void free_handle(bjac_handle *h) {
                     h->d_p, h->d_q, h->d_x0, h->d_part, h->d_S};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    sell_free(&h->sell);
     if (h->h_S) cudaFreeHost(h->h_S);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -353,6 +369,83 @@ static int choose_apply_kind(bjac_handle *h) {
     return MPBJAC_OK;
 }
 
+// Layout of the loop SpMV. policy.spmv_format 1 keeps the caller's CSR arrays and 2 always
+// builds the SELL-32 copy. By default the copy is built when its padding stays under 1.5 nnz
+// and y = A x is timed in both layouts (interleaved rounds on a nonzero x, median of 7 after
+// a warm-up round, on the handle's stream); the faster is kept, and the decision is cached
+// per (n, nnz) for the life of the process. Both layouts give the same result bits.
+struct SpFmtTune {
+    int n, nnz, sell;
+    float ms[2];
+};
+static std::vector<SpFmtTune> g_spfmt_cache;
+
+static int choose_spmv_format(bjac_handle *h) {
+    const int f = h->pol.spmv_format;
+    cudaStream_t st = h->stream;
+    h->use_sell = 0;
+    if (f == 1) return MPBJAC_OK;
+    if (f == 0) {
+        for (const SpFmtTune &t : g_spfmt_cache)
+            if (t.n == h->A.n && t.nnz == h->A.nnz) {
+                h->spmv_ms[0] = t.ms[0];
+                h->spmv_ms[1] = t.ms[1];
+                if (!t.sell) return MPBJAC_OK;
+                int rc = sell_build(h->A, 1.5, &h->sell, st);
+                if (rc) return rc;
+                h->use_sell = h->sell.val != nullptr;
+                return MPBJAC_OK;
+            }
+    }
+    int rc = sell_build(h->A, f == 2 ? 0.0 : 1.5, &h->sell, st);
+    if (rc) return rc;
+    if (!h->sell.val) {
+        if (f == 2) return fail(MPBJAC_ERR_UNSUPPORTED, "A needs more than 2^31 stored SELL-32 entries");
+        g_spfmt_cache.push_back({h->A.n, h->A.nnz, 0, {0.0f, 0.0f}});
+        return MPBJAC_OK;
+    }
+    if (f == 2) {
+        h->use_sell = 1;
+        return MPBJAC_OK;
+    }
+    double *x = h->d_p, *y = h->d_q;
+    MPB_CUDA(cudaMemsetAsync(x, 0x3F, sizeof(double) * h->n, st));     // every entry about 4.8e-4
+    cudaEvent_t e0, e1;
+    MPB_CUDA(cudaEventCreate(&e0));
+    MPB_CUDA(cudaEventCreate(&e1));
+    constexpr int kRounds = 8;
+    float t[2][kRounds] = {};
+    for (int rep = 0; rep < kRounds; ++rep) {
+        for (int k = 0; k < 2; ++k) {
+            MPB_CUDA(cudaEventRecord(e0, st));
+            rc = k == 0 ? launch_spmv(h->A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st)
+                        : launch_spmv_sell(h->sell, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, kSpY, st);
+            if (rc) return rc;
+            MPB_CUDA(cudaEventRecord(e1, st));
+            MPB_CUDA(cudaEventSynchronize(e1));
+            cudaEventElapsedTime(&t[k][rep], e0, e1);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int k = 0; k < 2; ++k) {
+        std::sort(t[k] + 1, t[k] + kRounds);
+        h->spmv_ms[k] = t[k][1 + (kRounds - 1) / 2];
+    }
+    h->use_sell = h->spmv_ms[1] < h->spmv_ms[0];
+    if (!h->use_sell) sell_free(&h->sell);
+    g_spfmt_cache.push_back({h->A.n, h->A.nnz, h->use_sell, {h->spmv_ms[0], h->spmv_ms[1]}});
+    return MPBJAC_OK;
+}
+
+// the loop SpMV (q = A p, sigma = p.q, alpha) in the handle's layout
+static int launch_loop_spmv(const bjac_handle *h, cudaStream_t st) {
+    unsigned int *ticket = &h->d_S->tickets[kTicketSpmv];
+    if (h->use_sell)
+        return launch_spmv_sell(h->sell, h->d_p, nullptr, h->d_q, h->d_part, ticket, nullptr, h->d_S, kSpPcg, st);
+    return launch_spmv(h->A, h->d_p, h->d_q, h->d_part, ticket, nullptr, h->d_S, 2, st);
+}
+
 extern "C" {
 
 const char *bjac_last_error(void) { return g_err.c_str(); }
@@ -392,6 +485,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_MLP needs mlp_params");
     if (P.temporal != BJAC_TEMPORAL_NONE && P.select == BJAC_SELECT_UNIFORM)
         return fail(MPBJAC_ERR_INVALID_ARG, "aMP switching needs a low-precision set");
+    if (P.spmv_format < 0 || P.spmv_format > 2) return fail(MPBJAC_ERR_INVALID_ARG, "spmv_format must be 0, 1 or 2");
 
     bjac_handle *h = new bjac_handle();
     h->A = *A;
@@ -560,6 +654,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     memset(h->h_S, 0, sizeof(SolverState));
     MPB_TRY(cudaMemsetAsync(h->d_S, 0, sizeof(SolverState), st) == cudaSuccess
                 ? 0 : cuda_fail(cudaGetLastError(), "memset"));
+    MPB_TRY(choose_spmv_format(h));
     MPB_TRY(cudaEventRecord(h->ev1, st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "event"));
     MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "setup"));
     cudaEventElapsedTime(&h->setup_ms, h->ev0, h->ev1);
@@ -624,7 +719,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     const bool temporal = (which == 0) && h->pol.temporal != BJAC_TEMPORAL_NONE;
     const bool use_low = (which == 0) && h->have_lo;
     if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
-    int rc = launch_spmv(h->A, h->d_p, h->d_q, h->d_part, &h->d_S->tickets[kTicketSpmv], nullptr, h->d_S, 2, cs);
+    int rc = launch_loop_spmv(h, cs);
     if (rc) return rc;
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
     if (temporal) {
@@ -792,6 +887,21 @@ extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol,
 // ------------------------------------------------------------------------------------------
 // single steps
 // ------------------------------------------------------------------------------------------
+// standalone SpMV kinds on a SELL-32 copy built for this call alone (bjac_spmv_kernel(5),
+// for tests of the layout on any matrix); synchronises the stream before freeing the copy
+static int sell_once(const bjac_csr &A, int kind, const double *x, const double *b, double *y, double *part,
+                     unsigned int *ticket, double *out, cudaStream_t st) {
+    SellMat m;
+    int rc = sell_build(A, 0.0, &m, st);
+    if (rc) return rc;
+    if (!m.val) return fail(MPBJAC_ERR_UNSUPPORTED, "A needs more than 2^31 stored SELL-32 entries");
+    rc = launch_spmv_sell(m, x, b, y, part, ticket, out, nullptr, kind, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    sell_free(&m);
+    if (rc) return rc;
+    return e == cudaSuccess ? MPBJAC_OK : cuda_fail(e, "SELL-32 SpMV");
+}
+
 extern "C" int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *stream) {
     int rc = check_csr_host(A);
     if (rc) return rc;
@@ -799,7 +909,11 @@ extern "C" int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *
     cudaStream_t st = (cudaStream_t)stream;
     rc = prepare_spmv(*A);
     if (rc) return rc;
-    if (!xy) return launch_spmv(*A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st);
+    const bool sell = spmv_forced_sell();
+    if (!xy) {
+        if (sell) return sell_once(*A, kSpY, x, nullptr, y, nullptr, nullptr, nullptr, st);
+        return launch_spmv(*A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st);
+    }
     // scratch for the deterministic reduction: partial sums and a ticket counter
     void *scratch = nullptr;
     const size_t bytes = sizeof(double) * kMaxGrid + 256;
@@ -807,7 +921,8 @@ extern "C" int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *
     double *part = static_cast<double *>(scratch);
     unsigned int *ticket = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * kMaxGrid);
     MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
-    rc = launch_spmv(*A, x, y, part, ticket, xy, nullptr, 1, st);
+    rc = sell ? sell_once(*A, kSpYDot, x, nullptr, y, part, ticket, xy, st)
+              : launch_spmv(*A, x, y, part, ticket, xy, nullptr, 1, st);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -828,7 +943,8 @@ extern "C" int bjac_residual(const bjac_csr *A, const double *b, const double *x
         reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * 2 * kMaxGrid);
     double *dummy = reinterpret_cast<double *>(static_cast<char *>(scratch) + sizeof(double) * 2 * kMaxGrid + 64);
     MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
-    rc = launch_residual(*A, b, x, r, part, ticket, rr ? rr : dummy, nullptr, 0, st);
+    rc = spmv_forced_sell() ? sell_once(*A, kResStandalone, x, b, r, part, ticket, rr ? rr : dummy, st)
+                            : launch_residual(*A, b, x, r, part, ticket, rr ? rr : dummy, nullptr, 0, st);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -854,6 +970,35 @@ extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *
     }
     return launch_apply_generic(kApplyStandalone, h->have_lo ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                 nullptr, h->stream);
+}
+
+extern "C" int bjac_handle_spmv(bjac_handle *h, const double *x, double *y, double *xy) {
+    if (!h || !x || !y) return fail(MPBJAC_ERR_INVALID_ARG, "handle, x and y must be non-NULL");
+    unsigned int *ticket = &h->d_S->tickets[kTicketSpmv];
+    const int mode = xy ? 1 : 0;
+    if (h->use_sell)
+        return launch_spmv_sell(h->sell, x, nullptr, y, h->d_part, ticket, xy, nullptr, mode ? kSpYDot : kSpY,
+                                h->stream);
+    return launch_spmv(h->A, x, y, h->d_part, ticket, xy, nullptr, mode, h->stream);
+}
+
+extern "C" int bjac_convert(const double *x, float *f, double *w, int32_t n, void *stream) {
+    if (n < 0 || (n > 0 && !x)) return fail(MPBJAC_ERR_INVALID_ARG, "need n >= 0 and x");
+    if (n == 0) return MPBJAC_OK;
+    k_convert<<<vec_grid(n), kNT, 0, (cudaStream_t)stream>>>(n, x, f, w);
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_spmv_format(const bjac_handle *h, int32_t *format, int64_t *entries, float *ms) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    if (format) *format = h->use_sell;
+    if (entries) *entries = h->use_sell ? h->sell.entries : 0;
+    if (ms) {
+        ms[0] = h->spmv_ms[0];
+        ms[1] = h->spmv_ms[1];
+    }
+    return MPBJAC_OK;
 }
 
 extern "C" int bjac_info(const bjac_handle *h, int32_t *nb, int64_t *pool_bytes, int64_t *g_entries) {

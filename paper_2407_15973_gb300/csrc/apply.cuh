@@ -33,6 +33,7 @@ int launch_apply_reg(int mode, const PSet &P, const ApplyIO &io, SolverState *S,
 int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S,
                          cudaStream_t st);
 
+bool spmv_forced_sell();                // bjac_spmv_kernel(5): standalone calls use a SELL-32 copy
 int prepare_spmv(const bjac_csr &A);    // kernel attributes for A's SpMV variant (before any capture)
 int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, unsigned int *ticket,
                 double *dot_out, SolverState *S, int mode, cudaStream_t st);

@@ -143,34 +143,65 @@ __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0
 namespace mpbjac {
 
 // ----------------------------------------------------------------------------------------
-// binary64 <-> binary32 conversions done with integer operations, so that they do not use
-// the (narrow) FP64 pipe of sm_103a. Written from the IEEE 754 bit layouts:
+// binary64 <-> binary32 conversions done with integer operations only, so that they take no
+// slot of the (narrow) FP64 pipe of sm_103a. Written from the IEEE 754 bit layouts:
 //   binary64 = sign | 11-bit exponent (bias 1023) | 52-bit fraction
 //   binary32 = sign | 8-bit exponent (bias 127)   | 23-bit fraction
-// Inputs outside the normal binary32 range (zero, subnormal, overflow, inf, NaN) take the
-// hardware conversion instead; results are identical to round-to-nearest-even.
+// Every input class is handled (zeros, subnormal results, overflow, infinities, NaN);
+// finite results are round-to-nearest-even with subnormals kept, i.e. the correctly
+// rounded value. A NaN stays a quiet NaN that keeps the top payload bits.
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ float f64_to_f32_rn(double d) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned int sign = (unsigned int)(u >> 63) << 31;
     const int e = (int)((u >> 52) & 0x7FF);
-    if (e < 1023 - 126 || e > 1023 + 127) return __double2float_rn(d);
     const unsigned long long frac = u & 0xFFFFFFFFFFFFFull;
-    unsigned int r = ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(frac >> 29);
-    const unsigned int rem = (unsigned int)(frac & 0x1FFFFFFFu);     // the 29 dropped bits
-    const unsigned int half = 0x10000000u;
-    r += (rem > half) | ((rem == half) & (r & 1u));                   // carry may reach the exponent
-    return __uint_as_float(((unsigned int)(u >> 63) << 31) | r);
+    unsigned int r;
+    if (e == 0x7FF) {                                   // infinity or NaN
+        r = 0x7F800000u | (frac ? (0x400000u | (unsigned int)(frac >> 29)) : 0u);
+    } else if (e > 1023 + 127) {                        // beyond the binary32 range: infinity
+        r = 0x7F800000u;
+    } else if (e >= 1023 - 126) {                       // normal binary32 result
+        r = ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(frac >> 29);
+        const unsigned int rem = (unsigned int)(frac & 0x1FFFFFFFu);   // the 29 dropped bits
+        const unsigned int half = 0x10000000u;
+        r += (rem > half) | ((rem == half) & (r & 1u));               // carry may reach the exponent
+    } else if (e == 0) {                                // binary64 zero or subnormal: below 2^-1022
+        r = 0u;
+    } else {
+        // binary32 subnormal or zero: |d| = M 2^(e - 1075) with M = 2^52 + frac, i.e.
+        // M 2^-(926 - e) units of 2^-149; shift by 926 - e > 29 and round to nearest even
+        const int sh = 926 - e;
+        if (sh > 54) {
+            r = 0u;                                     // below half of 2^-149
+        } else {
+            const unsigned long long M = frac | (1ull << 52);
+            const unsigned long long q = M >> sh;
+            const unsigned long long rem = M & ((1ull << sh) - 1ull);
+            const unsigned long long half = 1ull << (sh - 1);
+            r = (unsigned int)q + (unsigned int)((rem > half) | ((rem == half) & (q & 1ull)));
+        }
+    }
+    return __uint_as_float(sign | r);
 }
 
 __device__ __forceinline__ double f32_to_f64(float f) {
     const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFFu;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);   // +-0
-    if (e == 0u || e == 0xFFu) return (double)f;                                  // subnormal, inf, NaN
-    const unsigned long long bits = sign | ((unsigned long long)(e + 1023u - 127u) << 52) |
-                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)bits);
+    const unsigned int e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    unsigned long long bits;
+    if (e == 0xFFu) {                                   // infinity or NaN (payload kept)
+        bits = 0x7FF0000000000000ull | ((unsigned long long)m << 29);
+    } else if (e != 0u) {                               // normal
+        bits = ((unsigned long long)(e + 1023u - 127u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {                               // zero
+        bits = 0ull;
+    } else {                                            // subnormal m 2^-149: normalise
+        const int p = 31 - __clz((int)m);               // leading bit, 0..22
+        bits = ((unsigned long long)(p - 149 + 1023) << 52) |
+               (((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
+    return __longlong_as_double((long long)(sign | bits));
 }
 
 }  // namespace mpbjac

@@ -10,6 +10,7 @@
 // unaligned tail of the arrays, is read straight from global memory instead. Every wait
 // is bounded.
 #include "common.cuh"
+#include "spmv.cuh"
 #include "tma.cuh"
 
 #include <algorithm>
@@ -17,7 +18,6 @@
 
 namespace mpbjac {
 
-constexpr int kSpNT = 256;               // threads per CTA = rows per tile
 
 template <int CAP, int NST>
 struct SpGeo {
@@ -29,60 +29,10 @@ struct SpGeo {
 using SpShort = SpGeo<2048, 3>;   // rows of up to ~8 nonzeros
 using SpLong = SpGeo<8192, 2>;    // longer rows (27-point stencils)
 
-enum SpmvKind {
-    kSpY = 0,         // y = A x
-    kSpYDot = 1,      // y = A x, *out = x . y
-    kSpPcg = 2,       // PCG: q = A p, sigma = p . q, alpha = rho / sigma
-    kResStandalone = 10,  // r = b - A x, *out = r . r
-    kResStart = 11,       // PCG start: bnorm, relres, state
-    kResCheck = 12,       // true residual after the loop; restart decision
-};
-
 struct StageMeta {
     int lo4;      // first staged nonzero (multiple of 4)
     int direct;   // 1: this tile is read from global memory
 };
-
-template <int KIND>
-__device__ __forceinline__ void spmv_finish(double t1, double t2, double *out, SolverState *S) {
-    if (KIND == kSpYDot || KIND == kResStandalone) {
-        *out = t1;
-    } else if (KIND == kSpPcg) {
-        S->x_pending = 0;      // set again once this iteration updates r
-        S->sigma = t1;
-        if (!finite_pos(t1)) S->state = kBreakdownSigma;
-        else S->alpha = S->rho / t1;
-    } else if (KIND == kResStart) {
-        const double bnorm = sqrt(t2);
-        S->bnorm = bnorm;
-        S->x_pending = 0;
-        if (bnorm == 0.0) {
-            S->relres = 0.0;
-            S->true_relres = 0.0;
-            S->state = kConverged;      // x is zeroed by the host
-            return;
-        }
-        const double rel = sqrt(t1) / bnorm;
-        S->relres = rel;
-        S->true_relres = rel;
-        if (S->hist) S->hist[S->iter] = rel;
-        if (!(rel < 1.0e308)) S->state = kBreakdown;
-        else if (rel <= S->tol) S->state = kConverged;
-        else if (S->iter >= S->maxit) S->state = kMaxit;
-        else S->state = kRunning;
-        S->use_low = choose_low(S, rel);
-    } else {   // kResCheck
-        const double rel = S->bnorm > 0.0 ? sqrt(t1) / S->bnorm : 0.0;
-        S->true_relres = rel;
-        S->x_pending = 0;
-        if (S->state == kConverged && rel > S->tol && S->iter < S->maxit && S->restarts < 8) {
-            S->state = kRunning;          // restart from r = b - A x
-            S->restarts += 1;
-            S->relres = rel;
-            S->use_low = choose_low(S, rel);
-        }
-    }
-}
 
 template <int CAP, int NST, int KIND>
 __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *__restrict__ rowptr,
@@ -679,7 +629,11 @@ struct SpTune {
 };
 static std::vector<SpTune> g_sp_tune;
 
-static int g_sp_force = 0;   // 0 timed choice, 1 TMA-staged, 2 warp-cooperative, 3 pipelined warp, 4 per-warp TMA
+// 0 timed choice, 1 TMA-staged, 2 warp-cooperative, 3 pipelined warp, 4 per-warp TMA,
+// 5 SELL-32 copy built per call by the standalone entry points (the CSR kernels keep the
+// timed choice)
+static int g_sp_force = 0;
+bool spmv_forced_sell() { return g_sp_force == 5; }
 
 static int spmv_variant(const bjac_csr &A) {
     if (long_rows(A)) return kSpVarTma;
@@ -853,7 +807,7 @@ extern "C" int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms) 
 }
 
 extern "C" int bjac_spmv_kernel(int32_t variant) {
-    if (variant < 0 || variant > 4) return mpbjac::fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..4");
+    if (variant < 0 || variant > 5) return mpbjac::fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..5");
     const int old = mpbjac::g_sp_force;
     mpbjac::g_sp_force = variant;
     return old;

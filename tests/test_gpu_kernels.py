@@ -57,7 +57,7 @@ def test_spmv_integer_exact(B):
     assert host(xy)[0] == float(np.dot(x, ref))    # integers below 2^53: exact in any order
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("case", list(SPMV_CASES))
 def test_spmv_parity(B, case, variant):
     A = SPMV_CASES[case]()
@@ -78,6 +78,68 @@ def test_spmv_parity(B, case, variant):
     assert np.max(np.abs(got - ref)) <= spmv_tol(A, x)
     assert abs(host(xy)[0] - O.dot(x, ref)) <= 1e-14 * np.sum(np.abs(x * ref)) + 1e-300
     assert np.max(np.abs(res)) <= spmv_tol(A, x)
+
+
+@pytest.mark.parametrize("case", list(SPMV_CASES))
+def test_spmv_layouts_bitwise_equal(B, case):
+    """Every SpMV kernel (four CSR kernels, the SELL-32 copy) sums each row as the same FMA
+    chain in CSR order, so all give the same bits."""
+    A = SPMV_CASES[case]()
+    x = cuda(PB.solution(A.n, 23))
+    dA = B.DeviceCSR(A)
+    outs = []
+    for variant in (1, 2, 3, 4, 5):
+        y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+        old = B.bjac_spmv_kernel(variant)
+        try:
+            B.bjac_spmv(dA, x, y)
+        finally:
+            B.bjac_spmv_kernel(old)
+        outs.append(host(y))
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint64), outs[0].view(np.uint64))
+
+
+def _conversion_inputs():
+    f32 = np.finfo(np.float32)
+    tiny = float(f32.smallest_subnormal)
+    vals = [0.0, -0.0, 1.0, -1.0, np.pi, 1.0 / 3.0, float(f32.max), -float(f32.max),
+            float(f32.max) * (1 + 2.0 ** -25), float(f32.max) * (1 + 2.0 ** -24), 2.0 ** 128, 1e300, -1e300,
+            float(f32.tiny), float(f32.tiny) * (1 - 2.0 ** -30), tiny, tiny * 0.5, tiny * 0.5000001, tiny * 1.5,
+            tiny * 2.5, tiny * 0.49, 1e-50, -1e-50, 5e-324, -5e-324, 2.2250738585072014e-308,
+            np.inf, -np.inf, np.nan,
+            1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 1.0 + 2.0 ** -24 + 2.0 ** -52, 1.0 - 2.0 ** -25]
+    rng = np.random.default_rng(11)
+    mag = 10.0 ** rng.uniform(-50, 40, 4000)
+    rand = mag * rng.choice([-1.0, 1.0], 4000)
+    sub = rng.integers(1, 2 ** 23, 2000) * tiny * rng.uniform(0.5, 1.5, 2000)    # around binary32 subnormals
+    return np.concatenate([np.array(vals), rand, sub])
+
+
+def test_integer_conversions_match_hardware_and_oracle(B):
+    """The apply kernels' integer-only binary64 -> binary32 rounding and widening agree bit for
+    bit with the hardware conversion and with the oracle's rounding (written independently
+    from the IEEE 754 layout), across normal, subnormal, overflowing, infinite and NaN inputs."""
+    x = _conversion_inputs()
+    dx = cuda(x)
+    f, w = B.bjac_convert(dx)
+    fb = host(f).view(np.uint32)
+    hw = host(dx.to(torch.float32)).view(np.uint32)
+    nan = np.isnan(x)
+    assert np.array_equal(fb[~nan], hw[~nan])
+    assert np.all(np.isnan(host(f)[nan]))
+    orc = O.round_bits(O.FP32, x)
+    assert np.array_equal(fb[~nan], orc[~nan])
+    wb = host(w)
+    assert np.array_equal(wb[~nan].view(np.uint64), host(f.to(torch.float64))[~nan].view(np.uint64))
+    assert np.all(np.isnan(wb[nan]))
+    # widening alone: every binary32 class, including subnormal inputs
+    fin = np.concatenate([np.array([0.0, -0.0, np.inf, -np.inf], np.float32),
+                          (np.arange(1, 4096, dtype=np.uint32) * 2047).view(np.float32),
+                          np.random.default_rng(12).standard_normal(3000).astype(np.float32) * 1e30])
+    f2, w2 = B.bjac_convert(cuda(fin.astype(np.float64)))
+    assert np.array_equal(host(f2).view(np.uint32), fin.view(np.uint32))
+    assert np.array_equal(host(w2).view(np.uint64), fin.astype(np.float64).view(np.uint64))
 
 
 def test_residual_parity(B):
