@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
     ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
                     help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
-    ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell"],
+    ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell", "sell-pf"],
                     help="pin the loop SpMV's matrix layout instead of the timed choice")
     ap.add_argument("--apply-kernel", default="auto", choices=["auto", "generic", "tma", "reg"],
                     help="pin the low-precision apply kernel instead of the timed choice")
@@ -206,7 +206,7 @@ def run_ours(args, rank, world, dist):
     spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
     B.bjac_spmv_kernel(spmv_pin)
     apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3}[args.apply_kernel]
-    layout_pin = {"auto": 0, "csr": 1, "sell": 2}[args.spmv_layout]
+    layout_pin = {"auto": 0, "csr": 1, "sell": 2, "sell-pf": 3}[args.spmv_layout]
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
                 graph_mode=1 if args.eager else 0, spmv_format=layout_pin)
     if args.profile_iters:
@@ -282,7 +282,7 @@ def run_ours(args, rank, world, dist):
         spmv_var[name] = round(ev0.elapsed_time(ev1) / 20, 5)
     # the loop SpMV in both layouts through handles (y = A x with the dot, standalone launches)
     layout_ms = {}
-    for name, fmt_pin in (("csr", 1), ("sell32", 2)):
+    for name, fmt_pin in (("csr", 1), ("sell32", 2), ("sell32-prefetch", 3)):
         hl = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], spmv_format=fmt_pin)
         for _ in range(3):
             hl.spmv(xs, yv, xy)
@@ -297,7 +297,7 @@ def run_ours(args, rank, world, dist):
     apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg"}[apply_kernel]
     csr_name = {"tma": "k_spmv", "warp": "k_spmv_warp", "pipe": "k_spmv_pipe", "wtma": "k_spmv_wtma"}[
         B.bjac_spmv_tuning(dA)[0]]
-    spmv_name = "k_spmv_sell" if layout["format"] == "sell32" else csr_name
+    spmv_name = {"sell32": "k_spmv_sell", "sell32-prefetch": "k_spmv_sell_pf"}.get(layout["format"], csr_name)
     kernel_name = {"spmv": spmv_name, "apply": apply_name, "update_xp": "k_update_xp"}[dom]
     roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
@@ -308,8 +308,8 @@ def run_ours(args, rank, world, dist):
                 "apply_kernel": apply_name,
                 "spmv_kernel_name": spmv_name,
                 "spmv_layout": {"format": layout["format"], "stored_entries": layout["entries"],
-                                "setup_timing_ms": {"csr": round(layout["ms"][0], 4),
-                                                    "sell32": round(layout["ms"][1], 4)},
+                                "setup_timing_ms": dict(zip(("csr", "sell32", "sell32-prefetch"),
+                                                            [round(t, 4) for t in layout["ms"]])),
                                 "standalone_ms": layout_ms},
                 "spmv_variant_ms": spmv_var,
                 "spmv_kernel": B.bjac_spmv_tuning(dA)[0],
@@ -351,8 +351,8 @@ def run_ours(args, rank, world, dist):
     d2h = n * 8
 
     setup_kernels = 2 + (0 if head["select"] in (B.SELECT_FIXED, B.SELECT_UNIFORM) else 1)
-    setup_kernels += 3 if layout["format"] == "sell32" else 0       # slice lengths, scan, fill
-    per_step = [setup_kernels + 3 + 3 * s["iters"] + 1 for s in st_mixed]
+    setup_kernels += 3 if layout["format"] != "csr" else 0       # slice lengths, scan, fill
+    per_step = [setup_kernels + s["kernel_launches"] for s in st_mixed]     # setup + the solve's own count
     out = {
         "metric": METRIC, "value": round(ms_mixed, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_mixed, 4), "higher_is_better": False,

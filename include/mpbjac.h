@@ -92,9 +92,11 @@ typedef struct bjac_policy {
                                batches of 32 iterations and checks the state between batches */
     int32_t spmv_format;    /* matrix layout of the loop SpMV q = A p: 0 chosen at setup (a
                                SELL-32 copy is built when its padding stays under 1.5 nnz,
-                               both layouts are timed once per matrix shape and the faster is
-                               kept), 1 the caller's CSR arrays, 2 always the SELL-32 copy.
-                               Either layout sums every row in CSR order: same result bits. */
+                               the CSR kernel and both SELL-32 kernels are timed once per
+                               matrix shape and the fastest is kept), 1 the caller's CSR
+                               arrays, 2 the SELL-32 copy, one slice at a time per warp, 3 the
+                               SELL-32 copy with the next slice's first entries prefetched.
+                               Every layout sums each row in CSR order: same result bits.  */
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
 
@@ -113,6 +115,9 @@ typedef struct pcg_stats {
     int32_t blocks_per_fmt[4];
     float setup_ms;         /* time of bjac_setup (copied from the handle)                */
     float solve_ms;         /* device time of this solve (CUDA events on the stream)      */
+    int32_t kernel_launches;/* kernels of this library the solve launched (the loop body's
+                               copies that ran after convergence, which return at once,
+                               included)                                                  */
 } pcg_stats;
 
 typedef struct bjac_handle bjac_handle;
@@ -225,9 +230,9 @@ int bjac_convert(const double *x, float *f, double *w, int32_t n, void *stream);
 
 /* Layout of the loop SpMV (HOST outputs, each nullable): *format 0 = CSR arrays of the
  * caller, 1 = SELL-32 copy (slices of 32 rows padded to the slice's longest row, stored
- * column-major); *entries = stored entries of the SELL-32 copy including padding (0 if none
- * was kept); ms[2] = median times of one y = A x in the CSR and SELL-32 layouts when the
- * setup timed them (else 0). */
+ * column-major), 2 = the SELL-32 copy with prefetch; *entries = stored entries of the SELL-32
+ * copy including padding (0 if none was kept); ms[3] = median times of one y = A x with the
+ * CSR kernel and the two SELL-32 kernels when the setup timed them (else 0). */
 int bjac_spmv_format(const bjac_handle *h, int32_t *format, int64_t *entries, float *ms);
 
 /* Sizes: nb, bytes of the low-precision pool, entries of the binary64 pool (0 if not kept). */

@@ -48,7 +48,8 @@ class pcg_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("status", C.c_int32), ("restarts", C.c_int32),
                 ("fallback_used", C.c_int32), ("low_applies", C.c_int32), ("high_applies", C.c_int32),
                 ("graph_launches", C.c_int32), ("relres", C.c_double), ("true_relres", C.c_double),
-                ("blocks_per_fmt", C.c_int32 * 4), ("setup_ms", C.c_float), ("solve_ms", C.c_float)]
+                ("blocks_per_fmt", C.c_int32 * 4), ("setup_ms", C.c_float), ("solve_ms", C.c_float),
+                ("kernel_launches", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -231,7 +232,7 @@ class Handle:
                     fallback_used=bool(st.fallback_used), low_applies=st.low_applies,
                     high_applies=st.high_applies, graph_launches=st.graph_launches, relres=st.relres,
                     true_relres=st.true_relres, blocks_per_fmt=list(st.blocks_per_fmt),
-                    setup_ms=st.setup_ms, solve_ms=st.solve_ms)
+                    setup_ms=st.setup_ms, solve_ms=st.solve_ms, kernel_launches=st.kernel_launches)
 
     def profile(self, b, x, tol=1e-10, maxit=1000):
         """Per-kernel mean milliseconds of one PCG iteration (eager launches, CUDA events)."""
@@ -251,12 +252,12 @@ class Handle:
         _check(lib().bjac_handle_spmv(self.h, _ptr(x), _ptr(y), _ptr(xy)))
 
     def spmv_format(self):
-        """Layout of the loop SpMV: dict(format 'csr' | 'sell32', stored SELL-32 entries,
-        timed ms of y = A x in the CSR and SELL-32 layouts)."""
+        """Layout of the loop SpMV: dict(format 'csr' | 'sell32' | 'sell32-prefetch', stored
+        SELL-32 entries, timed ms of y = A x with the CSR and the two SELL-32 kernels)."""
         f, e = C.c_int32(), C.c_int64()
-        ms = (C.c_float * 2)()
+        ms = (C.c_float * 3)()
         _check(lib().bjac_spmv_format(self.h, C.byref(f), C.byref(e), ms))
-        return dict(format="sell32" if f.value else "csr", entries=e.value, ms=list(ms))
+        return dict(format={0: "csr", 1: "sell32", 2: "sell32-prefetch"}[f.value], entries=e.value, ms=list(ms))
 
     def apply_kernel(self):
         """(kernel name, autotuner timings in ms) of the low-precision apply."""

@@ -67,6 +67,7 @@ static int vec_grid2(int n) {
 // preconditioner application (Algorithms 3.2 / 3.3 read this relres). r, q: 16-byte aligned.
 __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
                                                   double *part, SolverState *S) {
+    pdl_enter();
     __shared__ double red[kWarps];
     if (S->state != kRunning) return;
     const double alpha = S->alpha;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
 // SpMV). z and p are 16-byte aligned (handle memory); x is the caller's vector and is checked.
 __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
+    pdl_enter();
     const int xp = S->x_pending;
     const int run = S->state == kRunning;
     double *__restrict__ x = S->x;
@@ -223,7 +225,9 @@ struct bjac_handle {
     float tune_ms[3] = {0, 0, 0};         // autotuner timings (generic, TMA, register)
     SellMat sell{};                       // SELL-32 copy of A (val NULL if not kept)
     int use_sell = 0;                     // loop SpMV on the SELL-32 copy
-    float spmv_ms[2] = {0, 0};            // timed y = A x: CSR, SELL-32
+    float spmv_ms[3] = {0, 0, 0};         // timed y = A x: CSR, SELL-32, SELL-32 with prefetch
+    int body_launches[2] = {0, 0};        // kernels in one body of each solve graph
+    long long launches = 0;               // kernels launched by the last solve
 };
 
 static void free_handle(bjac_handle *h) {
@@ -369,14 +373,16 @@ static int choose_apply_kind(bjac_handle *h) {
     return MPBJAC_OK;
 }
 
-// Layout of the loop SpMV. policy.spmv_format 1 keeps the caller's CSR arrays and 2 always
-// builds the SELL-32 copy. By default the copy is built when its padding stays under 1.5 nnz
-// and y = A x is timed in both layouts (interleaved rounds on a nonzero x, median of 7 after
-// a warm-up round, on the handle's stream); the faster is kept, and the decision is cached
-// per (n, nnz) for the life of the process. Both layouts give the same result bits.
+// Layout of the loop SpMV. policy.spmv_format 1 keeps the caller's CSR arrays, 2 always
+// builds the SELL-32 copy (one slice at a time per warp) and 3 the same copy with the next
+// slice's head prefetched. By default the copy is built when its padding stays under 1.5 nnz
+// and y = A x is timed with the CSR kernel and both SELL-32 kernels (interleaved rounds on a
+// nonzero x, median of 7 after a warm-up round, on the handle's stream); the fastest is
+// kept, and the decision is cached per (n, nnz) for the life of the process. All give the
+// same result bits.
 struct SpFmtTune {
-    int n, nnz, sell;
-    float ms[2];
+    int n, nnz, choice;       // 0 CSR, 1 SELL-32, 2 SELL-32 with prefetch
+    float ms[3];
 };
 static std::vector<SpFmtTune> g_spfmt_cache;
 
@@ -388,24 +394,25 @@ static int choose_spmv_format(bjac_handle *h) {
     if (f == 0) {
         for (const SpFmtTune &t : g_spfmt_cache)
             if (t.n == h->A.n && t.nnz == h->A.nnz) {
-                h->spmv_ms[0] = t.ms[0];
-                h->spmv_ms[1] = t.ms[1];
-                if (!t.sell) return MPBJAC_OK;
+                for (int i = 0; i < 3; ++i) h->spmv_ms[i] = t.ms[i];
+                if (t.choice == 0) return MPBJAC_OK;
                 int rc = sell_build(h->A, 1.5, &h->sell, st);
                 if (rc) return rc;
                 h->use_sell = h->sell.val != nullptr;
+                h->sell.kernel = t.choice - 1;
                 return MPBJAC_OK;
             }
     }
-    int rc = sell_build(h->A, f == 2 ? 0.0 : 1.5, &h->sell, st);
+    int rc = sell_build(h->A, f >= 2 ? 0.0 : 1.5, &h->sell, st);
     if (rc) return rc;
     if (!h->sell.val) {
-        if (f == 2) return fail(MPBJAC_ERR_UNSUPPORTED, "A needs more than 2^31 stored SELL-32 entries");
-        g_spfmt_cache.push_back({h->A.n, h->A.nnz, 0, {0.0f, 0.0f}});
+        if (f >= 2) return fail(MPBJAC_ERR_UNSUPPORTED, "A needs more than 2^31 stored SELL-32 entries");
+        g_spfmt_cache.push_back({h->A.n, h->A.nnz, 0, {0.0f, 0.0f, 0.0f}});
         return MPBJAC_OK;
     }
-    if (f == 2) {
+    if (f >= 2) {
         h->use_sell = 1;
+        h->sell.kernel = f - 2;
         return MPBJAC_OK;
     }
     double *x = h->d_p, *y = h->d_q;
@@ -414,12 +421,16 @@ static int choose_spmv_format(bjac_handle *h) {
     MPB_CUDA(cudaEventCreate(&e0));
     MPB_CUDA(cudaEventCreate(&e1));
     constexpr int kRounds = 8;
-    float t[2][kRounds] = {};
+    float t[3][kRounds] = {};
     for (int rep = 0; rep < kRounds; ++rep) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 3; ++k) {
             MPB_CUDA(cudaEventRecord(e0, st));
-            rc = k == 0 ? launch_spmv(h->A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st)
-                        : launch_spmv_sell(h->sell, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, kSpY, st);
+            if (k == 0) {
+                rc = launch_spmv(h->A, x, y, nullptr, nullptr, nullptr, nullptr, 0, st);
+            } else {
+                h->sell.kernel = k - 1;
+                rc = launch_spmv_sell(h->sell, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, kSpY, st);
+            }
             if (rc) return rc;
             MPB_CUDA(cudaEventRecord(e1, st));
             MPB_CUDA(cudaEventSynchronize(e1));
@@ -428,13 +439,16 @@ static int choose_spmv_format(bjac_handle *h) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int k = 0; k < 2; ++k) {
+    int best = 0;
+    for (int k = 0; k < 3; ++k) {
         std::sort(t[k] + 1, t[k] + kRounds);
         h->spmv_ms[k] = t[k][1 + (kRounds - 1) / 2];
+        if (h->spmv_ms[k] < h->spmv_ms[best]) best = k;
     }
-    h->use_sell = h->spmv_ms[1] < h->spmv_ms[0];
-    if (!h->use_sell) sell_free(&h->sell);
-    g_spfmt_cache.push_back({h->A.n, h->A.nnz, h->use_sell, {h->spmv_ms[0], h->spmv_ms[1]}});
+    h->use_sell = best > 0;
+    if (best > 0) h->sell.kernel = best - 1;
+    else sell_free(&h->sell);
+    g_spfmt_cache.push_back({h->A.n, h->A.nnz, best, {h->spmv_ms[0], h->spmv_ms[1], h->spmv_ms[2]}});
     return MPBJAC_OK;
 }
 
@@ -485,7 +499,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_MLP needs mlp_params");
     if (P.temporal != BJAC_TEMPORAL_NONE && P.select == BJAC_SELECT_UNIFORM)
         return fail(MPBJAC_ERR_INVALID_ARG, "aMP switching needs a low-precision set");
-    if (P.spmv_format < 0 || P.spmv_format > 2) return fail(MPBJAC_ERR_INVALID_ARG, "spmv_format must be 0, 1 or 2");
+    if (P.spmv_format < 0 || P.spmv_format > 3) return fail(MPBJAC_ERR_INVALID_ARG, "spmv_format must be 0..3");
 
     bjac_handle *h = new bjac_handle();
     h->A = *A;
@@ -712,22 +726,45 @@ static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool l
     return launch_apply_generic(mode, lo, hi, io, h->d_S, st);
 }
 
+// Iterations per body of the device-side while loop. After convergence the remaining copies
+// of the body return at once; the loop condition is evaluated once per body.
+constexpr int kBodyIters = 4;
+
+// launches made by this thread carry the programmatic attribute while on
+namespace mpbjac {
+static thread_local bool t_pdl = false;
+bool pdl_on() { return t_pdl; }
+void pdl_set(bool on) { t_pdl = on; }
+}  // namespace mpbjac
+struct PdlOff {
+    ~PdlOff() { pdl_set(false); }
+};
+
 // One PCG iteration: captured into the body of a device-side while loop, or launched
 // eagerly by the profiler with an event between kernels (ev != nullptr: ev[0..4]).
+// pdl_first: the SpMV may overlap its predecessor kernel (programmatic launch; the later
+// kernels of the iteration always may, unless events sit between them). set_cond: this
+// copy's x/p update sets the while-loop condition. *launches += kernels launched.
 static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphConditionalHandle cond,
-                        cudaEvent_t *ev = nullptr, bool in_graph = true) {
+                        cudaEvent_t *ev, bool pdl_first, bool set_cond, int *launches) {
+    PdlOff pdl_guard;
     const bool temporal = (which == 0) && h->pol.temporal != BJAC_TEMPORAL_NONE;
     const bool use_low = (which == 0) && h->have_lo;
+    const bool pdl = ev == nullptr;
     if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
+    pdl_set(pdl && pdl_first);
     int rc = launch_loop_spmv(h, cs);
     if (rc) return rc;
+    *launches += 1;
+    pdl_set(pdl);
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
     if (temporal) {
-        k_update_r<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_q, h->d_r, h->d_part, h->d_S);
-        MPB_CUDA(cudaGetLastError());
+        MPB_CUDA(launch_kernel(k_update_r, vec_grid2(h->n), kNT, 0, cs, h->n, (const double *)h->d_q, h->d_r,
+                               h->d_part, h->d_S));
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
         if (rc) return rc;
+        *launches += lo_uses_tma(h) ? 3 : 2;
     } else {
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         ApplyIO io = base_io(h);
@@ -736,10 +773,12 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         else rc = launch_apply_generic(kApplyFused, use_low ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                        h->d_S, cs);
         if (rc) return rc;
+        *launches += 1;
     }
     if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));
-    k_update_xp<<<vec_grid2(h->n), kNT, 0, cs>>>(h->n, h->d_z, h->d_p, h->d_S, cond, (in_graph && !ev) ? 1 : 0);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_update_xp, vec_grid2(h->n), kNT, 0, cs, h->n, (const double *)h->d_z, h->d_p, h->d_S,
+                           cond, set_cond ? 1 : 0));
+    *launches += 1;
     if (ev) MPB_CUDA(cudaEventRecord(ev[4], cs));
     return MPBJAC_OK;
 }
@@ -764,7 +803,9 @@ static int build_graph(bjac_handle *h, int which) {
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaStreamCreate"); }
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); return cuda_fail(e, "BeginCaptureToGraph"); }
-    int rc = capture_body(h, which, cs, cond);
+    int rc = MPBJAC_OK, body_launches = 0;
+    for (int k = 0; k < kBodyIters && rc == MPBJAC_OK; ++k)
+        rc = capture_body(h, which, cs, cond, nullptr, k > 0, k == kBodyIters - 1, &body_launches);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
@@ -777,6 +818,7 @@ static int build_graph(bjac_handle *h, int which) {
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphInstantiate"); }
     h->graph[which] = g;
     h->exec[which] = ex;
+    h->body_launches[which] = body_launches;
     return MPBJAC_OK;
 }
 
@@ -797,36 +839,50 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;
     k_zero_if_zero_rhs<<<vec_grid(h->n), kNT, 0, st>>>(h->n, h->d_S);
+    h->launches += 2;
     const bool eager = h->pol.graph_mode == 1;
     if (!eager && !h->exec[which]) {
         rc = build_graph(h, which);
         if (rc) return rc;
     }
+    int iter_before = 0;
     for (int pass = 0; pass < 9; ++pass) {
         const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
-        rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1,
-                                 !temporal && hs.low_default == 0);
+        const bool low_only = !temporal && hs.low_default == 1, high_only = !temporal && hs.low_default == 0;
+        rc = launch_apply_select(h, kApplyInit, st, low_only, high_only);
         if (rc) return rc;
+        h->launches += (lo_uses_tma(h) && !high_only && !low_only) ? 2 : 1;
         if (eager) {
             // the same loop body, enqueued from the host in batches of 32 iterations; once the
             // state leaves "running" every kernel returns at once
             int32_t state = kRunning;
+            int n_launch = 0;
             while (state == kRunning) {
                 for (int k = 0; k < 32; ++k) {
-                    rc = capture_body(h, which, st, cudaGraphConditionalHandle{}, nullptr, false);
+                    rc = capture_body(h, which, st, cudaGraphConditionalHandle{}, nullptr, true, false, &n_launch);
                     if (rc) return rc;
                 }
                 MPB_CUDA(cudaMemcpyAsync(&state, &h->d_S->state, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
                 MPB_CUDA(cudaStreamSynchronize(st));
             }
+            h->launches += n_launch;
         } else {
             MPB_CUDA(cudaGraphLaunch(h->exec[which], st));
             *graph_launches += 1;
         }
         rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 2, st);
         if (rc) return rc;
+        h->launches += 1;
         MPB_CUDA(cudaMemcpyAsync(&hs, h->d_S, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
         MPB_CUDA(cudaStreamSynchronize(st));
+        if (!eager) {
+            // the body runs at least once per graph launch, then until a body ends with the
+            // state no longer running
+            const int ran = hs.iter - iter_before;
+            const int bodies = ran > 0 ? (ran + kBodyIters - 1) / kBodyIters : 1;
+            h->launches += (long long)bodies * h->body_launches[which];
+        }
+        iter_before = hs.iter;
         if (hs.state != kRunning) break;      // no restart requested
     }
     return MPBJAC_OK;
@@ -841,6 +897,7 @@ extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol,
     MPB_CUDA(cudaEventRecord(h->ev0, st));
     if (h->d_x0) MPB_CUDA(cudaMemcpyAsync(h->d_x0, x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
     int launches = 0;
+    h->launches = 0;
     int rc = run_solve(h, 0, b, x, tol, maxit, relres_hist, &launches);
     if (rc) return rc;
     SolverState res = *h->h_S;
@@ -873,6 +930,7 @@ extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol,
         stats->low_applies = res.low_applies;
         stats->high_applies = res.high_applies;
         stats->graph_launches = launches;
+        stats->kernel_launches = h->launches > INT32_MAX ? INT32_MAX : (int32_t)h->launches;
         stats->relres = res.relres;
         stats->true_relres = res.true_relres;
         for (int i = 0; i < 4; ++i) stats->blocks_per_fmt[i] = h->blocks_per_fmt[i];
@@ -992,12 +1050,10 @@ extern "C" int bjac_convert(const double *x, float *f, double *w, int32_t n, voi
 
 extern "C" int bjac_spmv_format(const bjac_handle *h, int32_t *format, int64_t *entries, float *ms) {
     if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
-    if (format) *format = h->use_sell;
+    if (format) *format = h->use_sell ? 1 + h->sell.kernel : 0;
     if (entries) *entries = h->use_sell ? h->sell.entries : 0;
-    if (ms) {
-        ms[0] = h->spmv_ms[0];
-        ms[1] = h->spmv_ms[1];
-    }
+    if (ms)
+        for (int i = 0; i < 3; ++i) ms[i] = h->spmv_ms[i];
     return MPBJAC_OK;
 }
 
@@ -1068,7 +1124,9 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     const int cap = maxit < 64 ? maxit : 64;
     std::vector<cudaEvent_t> ev((size_t)cap * 5);
     for (auto &e : ev) MPB_CUDA(cudaEventCreate(&e));
-    for (int k = 0; k < cap && rc == 0; ++k) rc = capture_body(h, 0, st, cudaGraphConditionalHandle{}, &ev[(size_t)k * 5]);
+    int n_launch = 0;
+    for (int k = 0; k < cap && rc == 0; ++k)
+        rc = capture_body(h, 0, st, cudaGraphConditionalHandle{}, &ev[(size_t)k * 5], false, false, &n_launch);
     if (rc == 0) MPB_CUDA(cudaMemcpyAsync(&hs, h->d_S, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
     if (rc == 0) MPB_CUDA(cudaStreamSynchronize(st));
     const int ran = rc == 0 ? (hs.iter < cap ? hs.iter : cap) : 0;

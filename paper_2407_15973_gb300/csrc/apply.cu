@@ -74,6 +74,7 @@ __device__ __forceinline__ float low_row(const QT *__restrict__ Q, const float *
 
 template <int MODE>
 __global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO io, SolverState *S) {
+    pdl_enter();
     __shared__ double s_r[kWarps][128];
     __shared__ float s_rh[kWarps][128];
     __shared__ double s_red[kWarps];
@@ -165,6 +166,7 @@ struct TmaGeom {
 template <typename QT, int BS, int MODE>
 __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet P, ApplyIO io, SolverState *S,
                                                                             int n) {
+    pdl_enter();
     using Geo = TmaGeom<QT, BS>;
     constexpr int RPL = BS / 32;     // rows per lane
     extern __shared__ __align__(128) uint8_t smem[];
@@ -344,6 +346,7 @@ template <> __device__ __forceinline__ float vec_entry<__half>(const uint4 &v, i
 
 template <typename QT, int BS, int MODE>
 __global__ void __launch_bounds__(kNT, 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
+    pdl_enter();
     using Geo = RegGeom<QT, BS>;
     constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
     __shared__ __align__(16) float s_rh[kWarps][BS];
@@ -485,8 +488,7 @@ static int launch_tma_t(const PSet &P, const ApplyIO &io, SolverState *S, int n,
     const int need = (P.nb + Geo::kNW - 1) / Geo::kNW;
     if (g > need) g = need;
     if (g < 1) g = 1;
-    k_apply_tma<QT, BS, MODE><<<g, Geo::kThreads, Geo::kSmem, st>>>(P, io, S, n);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_apply_tma<QT, BS, MODE>, g, Geo::kThreads, Geo::kSmem, st, P, io, S, n));
     return MPBJAC_OK;
 }
 
@@ -518,8 +520,7 @@ static int launch_reg_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaSt
     if (g > need) g = need;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g < 1) g = 1;
-    k_apply_reg<QT, BS, MODE><<<g, kNT, 0, st>>>(P, io, S);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_apply_reg<QT, BS, MODE>, g, kNT, 0, st, P, io, S));
     return MPBJAC_OK;
 }
 
@@ -570,12 +571,11 @@ int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO
                                                                       : (lo.nb > hi.nb ? lo.nb : hi.nb);
     const int g = generic_grid(nb);
     switch (mode) {
-        case kApplyStandalone: k_apply_generic<kApplyStandalone><<<g, kNT, 0, st>>>(lo, hi, io, S); break;
-        case kApplyInit: k_apply_generic<kApplyInit><<<g, kNT, 0, st>>>(lo, hi, io, S); break;
-        case kApplyTemporal: k_apply_generic<kApplyTemporal><<<g, kNT, 0, st>>>(lo, hi, io, S); break;
-        default: k_apply_generic<kApplyFused><<<g, kNT, 0, st>>>(lo, hi, io, S); break;
+        case kApplyStandalone: MPB_CUDA(launch_kernel(k_apply_generic<kApplyStandalone>, g, kNT, 0, st, lo, hi, io, S)); break;
+        case kApplyInit: MPB_CUDA(launch_kernel(k_apply_generic<kApplyInit>, g, kNT, 0, st, lo, hi, io, S)); break;
+        case kApplyTemporal: MPB_CUDA(launch_kernel(k_apply_generic<kApplyTemporal>, g, kNT, 0, st, lo, hi, io, S)); break;
+        default: MPB_CUDA(launch_kernel(k_apply_generic<kApplyFused>, g, kNT, 0, st, lo, hi, io, S)); break;
     }
-    MPB_CUDA(cudaGetLastError());
     return MPBJAC_OK;
 }
 

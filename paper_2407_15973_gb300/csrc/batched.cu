@@ -770,6 +770,7 @@ extern "C" int pcg_solve_batched(bjac_batch *h, const double *const *b, double *
             o.relres = sd[4 * S + s];
             o.true_relres = sd[5 * S + s];
             o.graph_launches = 1;
+            o.kernel_launches = 1;      // the persistent kernel (shared by all systems)
             for (int i = 0; i < 4; ++i) o.blocks_per_fmt[i] = h->blocks_per_fmt[i];
             o.setup_ms = h->setup_ms;
             o.solve_ms = ms;

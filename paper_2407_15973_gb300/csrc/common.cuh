@@ -34,6 +34,41 @@ constexpr int kMaxGrid = 152 * 8;        // upper bound on CTAs of any reducing 
 int sm_count();
 
 // ----------------------------------------------------------------------------------------
+// programmatic dependent launch: a loop kernel launched with the programmatic attribute may
+// be scheduled while its predecessor in the stream is still draining. It waits here until
+// that predecessor has completed and its writes are visible, before touching any global
+// memory, and at once lets its own successor be scheduled (the successor waits the same
+// way). Both instructions are no-ops for a kernel launched without the attribute.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host: whether launches made by this thread now carry the programmatic attribute (set
+// around the PCG loop body only).
+bool pdl_on();
+void pdl_set(bool on);
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                                 Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    if (pdl_on()) {
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// ----------------------------------------------------------------------------------------
 // solver state shared by the kernels of one PCG loop (device memory, one per handle)
 // ----------------------------------------------------------------------------------------
 enum SolverStateCode : int32_t {

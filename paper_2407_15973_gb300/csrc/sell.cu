@@ -107,12 +107,48 @@ __device__ __forceinline__ void sell_part(const double *__restrict__ pv, const i
         if (cc[u] >= 0) acc = fma(vv[u], xv[u], acc);
 }
 
+// gathers and FMA chain of U entries already loaded into registers
+template <int U>
+__device__ __forceinline__ void sell_fma(const double (&vv)[8], const int (&cc)[8], const double *__restrict__ x,
+                                         double &acc) {
+    double xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (cc[u] >= 0) acc = fma(vv[u], xv[u], acc);
+}
+
+// the first (up to) 8 entries of every row of slice s, or nothing past the last slice
+__device__ __forceinline__ void sell_head(int s, int nslices, int lane, const int32_t *__restrict__ off,
+                                          const int32_t *__restrict__ col, const double *__restrict__ val,
+                                          double (&vv)[8], int (&cc)[8], int &o0, int &len) {
+    o0 = 0;
+    len = 0;
+    if (s < nslices) {
+        o0 = __ldg(off + s);
+        len = (__ldg(off + s + 1) - o0) >> 5;
+    }
+    const int cnt = len < 8 ? len : 8;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (u < cnt) {
+            vv[u] = __ldcs(val + o0 + 32 * u + lane);
+            cc[u] = __ldcs(col + o0 + 32 * u + lane);
+        } else {
+            vv[u] = 0.0;
+            cc[u] = -1;
+        }
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kSpNT, 4) k_spmv_sell(int n, int nslices, const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ col, const double *__restrict__ val,
                                                        const double *__restrict__ x, const double *__restrict__ b,
                                                        double *__restrict__ y, double *part, unsigned int *ticket,
                                                        double *out, SolverState *S) {
+    pdl_enter();
     constexpr int NW = kSpNT / 32;
     constexpr bool RES = KIND >= 10;
     __shared__ double red[2][NW];
@@ -148,6 +184,101 @@ __global__ void __launch_bounds__(kSpNT, 4) k_spmv_sell(int n, int nslices, cons
             case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, acc); break;
             case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, acc); break;
             default: break;
+        }
+        if (row < n) {
+            if (RES) {
+                const double ri = bi - acc;
+                y[row] = ri;
+                acc1 = fma(ri, ri, acc1);
+                acc2 = fma(bi, bi, acc2);
+            } else {
+                y[row] = acc;
+                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
+            }
+        }
+    }
+    if (KIND == kSpY) return;
+    const double b1 = block_sum<kSpNT>(acc1, red[0]);
+    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = b1;
+        part[2 * blockIdx.x + 1] = b2;
+    }
+    if (!last_cta(ticket)) return;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+}
+
+// The same SpMV with the first chunk (up to 8 entries per row) of a warp's next slice loaded
+// into registers while the current slice's x gathers and FMA chains run, so that every warp
+// keeps two slices' loads in flight. Longer rows finish with unprefetched chunks of 8.
+template <int KIND>
+__global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, const int32_t *__restrict__ off,
+                                                          const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val,
+                                                          const double *__restrict__ x, const double *__restrict__ b,
+                                                          double *__restrict__ y, double *part, unsigned int *ticket,
+                                                          double *out, SolverState *S) {
+    pdl_enter();
+    constexpr int NW = kSpNT / 32;
+    constexpr bool RES = KIND >= 10;
+    __shared__ double red[2][NW];
+    if (KIND == kSpPcg) {
+        // the previous iteration's x update is done (stream order): clear its flag even when
+        // this iteration does not run, so a loop body after convergence changes nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
+        if (S->state != kRunning) return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
+    double acc1 = 0.0, acc2 = 0.0;
+    double nv[8];
+    int nc[8], n_o0, n_len;
+    sell_head(gw, nslices, lane, off, col, val, nv, nc, n_o0, n_len);
+    for (int s = gw; s < nslices; s += nw) {
+        double cv[8];
+        int cc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            cv[u] = nv[u];
+            cc[u] = nc[u];
+        }
+        const int o0 = n_o0, len = n_len;
+        sell_head(s + nw, nslices, lane, off, col, val, nv, nc, n_o0, n_len);
+        const int row = (s << 5) + lane;
+        double xr = 0.0, bi = 0.0;
+        if (row < n) {
+            if (RES) bi = b[row];
+            else if (KIND != kSpY) xr = __ldg(x + row);
+        }
+        double acc = 0.0;
+        switch (len < 8 ? len : 8) {
+            case 1: sell_fma<1>(cv, cc, x, acc); break;
+            case 2: sell_fma<2>(cv, cc, x, acc); break;
+            case 3: sell_fma<3>(cv, cc, x, acc); break;
+            case 4: sell_fma<4>(cv, cc, x, acc); break;
+            case 5: sell_fma<5>(cv, cc, x, acc); break;
+            case 6: sell_fma<6>(cv, cc, x, acc); break;
+            case 7: sell_fma<7>(cv, cc, x, acc); break;
+            case 8: sell_fma<8>(cv, cc, x, acc); break;
+            default: break;
+        }
+        if (len > 8) {
+            const double *pv = val + o0 + lane;
+            const int32_t *pc = col + o0 + lane;
+            int j = 8;
+            for (; j + 8 <= len; j += 8) sell_part<8>(pv + 32 * j, pc + 32 * j, x, acc);
+            switch (len - j) {
+                case 1: sell_part<1>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 2: sell_part<2>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 3: sell_part<3>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 4: sell_part<4>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 5: sell_part<5>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                default: break;
+            }
         }
         if (row < n) {
             if (RES) {
@@ -242,20 +373,26 @@ int sell_build(const bjac_csr &A, double max_ratio, SellMat *out, cudaStream_t s
 template <int KIND>
 static int launch_sell_t(const SellMat &M, const double *x, const double *b, double *y, double *part,
                          unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    static int per_sm[2] = {0, 0};
+    const int pf = M.kernel == 1;
+    if (per_sm[pf] == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv_sell<KIND>, kSpNT, 0) != cudaSuccess || v < 1)
-            v = 1;
-        per_sm = v;
+        cudaError_t e = pf ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv_sell_pf<KIND>, kSpNT, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv_sell<KIND>, kSpNT, 0);
+        if (e != cudaSuccess || v < 1) v = 1;
+        per_sm[pf] = v;
     }
-    int g = sm_count() * per_sm;
+    int g = sm_count() * per_sm[pf];
     if (g > kMaxGrid) g = kMaxGrid;
     const int need = (M.nslices + kSpNT / 32 - 1) / (kSpNT / 32);
     if (g > need) g = need;
     if (g < 1) g = 1;
-    k_spmv_sell<KIND><<<g, kSpNT, 0, st>>>(M.n, M.nslices, M.off, M.col, M.val, x, b, y, part, ticket, out, S);
-    MPB_CUDA(cudaGetLastError());
+    if (pf)
+        MPB_CUDA(launch_kernel(k_spmv_sell_pf<KIND>, g, kSpNT, 0, st, M.n, M.nslices, (const int32_t *)M.off,
+                               (const int32_t *)M.col, (const double *)M.val, x, b, y, part, ticket, out, S));
+    else
+        MPB_CUDA(launch_kernel(k_spmv_sell<KIND>, g, kSpNT, 0, st, M.n, M.nslices, (const int32_t *)M.off,
+                               (const int32_t *)M.col, (const double *)M.val, x, b, y, part, ticket, out, S));
     return MPBJAC_OK;
 }
 

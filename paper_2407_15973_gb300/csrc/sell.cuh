@@ -12,6 +12,7 @@ struct SellMat {
     double *val = nullptr;        // [entries] value, 0 for padding
     long long entries = 0;        // stored entries including the padding
     int max_len = 0;              // longest row
+    int kernel = 0;               // 0: one slice at a time per warp; 1: next slice's head prefetched
 };
 
 // Build the copy of A on the stream (reads the CSR once, writes 12 bytes per stored entry).

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
                                                 const double *__restrict__ x, const double *__restrict__ b,
                                                 double *__restrict__ y, double *part, unsigned int *ticket,
                                                 double *out, SolverState *S) {
+    pdl_enter();
     constexpr int RPT = kSpNT;           // rows per tile
     constexpr int kCap = CAP, kStages = NST, kStageBytes = CAP * 12;
     constexpr bool RES = KIND >= 10;
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
                                                      const double *__restrict__ val, const double *__restrict__ x,
                                                      const double *__restrict__ b, double *__restrict__ y,
                                                      double *part, unsigned int *ticket, double *out, SolverState *S) {
+    pdl_enter();
     constexpr int CH = 32 * K;          // nonzeros per chunk
     constexpr int NW = kSpNT / 32;
     constexpr bool RES = KIND >= 10;
@@ -323,6 +325,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
                                                      const double *__restrict__ val, const double *__restrict__ x,
                                                      const double *__restrict__ b, double *__restrict__ y,
                                                      double *part, unsigned int *ticket, double *out, SolverState *S) {
+    pdl_enter();
     constexpr int CH = 32 * K;
     constexpr int NW = kSpNT / 32;
     constexpr bool RES = KIND >= 10;
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(kWThreads) k_spmv_wtma(int n, int nnz, const i
                                                          const double *__restrict__ b, double *__restrict__ y,
                                                          double *part, unsigned int *ticket, double *out,
                                                          SolverState *S) {
+    pdl_enter();
     constexpr bool RES = KIND >= 10;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_meta[kWWarps][kWStages][2];
@@ -663,9 +667,8 @@ static int launch_t(const bjac_csr &A, const double *x, const double *b, double 
     if (g > kMaxGrid) g = kMaxGrid;
     if (g > ntiles) g = ntiles;
     if (g < 1) g = 1;
-    k_spmv<G::kCap, G::kStages, KIND><<<g, kSpNT, G::kSmem, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y,
-                                                                  part, ticket, out, S);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_spmv<G::kCap, G::kStages, KIND>, g, kSpNT, G::kSmem, st, A.n, A.nnz, A.rowptr, A.colidx,
+                           A.val, x, b, y, part, ticket, out, S));
     return MPBJAC_OK;
 }
 
@@ -685,8 +688,8 @@ static int launch_warp_t(const bjac_csr &A, const double *x, const double *b, do
     const int need = (ntiles + kSpNT / 32 - 1) / (kSpNT / 32);
     if (g > need) g = need;
     if (g < 1) g = 1;
-    k_spmv_warp<8, KIND><<<g, kSpNT, 0, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket, out, S);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_spmv_warp<8, KIND>, g, kSpNT, 0, st, A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part,
+                           ticket, out, S));
     return MPBJAC_OK;
 }
 
@@ -706,8 +709,8 @@ static int launch_pipe_t(const bjac_csr &A, const double *x, const double *b, do
     const int need = (ntiles + kSpNT / 32 - 1) / (kSpNT / 32);
     if (g > need) g = need;
     if (g < 1) g = 1;
-    k_spmv_pipe<8, KIND><<<g, kSpNT, 0, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket, out, S);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_spmv_pipe<8, KIND>, g, kSpNT, 0, st, A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part,
+                           ticket, out, S));
     return MPBJAC_OK;
 }
 
@@ -719,9 +722,8 @@ static int launch_wtma_t(const bjac_csr &A, const double *x, const double *b, do
     const int need = (ntiles + kWWarps - 1) / kWWarps;
     if (g > need) g = need;
     if (g < 1) g = 1;
-    k_spmv_wtma<KIND><<<g, kWThreads, kWSmem, st>>>(A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part, ticket,
-                                                    out, S);
-    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(launch_kernel(k_spmv_wtma<KIND>, g, kWThreads, kWSmem, st, A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y,
+                           part, ticket, out, S));
     return MPBJAC_OK;
 }
 

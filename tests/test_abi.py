@@ -87,7 +87,7 @@ def test_invalid_spmv_format_rejected_on_host(libpath):
     csr = B.bjac_csr(64, 64, 16, 16, 16)
     bp = np.array([0, 32, 64], np.int32)
     pol = B.bjac_policy()
-    pol.select, pol.spmv_format = B.SELECT_UNIFORM, 3
+    pol.select, pol.spmv_format = B.SELECT_UNIFORM, 4
     out = ctypes.c_void_p()
     rc = L.bjac_setup(ctypes.byref(csr), bp.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(pol), ctypes.byref(out))
     assert rc == B.ERR_INVALID_ARG

@@ -34,8 +34,9 @@ CASES = {
 B_FP32, B_BF16, B_FP16S = 1, 2, 3
 
 
+@pytest.mark.parametrize("layout", [2, 3])
 @pytest.mark.parametrize("case", list(CASES))
-def test_handle_spmv_sell_matches_csr_bits(B, case):
+def test_handle_spmv_sell_matches_csr_bits(B, case, layout):
     pr, fmt = CASES[case]()
     A = pr.A
     dA = B.DeviceCSR(A)
@@ -43,11 +44,11 @@ def test_handle_spmv_sell_matches_csr_bits(B, case):
     y_csr = torch.empty(A.n, dtype=torch.float64, device="cuda")
     xy_csr = torch.zeros(1, dtype=torch.float64, device="cuda")
     B.bjac_spmv(dA, x, y_csr, xy_csr)
-    hs = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=fmt, spmv_format=2)
+    hs = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=fmt, spmv_format=layout)
     hc = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=fmt, spmv_format=1)
     try:
         fs, fc = hs.spmv_format(), hc.spmv_format()
-        assert fs["format"] == "sell32" and fs["entries"] == _entries(A)
+        assert fs["format"] == {2: "sell32", 3: "sell32-prefetch"}[layout] and fs["entries"] == _entries(A)
         assert fc["format"] == "csr" and fc["entries"] == 0
         y = torch.empty(A.n, dtype=torch.float64, device="cuda")
         xy = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -78,11 +79,10 @@ def test_default_layout_is_timed_and_reported(B):
     h = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_FIXED, fixed_fmt=B.BF16)
     try:
         f = h.spmv_format()
-        assert f["format"] in ("csr", "sell32")
-        assert f["ms"][0] > 0 and f["ms"][1] > 0
-        faster = "sell32" if f["ms"][1] < f["ms"][0] else "csr"
-        assert f["format"] == faster
-        assert f["entries"] == (_entries(pr.A) if f["format"] == "sell32" else 0)
+        assert all(t > 0 for t in f["ms"])
+        names = ["csr", "sell32", "sell32-prefetch"]
+        assert f["format"] == names[int(np.argmin(f["ms"]))]
+        assert f["entries"] == (_entries(pr.A) if f["format"] != "csr" else 0)
     finally:
         h.close()
 
@@ -109,19 +109,20 @@ def test_padding_limit_keeps_csr(B):
         assert h.spmv_format()["format"] == "csr"
     finally:
         h.close()
-    h = B.bjac_setup(dA, bp, select=B.SELECT_FIXED, fixed_fmt=B.FP32, spmv_format=2)
-    try:
-        assert h.spmv_format() ["entries"] == _entries(A)
-        x = cuda(PB.solution(n, 3))
-        y = torch.empty(n, dtype=torch.float64, device="cuda")
-        h.spmv(x, y)
-        assert np.max(np.abs(host(y) - O.spmv(A, host(x)))) <= spmv_tol(A, host(x))
-    finally:
-        h.close()
+    for layout in (2, 3):
+        h = B.bjac_setup(dA, bp, select=B.SELECT_FIXED, fixed_fmt=B.FP32, spmv_format=layout)
+        try:
+            assert h.spmv_format()["entries"] == _entries(A)
+            x = cuda(PB.solution(n, 3))
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            h.spmv(x, y)
+            assert np.max(np.abs(host(y) - O.spmv(A, host(x)))) <= spmv_tol(A, host(x))
+        finally:
+            h.close()
 
 
 def test_invalid_layout_rejected(B):
     pr = PB.make_problem("poisson2d", seed=0, m=16, bs=8)
     dA = B.DeviceCSR(pr.A)
     with pytest.raises(B.MpbjacError):
-        B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_UNIFORM, spmv_format=3)
+        B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_UNIFORM, spmv_format=4)
