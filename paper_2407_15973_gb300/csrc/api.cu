@@ -604,7 +604,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
         a.pool = h->d_pool;
     }
     MPB_TRY(prepare_spmv(*A));
-    MPB_TRY(launch_setup_blocks(a, bs_max, st));
+    MPB_TRY(launch_setup_blocks(a, bs_max, h->h_block_ptr.data(), st));
     if (P.select == BJAC_SELECT_MLP) {
         MPB_TRY(launch_mlp_select(P.mlp_params, nb, h->d_feat, h->d_kap, h->pol.safety_theta, h->d_fmt, st));
     }

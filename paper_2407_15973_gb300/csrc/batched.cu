@@ -653,7 +653,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     a.feat = h->feat;
     a.kap = h->kap;
     a.status = h->status;
-    int rc = launch_setup_blocks(a, 32, st);
+    int rc = launch_setup_blocks(a, 32, nullptr, st);
     if (rc) return bail(rc);
     int hstat[2] = {0, 0};
     BTRY(cudaMemcpyAsync(hstat, h->status, sizeof(hstat), cudaMemcpyDeviceToHost, st));

@@ -27,7 +27,8 @@ struct SetupArgs {
 };
 
 size_t setup_smem_bytes(int bs_max);
-int launch_setup_blocks(const SetupArgs &a, int bs_max, cudaStream_t st);
+// h_block_ptr (HOST, nullable): block sizes for grouping the blocks by size class.
+int launch_setup_blocks(const SetupArgs &a, int bs_max, const int32_t *h_block_ptr, cudaStream_t st);
 int launch_pack(int nb, const int32_t *block_ptr, const int64_t *goff, const double *G, const uint8_t *fmt,
                 const int64_t *qoff, uint8_t *pool, float *scale, cudaStream_t st);
 
