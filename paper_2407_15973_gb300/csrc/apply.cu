@@ -10,7 +10,8 @@
 // needs no cross-lane reduction.
 //
 // Two kernels:
-//  * k_apply_generic: one warp per block, any block size 1..128, any mix of formats.
+//  * k_apply_generic: one warp per block, any block size 1..128, any mix of formats; rows
+//    that are 16-byte aligned are read with vector loads by the lane that owns them.
 //  * k_apply_tma: all blocks of one size (32 or 64) and one low format. Persistent
 //    CTAs stream groups of consecutive blocks (plus the matching slices of r and q)
 //    through a ring of shared-memory stages filled by cp.async.bulk (TMA bulk copies)
@@ -56,6 +57,82 @@ __device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyI
 }
 
 // ----------------------------------------------------------------------------------------
+// 16-byte loads of a block's rows. Because every block is symmetric, row i is also column i,
+// so lane i can read its own row i with vector loads and run the FMA chain over j in natural
+// order (the same arithmetic, in the same order, as the column sweep below).
+// ----------------------------------------------------------------------------------------
+template <typename QT, int BS>
+struct RegGeom {
+    static constexpr int kRPL = BS / 32;                       // rows per lane
+    static constexpr int kVPR = BS * (int)sizeof(QT) / 16;     // 16-byte vectors per row
+    static constexpr int kEPV = 16 / (int)sizeof(QT);          // entries per vector
+};
+
+template <typename QT>
+__device__ __forceinline__ float vec_entry(const uint4 &v, int e);
+template <> __device__ __forceinline__ float vec_entry<float>(const uint4 &v, int e) {
+    const unsigned w = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+    return __uint_as_float(w);
+}
+template <> __device__ __forceinline__ float vec_entry<__nv_bfloat16>(const uint4 &v, int e) {
+    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+    return __uint_as_float((e & 1) ? (w & 0xFFFF0000u) : (w << 16));     // bfloat16 -> binary32 is exact
+}
+template <> __device__ __forceinline__ float vec_entry<__half>(const uint4 &v, int e) {
+    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+    return __half2float(__ushort_as_half((unsigned short)((e & 1) ? (w >> 16) : (w & 0xFFFFu))));
+}
+
+// one output row of a low-precision block: row = this row's 16-byte vectors, rh = r-hat
+template <typename QT>
+__device__ __forceinline__ float vec_row_low(const uint4 *__restrict__ row, int vpr, const float *rh) {
+    constexpr int EPV = 16 / (int)sizeof(QT);
+    const float4 *rh4 = reinterpret_cast<const float4 *>(rh);
+    float a = 0.0f;
+    for (int v0 = 0; v0 < vpr; v0 += 2) {
+        uint4 q[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (v0 + u < vpr) q[u] = __ldg(row + v0 + u);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (v0 + u < vpr) {
+#pragma unroll
+                for (int e4 = 0; e4 < EPV; e4 += 4) {
+                    const float4 r4 = rh4[((v0 + u) * EPV + e4) >> 2];
+                    a = fmaf(vec_entry<QT>(q[u], e4 + 0), r4.x, a);
+                    a = fmaf(vec_entry<QT>(q[u], e4 + 1), r4.y, a);
+                    a = fmaf(vec_entry<QT>(q[u], e4 + 2), r4.z, a);
+                    a = fmaf(vec_entry<QT>(q[u], e4 + 3), r4.w, a);
+                }
+            }
+        }
+    }
+    return a;
+}
+
+// one output row of a binary64 block
+__device__ __forceinline__ double vec_row_f64(const uint4 *__restrict__ row, int vpr, const double *r) {
+    const double2 *r2 = reinterpret_cast<const double2 *>(r);
+    double a = 0.0;
+    for (int v0 = 0; v0 < vpr; v0 += 2) {
+        uint4 q[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (v0 + u < vpr) q[u] = __ldg(row + v0 + u);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (v0 + u < vpr) {
+                const double2 rr = r2[v0 + u];
+                a = fma(__hiloint2double((int)q[u].y, (int)q[u].x), rr.x, a);
+                a = fma(__hiloint2double((int)q[u].w, (int)q[u].z), rr.y, a);
+            }
+        }
+    }
+    return a;
+}
+
+// ----------------------------------------------------------------------------------------
 // generic: one warp per block
 // ----------------------------------------------------------------------------------------
 template <typename QT>
@@ -73,10 +150,10 @@ __device__ __forceinline__ float low_row(const QT *__restrict__ Q, const float *
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO io, SolverState *S) {
+__global__ void __launch_bounds__(kNT, 3) k_apply_generic(PSet lo, PSet hi, ApplyIO io, SolverState *S) {
     pdl_enter();
-    __shared__ double s_r[kWarps][128];
-    __shared__ float s_rh[kWarps][128];
+    __shared__ __align__(16) double s_r[kWarps][128];
+    __shared__ __align__(16) float s_rh[kWarps][128];
     __shared__ double s_red[kWarps];
     int use_low = io.set;
     if (MODE != kApplyStandalone) {
@@ -105,6 +182,30 @@ __global__ void __launch_bounds__(kNT) k_apply_generic(PSet lo, PSet hi, ApplyIO
         const int f = __ldg(P.fmt + b);
         const uint8_t *base = P.pool + __ldg(P.qoff + b);
         const float sc = __ldg(P.scale + b);
+        const int eb = f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2;
+        if (((bs * eb) & 15) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+            // rows are 16-byte aligned: lane-owns-row vector loads
+            const int vpr = bs * eb / 16;
+            const uint4 *Q4 = reinterpret_cast<const uint4 *>(base);
+            for (int i = lane; i < bs; i += 32) {
+                const uint4 *row = Q4 + (size_t)i * vpr;
+                double zi;
+                if (f == BJAC_FP64) {
+                    zi = vec_row_f64(row, vpr, s_r[warp]);
+                } else {
+                    float acc;
+                    if (f == BJAC_FP32) acc = vec_row_low<float>(row, vpr, s_rh[warp]);
+                    else if (f == BJAC_BF16) acc = vec_row_low<__nv_bfloat16>(row, vpr, s_rh[warp]);
+                    else acc = vec_row_low<__half>(row, vpr, s_rh[warp]);
+                    zi = f32_to_f64(acc * sc);
+                }
+                io.z[s + i] = zi;
+                if (MODE == kApplyInit) io.p[s + i] = zi;
+                rho = fma(s_r[warp][i], zi, rho);
+            }
+            __syncwarp();
+            continue;
+        }
         for (int i = lane; i < bs; i += 32) {
             double zi;
             if (f == BJAC_FP64) {
@@ -322,28 +423,6 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
 // small per-warp buffer. The next block's row, r and q are loaded before the current block is
 // computed (two blocks in flight per warp). No TMA, no shared-memory copy of Q, no CTA sync.
 // ----------------------------------------------------------------------------------------
-template <typename QT, int BS>
-struct RegGeom {
-    static constexpr int kRPL = BS / 32;                       // rows per lane
-    static constexpr int kVPR = BS * (int)sizeof(QT) / 16;     // 16-byte vectors per row
-    static constexpr int kEPV = 16 / (int)sizeof(QT);          // entries per vector
-};
-
-template <typename QT>
-__device__ __forceinline__ float vec_entry(const uint4 &v, int e);
-template <> __device__ __forceinline__ float vec_entry<float>(const uint4 &v, int e) {
-    const unsigned w = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-    return __uint_as_float(w);
-}
-template <> __device__ __forceinline__ float vec_entry<__nv_bfloat16>(const uint4 &v, int e) {
-    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
-    return __uint_as_float((e & 1) ? (w & 0xFFFF0000u) : (w << 16));     // bfloat16 -> binary32 is exact
-}
-template <> __device__ __forceinline__ float vec_entry<__half>(const uint4 &v, int e) {
-    const unsigned w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
-    return __half2float(__ushort_as_half((unsigned short)((e & 1) ? (w >> 16) : (w & 0xFFFFu))));
-}
-
 template <typename QT, int BS, int MODE>
 __global__ void __launch_bounds__(kNT, 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
     pdl_enter();
@@ -459,9 +538,18 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_reg(PSet P, ApplyIO io, Solver
 // ----------------------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------------------
+// resident CTAs of the generic kernel (one wave), at most the blocks' warps
+template <int MODE>
 static int generic_grid(int nb) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_generic<MODE>, kNT, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v;
+    }
     const int need = (nb + kWarps - 1) / kWarps;
-    int g = sm_count() * 6;
+    int g = sm_count() * per_sm;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g > need) g = need;
     return g < 1 ? 1 : g;
@@ -569,12 +657,23 @@ int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO
                          cudaStream_t st) {
     const int nb = (mode == kApplyStandalone || mode == kApplyFused) ? (io.set ? lo.nb : hi.nb)
                                                                       : (lo.nb > hi.nb ? lo.nb : hi.nb);
-    const int g = generic_grid(nb);
     switch (mode) {
-        case kApplyStandalone: MPB_CUDA(launch_kernel(k_apply_generic<kApplyStandalone>, g, kNT, 0, st, lo, hi, io, S)); break;
-        case kApplyInit: MPB_CUDA(launch_kernel(k_apply_generic<kApplyInit>, g, kNT, 0, st, lo, hi, io, S)); break;
-        case kApplyTemporal: MPB_CUDA(launch_kernel(k_apply_generic<kApplyTemporal>, g, kNT, 0, st, lo, hi, io, S)); break;
-        default: MPB_CUDA(launch_kernel(k_apply_generic<kApplyFused>, g, kNT, 0, st, lo, hi, io, S)); break;
+        case kApplyStandalone:
+            MPB_CUDA(launch_kernel(k_apply_generic<kApplyStandalone>, generic_grid<kApplyStandalone>(nb), kNT, 0, st,
+                                   lo, hi, io, S));
+            break;
+        case kApplyInit:
+            MPB_CUDA(launch_kernel(k_apply_generic<kApplyInit>, generic_grid<kApplyInit>(nb), kNT, 0, st, lo, hi, io,
+                                   S));
+            break;
+        case kApplyTemporal:
+            MPB_CUDA(launch_kernel(k_apply_generic<kApplyTemporal>, generic_grid<kApplyTemporal>(nb), kNT, 0, st, lo,
+                                   hi, io, S));
+            break;
+        default:
+            MPB_CUDA(launch_kernel(k_apply_generic<kApplyFused>, generic_grid<kApplyFused>(nb), kNT, 0, st, lo, hi,
+                                   io, S));
+            break;
     }
     return MPBJAC_OK;
 }
