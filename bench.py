@@ -55,6 +55,9 @@ def parse():
                     help="pin the low-precision apply kernel instead of the timed choice")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven loop instead of the CUDA graph (the profiler sees every kernel)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workload configurations (27-point anisotropic 160^3, 256 batched "
+                         "2D systems, Voronoi 256^3)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only set up the headline policy and run this many eager PCG iterations "
                          "(a short, fixed launch sequence for ncu)")
@@ -374,6 +377,120 @@ def run_ours(args, rank, world, dist):
 
 
 # ------------------------------------------------------------------------------------------
+def other_configs():
+    """One measured step per policy (after a warm-up step that runs the autotuners for the
+    shape) on the other workload configurations; the batched one against the same systems
+    solved one after another by the single-system solver."""
+    import torch
+    from paper_2407_15973_gb300 import binding as B
+    from paper_2407_15973_gb300 import problems as PB
+    from paper_2407_15973_gb300 import selector as SEL
+    stream = torch.cuda.current_stream()
+    params = SEL.load() if os.path.exists(SEL.DEFAULT_WEIGHTS) else None
+
+    def timed_step(dA, bp, b, pol):
+        x = torch.zeros(dA.n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = B.bjac_setup(dA, bp, **pol)
+        st = h.solve(b, x, tol=TOL, maxit=20000)
+        h.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms": round(e0.elapsed_time(e1), 3), "setup_ms": round(st["setup_ms"], 3),
+                "solve_ms": round(st["solve_ms"], 3), "iters": st["iters"], "true_relres": st["true_relres"],
+                "converged": st["converged"], "blocks_per_fmt": st["blocks_per_fmt"],
+                "fallback_used": st["fallback_used"]}, x
+
+    out = {}
+    for key, name, modes in (
+            ("aniso27-q1-160^3-lognormal2-z1e4-bs64", "aniso27",
+             ("uniform-fp64", "fmp-fp32", "fmp-bf16", "rule", "mlp")),
+            ("voronoi7pt-256^3-5mat-1e6-uneven16..128", "voronoi3d",
+             ("uniform-fp64", "fmp-fp32", "rule", "mlp+fp64-fallback"))):
+        t0 = time.time()
+        pr = PB.make_problem(name, seed=0)
+        gen = time.time() - t0
+        dA = B.DeviceCSR(pr.A)
+        xs = torch.as_tensor(pr.x_star).cuda()
+        b = torch.empty(pr.A.n, dtype=torch.float64, device="cuda")
+        B.bjac_spmv(dA, xs, b)
+        pols = {"uniform-fp64": dict(select=B.SELECT_UNIFORM),
+                "fmp-fp32": dict(select=B.SELECT_FIXED, fixed_fmt=FMT["fp32"]),
+                "fmp-bf16": dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"]),
+                "rule": dict(select=B.SELECT_RULE)}
+        if params is not None:
+            pols["mlp"] = dict(select=B.SELECT_MLP, mlp_params=params)
+            pols["mlp+fp64-fallback"] = dict(select=B.SELECT_MLP, mlp_params=params, fp64_fallback=True)
+        timed_step(dA, pr.block_ptr, b, pols["fmp-fp32"])          # warm-up: autotuners for this shape
+        res = {}
+        for m in modes:
+            if m in pols:
+                res[m], x = timed_step(dA, pr.block_ptr, b, pols[m])
+                res[m]["x_rel_err"] = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+        base = res.get("uniform-fp64", {}).get("ms")
+        out[key] = {"n": pr.A.n, "nnz": pr.A.nnz, "blocks": pr.nb, "generate_s": round(gen, 1),
+                    "modes": res,
+                    "speedup_vs_fp64": {m: round(base / r["ms"], 3) for m, r in res.items() if base}}
+        del dA, b, xs
+
+    # 256 independent 2D systems in one persistent launch vs one after another
+    t0 = time.time()
+    systems = PB.batch2d(256, seed=0)
+    gen = time.time() - t0
+    dAs = [B.DeviceCSR(p.A) for p in systems]
+    bs = []
+    for d, p in zip(dAs, systems):
+        bv = torch.empty(p.A.n, dtype=torch.float64, device="cuda")
+        B.bjac_spmv(d, torch.as_tensor(p.x_star).cuda(), bv)
+        bs.append(bv)
+    pol = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["fp32"])
+
+    def batched_step():
+        xs_ = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in systems]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt = B.Batch(dAs, [p.block_ptr for p in systems], **pol)
+        rc, st = bt.solve(bs, xs_, tol=TOL, maxit=20000)
+        info = bt.info()
+        bt.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), rc, st, info
+
+    batched_step()
+    ms_b, rc, st, info = batched_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    seq_it = []
+    for d, p, bv in zip(dAs, systems, bs):
+        h = B.bjac_setup(d, p.block_ptr, **pol)
+        xv = torch.zeros(p.A.n, dtype=torch.float64, device="cuda")
+        seq_it.append(h.solve(bv, xv, tol=TOL, maxit=20000)["iters"])
+        h.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    its = [s["iters"] for s in st]
+    out["batched2d-256-sides32..512-fp32-bs16/32"] = {
+        "systems": len(systems), "rows": int(sum(p.A.n for p in systems)),
+        "nnz": int(sum(p.A.nnz for p in systems)), "generate_s": round(gen, 1),
+        "batched": {"ms": round(ms_b, 3), "setup_ms": round(st[0]["setup_ms"], 3),
+                    "solve_ms": round(st[0]["solve_ms"], 3), "status": rc,
+                    "all_converged": all(s["converged"] for s in st),
+                    "worst_true_relres": max(s["true_relres"] for s in st),
+                    "iters_max": max(its), "iters_mean": round(float(np.mean(its)), 1),
+                    "tile_rows": info["tile_rows"], "grid": info["grid"], "tiles": info["ntiles"]},
+        "sequential_single_solver": {"ms": round(ms_s, 3),
+                                     "max_iter_diff_vs_batched": int(np.max(np.abs(np.array(seq_it) - np.array(its))))},
+        "speedup_batched_vs_sequential": round(ms_s / ms_b, 3)}
+    return out
+
+
+# ------------------------------------------------------------------------------------------
 def oracle_sample(args, gpu_iters=None):
     """The CPU oracle, unchanged, on a bounded sample of the same workload: the full setup
     (block LU inverses + rounding) and args.cpu_iters PCG iterations, scaled to a whole
@@ -428,6 +545,8 @@ def main():
         dist = tdist
     out = run_ours(args, rank, world, dist)
     if rank == 0 and world == 1 and not args.profile_iters:
+        if not args.no_configs:
+            out["other_configs"] = other_configs()
         out["cpu_baseline"] = oracle_sample(args, out["iters"])
     if rank == 0:
         print(json.dumps(out))

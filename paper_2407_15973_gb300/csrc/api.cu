@@ -15,6 +15,7 @@
 #include "sell.cuh"
 #include "setup.cuh"
 #include "spmv.cuh"
+#include "update.cuh"
 
 namespace mpbjac {
 
@@ -55,103 +56,6 @@ static int vec_grid(int n) {
     return g < 1 ? 1 : g;
 }
 
-static int vec_grid2(int n) {
-    int g = sm_count() * 8;
-    const int need = (n / 2 + kNT - 1) / kNT;
-    if (g > need) g = need;
-    if (g > kMaxGrid) g = kMaxGrid;
-    return g < 1 ? 1 : g;
-}
-
-// aMP loop: r -= alpha q, relres = ||r|| / ||b||, convergence test, precision for the next
-// preconditioner application (Algorithms 3.2 / 3.3 read this relres). r, q: 16-byte aligned.
-__global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
-                                                  double *part, SolverState *S) {
-    pdl_enter();
-    __shared__ double red[kWarps];
-    if (S->state != kRunning) return;
-    const double alpha = S->alpha;
-    double rr = 0.0;
-    const int n2 = n >> 1;
-    const double2 *q2 = reinterpret_cast<const double2 *>(q);
-    double2 *r2 = reinterpret_cast<double2 *>(r);
-#pragma unroll 2
-    for (int i = blockIdx.x * kNT + threadIdx.x; i < n2; i += gridDim.x * kNT) {
-        const double2 qv = q2[i];
-        double2 rv = r2[i];
-        rv.x = fma(-alpha, qv.x, rv.x);
-        rv.y = fma(-alpha, qv.y, rv.y);
-        r2[i] = rv;
-        rr = fma(rv.x, rv.x, rr);
-        rr = fma(rv.y, rv.y, rr);
-    }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const double v = fma(-alpha, q[n - 1], r[n - 1]);
-        r[n - 1] = v;
-        rr = fma(v, v, rr);
-    }
-    const double bsum = block_sum<kNT>(rr, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
-    if (!last_cta(&S->tickets[kTicketUpdR])) return;
-    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
-    if (threadIdx.x != 0) return;
-    S->iter += 1;
-    S->x_pending = 1;
-    S->rr = t;
-    const double rel = sqrt(t) / S->bnorm;
-    S->relres = rel;
-    if (S->hist) S->hist[S->iter] = rel;
-    if (!(rel < 1.0e308)) S->state = kBreakdown;
-    else if (rel <= S->tol) S->state = kConverged;
-    else if (S->iter >= S->maxit) S->state = kMaxit;
-    S->use_low = choose_low(S, rel);
-}
-
-// x += alpha p (the update deferred from this iteration); p = z + beta p while running.
-// The state it reads was final before this kernel started, so thread 0 of CTA 0 sets the
-// graph's while-condition without any grid-wide step (x_pending is cleared by the next
-// SpMV). z and p are 16-byte aligned (handle memory); x is the caller's vector and is checked.
-__global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
-                                                   SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
-    pdl_enter();
-    const int xp = S->x_pending;
-    const int run = S->state == kRunning;
-    double *__restrict__ x = S->x;
-    const double alpha = S->alpha, beta = S->beta;
-    const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
-    if ((xp | run) && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        const int n2 = n >> 1;
-        const double2 *z2 = reinterpret_cast<const double2 *>(z);
-        double2 *p2 = reinterpret_cast<double2 *>(p);
-        double2 *x2 = reinterpret_cast<double2 *>(x);
-#pragma unroll 2
-        for (int i = gid; i < n2; i += stride) {
-            const double2 pv = p2[i];
-            if (xp) {
-                double2 xv = x2[i];
-                xv.x = fma(alpha, pv.x, xv.x);
-                xv.y = fma(alpha, pv.y, xv.y);
-                x2[i] = xv;
-            }
-            if (run) {
-                const double2 zv = z2[i];
-                p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
-            }
-        }
-        if ((n & 1) && gid == 0) {
-            const double pi = p[n - 1];
-            if (xp) x[n - 1] = fma(alpha, pi, x[n - 1]);
-            if (run) p[n - 1] = fma(beta, pi, z[n - 1]);
-        }
-    } else if (xp | run) {
-        for (int i = gid; i < n; i += stride) {
-            const double pi = p[i];
-            if (xp) x[i] = fma(alpha, pi, x[i]);
-            if (run) p[i] = fma(beta, pi, z[i]);
-        }
-    }
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, run ? 1u : 0u);
-}
 
 // element-wise f = RNE binary32 of x and w = f widened back, both by the integer routines the
 // apply kernels use
@@ -726,6 +630,12 @@ static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool l
     return launch_apply_generic(mode, lo, hi, io, h->d_S, st);
 }
 
+#define MPB_TRY_RC(expr)          \
+    do {                          \
+        const int rc_ = (expr);   \
+        if (rc_) return rc_;      \
+    } while (0)
+
 // Iterations per body of the device-side while loop. After convergence the remaining copies
 // of the body return at once; the loop condition is evaluated once per body.
 constexpr int kBodyIters = 4;
@@ -759,8 +669,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     pdl_set(pdl);
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
     if (temporal) {
-        MPB_CUDA(launch_kernel(k_update_r, vec_grid2(h->n), kNT, 0, cs, h->n, (const double *)h->d_q, h->d_r,
-                               h->d_part, h->d_S));
+        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
         if (rc) return rc;
@@ -776,8 +685,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         *launches += 1;
     }
     if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));
-    MPB_CUDA(launch_kernel(k_update_xp, vec_grid2(h->n), kNT, 0, cs, h->n, (const double *)h->d_z, h->d_p, h->d_S,
-                           cond, set_cond ? 1 : 0));
+    MPB_TRY_RC(launch_update_xp(h->n, h->d_z, h->d_p, h->d_S, cond, set_cond ? 1 : 0, cs));
     *launches += 1;
     if (ev) MPB_CUDA(cudaEventRecord(ev[4], cs));
     return MPBJAC_OK;

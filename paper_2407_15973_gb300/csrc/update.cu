@@ -1,0 +1,117 @@
+// Vector kernels of the PCG loop (Section 3.2 recurrences): r -= alpha q with ||r|| for the
+// aMP loop (Algorithms 3.2 / 3.3 read that relres), and x += alpha p, p = z + beta p.
+#include "common.cuh"
+#include "update.cuh"
+
+namespace mpbjac {
+
+static int vec_grid2(int n) {
+    int g = sm_count() * 8;
+    const int need = (n / 2 + kNT - 1) / kNT;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return g < 1 ? 1 : g;
+}
+
+// aMP loop: r -= alpha q, relres = ||r|| / ||b||, convergence test, precision for the next
+// preconditioner application (Algorithms 3.2 / 3.3 read this relres). r, q: 16-byte aligned.
+__global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
+                                                  double *part, SolverState *S) {
+    pdl_enter();
+    __shared__ double red[kWarps];
+    if (S->state != kRunning) return;
+    const double alpha = S->alpha;
+    double rr = 0.0;
+    const int n2 = n >> 1;
+    const double2 *q2 = reinterpret_cast<const double2 *>(q);
+    double2 *r2 = reinterpret_cast<double2 *>(r);
+#pragma unroll 2
+    for (int i = blockIdx.x * kNT + threadIdx.x; i < n2; i += gridDim.x * kNT) {
+        const double2 qv = q2[i];
+        double2 rv = r2[i];
+        rv.x = fma(-alpha, qv.x, rv.x);
+        rv.y = fma(-alpha, qv.y, rv.y);
+        r2[i] = rv;
+        rr = fma(rv.x, rv.x, rr);
+        rr = fma(rv.y, rv.y, rr);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const double v = fma(-alpha, q[n - 1], r[n - 1]);
+        r[n - 1] = v;
+        rr = fma(v, v, rr);
+    }
+    const double bsum = block_sum<kNT>(rr, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+    if (!last_cta(&S->tickets[kTicketUpdR])) return;
+    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
+    if (threadIdx.x != 0) return;
+    S->iter += 1;
+    S->x_pending = 1;
+    S->rr = t;
+    const double rel = sqrt(t) / S->bnorm;
+    S->relres = rel;
+    if (S->hist) S->hist[S->iter] = rel;
+    if (!(rel < 1.0e308)) S->state = kBreakdown;
+    else if (rel <= S->tol) S->state = kConverged;
+    else if (S->iter >= S->maxit) S->state = kMaxit;
+    S->use_low = choose_low(S, rel);
+}
+
+// x += alpha p (the update deferred from this iteration); p = z + beta p while running.
+// The state it reads was final before this kernel started, so thread 0 of CTA 0 sets the
+// graph's while-condition without any grid-wide step (x_pending is cleared by the next
+// SpMV). z and p are 16-byte aligned (handle memory); x is the caller's vector and is checked.
+__global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
+                                                   SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
+    pdl_enter();
+    const int xp = S->x_pending;
+    const int run = S->state == kRunning;
+    double *__restrict__ x = S->x;
+    const double alpha = S->alpha, beta = S->beta;
+    const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
+    if ((xp | run) && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const int n2 = n >> 1;
+        const double2 *z2 = reinterpret_cast<const double2 *>(z);
+        double2 *p2 = reinterpret_cast<double2 *>(p);
+        double2 *x2 = reinterpret_cast<double2 *>(x);
+#pragma unroll 2
+        for (int i = gid; i < n2; i += stride) {
+            const double2 pv = p2[i];
+            if (xp) {
+                double2 xv = x2[i];
+                xv.x = fma(alpha, pv.x, xv.x);
+                xv.y = fma(alpha, pv.y, xv.y);
+                x2[i] = xv;
+            }
+            if (run) {
+                const double2 zv = z2[i];
+                p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+            }
+        }
+        if ((n & 1) && gid == 0) {
+            const double pi = p[n - 1];
+            if (xp) x[n - 1] = fma(alpha, pi, x[n - 1]);
+            if (run) p[n - 1] = fma(beta, pi, z[n - 1]);
+        }
+    } else if (xp | run) {
+        for (int i = gid; i < n; i += stride) {
+            const double pi = p[i];
+            if (xp) x[i] = fma(alpha, pi, x[i]);
+            if (run) p[i] = fma(beta, pi, z[i]);
+        }
+    }
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, run ? 1u : 0u);
+}
+
+int launch_update_r(int n, const double *q, double *r, double *part, SolverState *S, cudaStream_t st) {
+    MPB_CUDA(launch_kernel(k_update_r, vec_grid2(n), kNT, 0, st, n, q, r, part, S));
+    return MPBJAC_OK;
+}
+
+int launch_update_xp(int n, const double *z, double *p, SolverState *S, cudaGraphConditionalHandle cond,
+                     int use_cond, cudaStream_t st) {
+    MPB_CUDA(launch_kernel(k_update_xp, vec_grid2(n), kNT, 0, st, n, z, p, S, cond, use_cond));
+    return MPBJAC_OK;
+}
+
+}  // namespace mpbjac
