@@ -282,8 +282,9 @@ static int choose_apply_kind(bjac_handle *h) {
 // slice's head prefetched. By default the copy is built when its padding stays under 1.5 nnz
 // and y = A x is timed with the CSR kernel and both SELL-32 kernels (interleaved rounds on a
 // nonzero x, median of 7 after a warm-up round, on the handle's stream); the fastest is
-// kept, and the decision is cached per (n, nnz) for the life of the process. All give the
-// same result bits.
+// kept (the prefetching one only when 3 % faster than the better of the others), and the
+// decision is cached per (n, nnz) for the life of the process. All give the same result
+// bits.
 struct SpFmtTune {
     int n, nnz, choice;       // 0 CSR, 1 SELL-32, 2 SELL-32 with prefetch
     float ms[3];
@@ -343,12 +344,13 @@ static int choose_spmv_format(bjac_handle *h) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int best = 0;
     for (int k = 0; k < 3; ++k) {
         std::sort(t[k] + 1, t[k] + kRounds);
         h->spmv_ms[k] = t[k][1 + (kRounds - 1) / 2];
-        if (h->spmv_ms[k] < h->spmv_ms[best]) best = k;
     }
+    // the prefetching kernel holds more registers: keep it only when clearly faster
+    int best = h->spmv_ms[1] < h->spmv_ms[0] ? 1 : 0;
+    if (h->spmv_ms[2] < 0.97f * h->spmv_ms[best]) best = 2;
     h->use_sell = best > 0;
     if (best > 0) h->sell.kernel = best - 1;
     else sell_free(&h->sell);

@@ -80,8 +80,11 @@ def test_default_layout_is_timed_and_reported(B):
     try:
         f = h.spmv_format()
         assert all(t > 0 for t in f["ms"])
-        names = ["csr", "sell32", "sell32-prefetch"]
-        assert f["format"] == names[int(np.argmin(f["ms"]))]
+        ms = f["ms"]
+        best = 1 if ms[1] < ms[0] else 0
+        if ms[2] < 0.97 * ms[best]:
+            best = 2
+        assert f["format"] == ["csr", "sell32", "sell32-prefetch"][best]
         assert f["entries"] == (_entries(pr.A) if f["format"] != "csr" else 0)
     finally:
         h.close()
