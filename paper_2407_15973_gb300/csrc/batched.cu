@@ -6,9 +6,13 @@
 // relres, iteration count, state) and converges on its own; the rows of finished systems are
 // skipped.
 //
-// Work is cut into tiles of TR rows that never cross a system (nor a diagonal block).
-// Per iteration the kernel runs five phases separated by grid barriers:
-//   A  q = A p on the tiles of running systems, per-tile partial of p.q
+// Work is cut into tiles of TR rows that never cross a system (nor a diagonal block). Each
+// tile's rows are also stored as 32-row slices in sliced-ELLPACK form (column-major, padded
+// to the slice's longest row, padding column -1), so the SpMV's loads are coalesced and each
+// row keeps its FMA chain in CSR order. Per iteration the kernel runs five phases separated
+// by grid barriers, over a list of the tiles whose system is still running (rebuilt after
+// every iteration, so finished systems cost nothing):
+//   A  q = A p on the listed tiles, per-tile partial of p.q
 //   B  per system: sigma = sum of its tiles' partials (fixed order), alpha = rho / sigma
 //   C  r -= alpha q, z = M^-1 r (Algorithm 3.1 for low blocks), per-tile partials r.r, r.z
 //   D  per system: relres, convergence / maxit, beta = rho' / rho
@@ -27,6 +31,7 @@
 
 #include "apply.cuh"
 #include "common.cuh"
+#include "rows.cuh"
 #include "setup.cuh"
 #include "tma.cuh"
 
@@ -45,6 +50,11 @@ struct BatchDev {
     const int32_t *tile_sys;     // [ntiles] owning system
     const int32_t *tile_blk;     // [ntiles] first block of each tile
     const int32_t *sys_tile;     // [nsys+1] first tile of each system
+    const int32_t *soff;         // [ntiles * TR/32 + 1] first stored entry of each 32-row slice
+    const int32_t *scol;         // sliced-ELLPACK column indices (-1: padding)
+    const double *sval;          // sliced-ELLPACK values
+    int32_t *alist;              // [2 * ntiles] two lists of the running systems' tiles (any order)
+    int32_t *nlist;              // [2] their lengths; the lists are used alternately
     const double *b;
     double *x, *r, *z, *p, *q;
     double *part;                // [2 * ntiles]
@@ -86,20 +96,43 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
     return *((volatile int32_t *)d.err) == 0;
 }
 
-// q or r rows of a tile: each lane owns one row (TR = 32) or two rows (TR = 64)
+// q or r rows of a tile: each lane owns one row of each of the tile's 32-row slices
 template <int TR>
 __device__ __forceinline__ void tile_spmv(const BatchDev &d, int t, const double *xin, int mode,
                                           double &part_a, double &part_b) {
     // mode 0: q = A p, part_a += p.q ; mode 1: r = b - A x, part_a += r.r, part_b += b.b
     const int lane = threadIdx.x & 31;
     const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
+        if (r0 + h * 32 >= r1) break;                    // same in every lane
         const int row = r0 + h * 32 + lane;
-        if (row >= r1) continue;
+        const int sl = t * (TR / 32) + h;
+        const int o0 = d.soff[sl];
+        const int len = (d.soff[sl + 1] - o0) >> 5;
+        const double *pv = d.sval + o0 + lane;
+        const int32_t *pc = d.scol + o0 + lane;
         double acc = 0.0;
-        const int lo = d.rowptr[row], hi = d.rowptr[row + 1];
-        for (int k = lo; k < hi; ++k) acc = fma(d.val[k], __ldcg(xin + d.colidx[k]), acc);
+        for (int j = 0; j < len; j += 4) {
+            double v[4], xv[4];
+            int c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j + u < len) {
+                    v[u] = __ldcs(pv + 32 * (j + u));
+                    c[u] = __ldcs(pc + 32 * (j + u));
+                } else {
+                    v[u] = 0.0;
+                    c[u] = -1;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldcg(xin + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+        }
+        if (row >= r1) continue;
         if (mode == 0) {
             d.q[row] = acc;
             part_a = fma(acc, __ldcg(xin + row), part_a);
@@ -120,7 +153,7 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
                                            float *s_rh, double *s_r, double &part_a, double &part_b) {
     const int lane = threadIdx.x & 31;
     const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
         if (row < r1) {
@@ -135,7 +168,7 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
         }
     }
     __syncwarp();
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
         if (row < r1) {
@@ -146,8 +179,22 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
             const int i = row - bs0, off = bs0 - r0;
             const int f = d.fmt[bk];
             const uint8_t *base = d.pool + d.qoff[bk];
+            const int eb = f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2;
             double zi;
-            if (f == BJAC_FP64) {
+            if (((bs * eb) & 15) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0 && (off & 3) == 0) {
+                // 16-byte aligned rows and r slices: the lane reads its own row with vector loads
+                const int vpr = bs * eb / 16;
+                const uint4 *rowq = reinterpret_cast<const uint4 *>(base) + (size_t)i * vpr;
+                if (f == BJAC_FP64) {
+                    zi = vec_row_f64(rowq, vpr, s_r + off);
+                } else {
+                    float acc;
+                    if (f == BJAC_FP32) acc = vec_row_low<float>(rowq, vpr, s_rh + off);
+                    else if (f == BJAC_BF16) acc = vec_row_low<__nv_bfloat16>(rowq, vpr, s_rh + off);
+                    else acc = vec_row_low<__half>(rowq, vpr, s_rh + off);
+                    zi = f32_to_f64(acc * d.scale[bk]);
+                }
+            } else if (f == BJAC_FP64) {
                 const double *G = reinterpret_cast<const double *>(base);
                 double acc = 0.0;
                 for (int j = 0; j < bs; ++j) acc = fma(G[(size_t)j * bs + i], s_r[off + j], acc);
@@ -175,9 +222,9 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
 }
 
 template <int TR>
-__global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
-    __shared__ float s_rh[kWarps][TR];
-    __shared__ double s_r[kWarps][TR];
+__global__ void __launch_bounds__(kNT, 3) k_pcg_batched(BatchDev d) {
+    __shared__ __align__(16) float s_rh[kWarps][TR];
+    __shared__ __align__(16) double s_r[kWarps][TR];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
 
@@ -193,12 +240,39 @@ __global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
             }
         }
     };
+    // the same per-tile work over the list of running tiles (built by build_list)
+    auto per_listed = [&](int cnt_slot, auto &&fn) {
+        const int cnt = __ldcg(d.nlist + cnt_slot);
+        for (int i = gw; i < cnt; i += nw) {
+            const int t = __ldcg(d.alist + (size_t)cnt_slot * d.ntiles + i);
+            double a = 0.0, b2 = 0.0;
+            fn(t, a, b2);
+            a = warp_sum(a);
+            b2 = warp_sum(b2);
+            if (lane == 0) {
+                d.part[2 * t] = a;
+                d.part[2 * t + 1] = b2;
+            }
+        }
+    };
+    // List of the tiles whose system is running, appended (in any order) to list `sl`, whose
+    // length must be zero. A grid barrier must follow before the list is read. The list not in
+    // use has its length cleared in phase B, after the last read of its old contents.
+    auto build_list = [&](int sl) {
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+        for (int t = tid; t < d.ntiles; t += nthr)
+            if (__ldcg(d.state + d.tile_sys[t]) == kRunning)
+                d.alist[(size_t)sl * d.ntiles + atomicAdd(d.nlist + sl, 1)] = t;
+    };
     auto sys_sum = [&](int s, int which) {     // fixed-order sum of system s's tile partials
         double v = 0.0;
         for (int t = d.sys_tile[s] + lane; t < d.sys_tile[s + 1]; t += 32) v += __ldcg(d.part + 2 * t + which);
         return warp_sum(v);
     };
 
+    // which list length is current: it alternates at every list build; the loop ends with an
+    // empty list in the current slot, so a restart builds into it again
+    int slot = 0;
     // ---- start: r = b - A x, relres, then z = M^-1 r, p = z, rho ----------------------
     for (int restart = 0; restart < 3; ++restart) {
         per_tile([&](int t, double &a, double &b2) {
@@ -244,17 +318,18 @@ __global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 1;
         if (!grid_barrier(d)) return;
+        build_list(slot);
+        if (!grid_barrier(d)) return;
 
         // ---- iterations --------------------------------------------------------------
         while (*((volatile int32_t *)d.active) != 0) {
             // A: q = A p, p.q
-            per_tile([&](int t, double &a, double &b2) {
-                if (__ldcg(d.state + d.tile_sys[t]) != kRunning) return;
-                tile_spmv<TR>(d, t, d.p, 0, a, b2);
-            });
+            per_listed(slot, [&](int t, double &a, double &b2) { tile_spmv<TR>(d, t, d.p, 0, a, b2); });
             if (!grid_barrier(d)) return;
-            // B: alpha per system
+            // B: alpha per system; the previous iteration's x updates are done
+            if (blockIdx.x == 0 && threadIdx.x == 0) d.nlist[slot ^ 1] = 0;
             for (int s = gw; s < d.nsys; s += nw) {
+                if (lane == 0) d.xpend[s] = 0;
                 if (d.state[s] != kRunning) continue;
                 const double sigma = sys_sum(s, 0);
                 if (lane == 0) {
@@ -264,9 +339,9 @@ __global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
             }
             if (!grid_barrier(d)) return;
             // C: r -= alpha q, z = M^-1 r, r.r and r.z
-            per_tile([&](int t, double &a, double &b2) {
+            per_listed(slot, [&](int t, double &a, double &b2) {
                 const int s = d.tile_sys[t];
-                if (__ldcg(d.state + s) != kRunning) return;
+                if (__ldcg(d.state + s) != kRunning) return;          // sigma broke down in B
                 tile_apply<TR>(d, t, __ldcg(d.alpha + s), 1, 0, s_rh[warp], s_r[warp], a, b2);
             });
             if (!grid_barrier(d)) return;
@@ -295,8 +370,8 @@ __global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
             if (!grid_barrier(d)) return;
             if (lane == 0 && my_active) atomicOr(d.active, 1);
-            // E: x += alpha p, p = z + beta p
-            per_tile([&](int t, double &, double &) {
+            // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped)
+            per_listed(slot, [&](int t, double &, double &) {
                 const int s = d.tile_sys[t];
                 const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
                 if (!xp && !run) return;
@@ -308,11 +383,12 @@ __global__ void __launch_bounds__(kNT) k_pcg_batched(BatchDev d) {
                     if (run) d.p[row] = fma(be, pi, d.z[row]);
                 }
             });
-            if (!grid_barrier(d)) return;
-            for (int s = gw; s < d.nsys; s += nw)
-                if (lane == 0) d.xpend[s] = 0;
+            slot ^= 1;
+            build_list(slot);
             if (!grid_barrier(d)) return;
         }
+        for (int s = gw; s < d.nsys; s += nw)
+            if (lane == 0) d.xpend[s] = 0;
         // ---- true residual of the converged systems; restart those that miss tol -----
         per_tile([&](int t, double &a, double &b2) {
             const int s = d.tile_sys[t];
@@ -367,7 +443,10 @@ struct bjac_batch {
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
     double *sd = nullptr;          // per-system doubles: bnorm rho alpha beta relres true_relres
     int32_t *si = nullptr;         // per-system ints: iter state xpend restarts
-    unsigned int *ctl = nullptr;   // barrier count, generation, err, active
+    unsigned int *ctl = nullptr;   // barrier count, generation, err, active, list lengths [2]
+    int32_t *soff = nullptr, *scol = nullptr, *alist = nullptr;   // sliced-ELLPACK tiles, tile lists
+    double *sval = nullptr;
+    std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
     int grid = 0;
     float tune_ms[2] = {0, 0};
     cudaGraph_t graph = nullptr;
@@ -385,7 +464,7 @@ static void free_batch(bjac_batch *h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     void *ptrs[] = {h->rowptr, h->colidx, h->val, h->block_ptr, h->goff, h->fmt, h->scale, h->qoff, h->pool, h->feat,
                     h->kap, h->status, h->tile_row, h->tile_sys, h->tile_blk, h->d_sys_tile, h->b, h->x, h->r, h->z,
-                    h->p, h->q, h->part, h->sd, h->si, h->ctl};
+                    h->p, h->q, h->part, h->sd, h->si, h->ctl, h->soff, h->scol, h->sval, h->alist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -443,6 +522,11 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     d.bar_gen = h->ctl + 1;
     d.err = reinterpret_cast<int32_t *>(h->ctl + 2);
     d.active = reinterpret_cast<int32_t *>(h->ctl + 3);
+    d.nlist = reinterpret_cast<int32_t *>(h->ctl + 4);
+    d.soff = h->soff;
+    d.scol = h->scol;
+    d.sval = h->sval;
+    d.alist = h->alist;
     return d;
 }
 
@@ -468,6 +552,28 @@ static int max_coresident(int tr) {
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<64>, kNT, 0);
     if (e != cudaSuccess || per < 1) per = 1;
     return sm_count() * per;
+}
+
+// one warp per 32-row slice of a tile: its rows' entries column-major, padded with (0, -1)
+__global__ void k_batch_ell(int nslices, int spt, const int32_t *__restrict__ tile_row,
+                            const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                            const double *__restrict__ val, const int32_t *__restrict__ soff,
+                            int32_t *__restrict__ scol, double *__restrict__ sval) {
+    const int lane = threadIdx.x & 31;
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nslices) return;
+    const int t = sl / spt, hh = sl - t * spt;
+    const int r0 = tile_row[t] + 32 * hh, r1 = tile_row[t + 1];
+    const int o0 = soff[sl], len = (soff[sl + 1] - o0) >> 5;
+    const int row = r0 + lane;
+    const int lo = row < r1 ? rowptr[row] : 0;
+    const int rl = row < r1 ? rowptr[row + 1] - lo : 0;
+    for (int j = 0; j < len; ++j) {
+        const size_t k = (size_t)o0 + 32 * (size_t)j + lane;
+        const bool in = j < rl;
+        sval[k] = in ? val[lo + j] : 0.0;
+        scol[k] = in ? colidx[lo + j] : -1;
+    }
 }
 
 static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
@@ -508,13 +614,47 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
     MPB_CUDA(cudaMemcpy(h->d_sys_tile, h->sys_tile.data(), sizeof(int32_t) * (h->nsys + 1), cudaMemcpyHostToDevice));
     cudaFree(h->part);
     MPB_CUDA(cudaMalloc(&h->part, sizeof(double) * 2 * h->ntiles));
+    // sliced-ELLPACK copy of every tile (32-row slices padded to their longest row)
+    const int spt = tr / 32;
+    const size_t nsl = (size_t)h->ntiles * spt;
+    std::vector<int32_t> so(nsl + 1);
+    long long acc = 0;
+    for (int t = 0; t < h->ntiles; ++t) {
+        for (int hh = 0; hh < spt; ++hh) {
+            so[(size_t)t * spt + hh] = (int32_t)acc;
+            const int r0 = trow[t] + 32 * hh, r1 = std::min(trow[t + 1], r0 + 32);
+            int len = 0;
+            for (int row = r0; row < r1; ++row) len = std::max(len, h->h_rowptr[row + 1] - h->h_rowptr[row]);
+            acc += 32ll * len;
+            if (acc > (long long)INT32_MAX - 64) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
+        }
+    }
+    so[nsl] = (int32_t)acc;
+    cudaFree(h->soff);
+    cudaFree(h->scol);
+    cudaFree(h->sval);
+    cudaFree(h->alist);
+    h->soff = nullptr;
+    h->scol = nullptr;
+    h->sval = nullptr;
+    h->alist = nullptr;
+    MPB_CUDA(cudaMalloc(&h->soff, sizeof(int32_t) * (nsl + 1)));
+    MPB_CUDA(cudaMalloc(&h->scol, sizeof(int32_t) * std::max(1ll, acc)));
+    MPB_CUDA(cudaMalloc(&h->sval, sizeof(double) * std::max(1ll, acc)));
+    MPB_CUDA(cudaMalloc(&h->alist, sizeof(int32_t) * 2 * (size_t)h->ntiles));
+    MPB_CUDA(cudaMemcpy(h->soff, so.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    const int grid = (int)((nsl * 32 + 255) / 256);
+    k_batch_ell<<<grid, 256, 0, h->stream>>>((int)nsl, spt, h->tile_row, h->rowptr, h->colidx, h->val, h->soff,
+                                             h->scol, h->sval);
+    MPB_CUDA(cudaGetLastError());
+    MPB_CUDA(cudaStreamSynchronize(h->stream));
     h->tile_rows = tr;
     return MPBJAC_OK;
 }
 
 static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bool use_graph) {
     BatchDev d = batch_dev(h, tol, maxit);
-    MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 4 * sizeof(unsigned int), st));
+    MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned int), st));
     if (!use_graph) return h->tile_rows == 32 ? launch_batched<32>(h, d, st, h->grid) : launch_batched<64>(h, d, st, h->grid);
     if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -610,6 +750,9 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         }
         const int32_t last = nz;
         BTRY(cudaMemcpyAsync(h->rowptr + n_tot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        h->h_rowptr.resize(n_tot + 1);
+        BTRY(cudaMemcpyAsync(h->h_rowptr.data(), h->rowptr, sizeof(int32_t) * (n_tot + 1), cudaMemcpyDeviceToHost,
+                             st));
         BTRY(cudaStreamSynchronize(st));
     }
     BTRY(cudaMalloc(&h->block_ptr, sizeof(int32_t) * (nb_tot + 1)));
@@ -672,7 +815,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     BTRY(cudaMalloc(&h->q, sizeof(double) * n_tot));
     BTRY(cudaMalloc(&h->sd, sizeof(double) * 6 * nsys));
     BTRY(cudaMalloc(&h->si, sizeof(int32_t) * 4 * nsys));
-    BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 4));
+    BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 6));
     BTRY(cudaMalloc(&h->d_sys_tile, sizeof(int32_t) * (nsys + 1)));
     // autotuner: tile height (32 or 64 rows per warp task) timed on 20 iterations of this batch
     {
