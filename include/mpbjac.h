@@ -146,8 +146,9 @@ typedef struct bjac_batch bjac_batch;
 /* Set up nsys independent systems A[s] (DEVICE CSR arrays, copied into one block-diagonal
  * matrix owned by the batch) with contiguous blocks block_ptr[s] (HOST, nb[s]+1 entries,
  * every block 1..32 rows). policy: select UNIFORM, FIXED or RULE (no aMP switching);
- * policy.stream is used for every call. The setup also times the persistent kernel with 32-
- * and 64-row work tiles on this batch (20 iterations each) and keeps the faster tile height.
+ * policy.stream is used for every call. The setup also times six variants of the persistent
+ * kernel (32- or 64-row work tiles, registers for 2, 4 or 6 CTAs per SM) on this batch
+ * (20 iterations each) and keeps the fastest.
  * Errors: INVALID_ARG, UNSUPPORTED, NOT_SPD, CUDA, NO_MEMORY. */
 int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *const *block_ptr, const int32_t *nb,
                      const bjac_policy *policy, bjac_batch **out);
@@ -161,8 +162,9 @@ int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *const *bloc
 int pcg_solve_batched(bjac_batch *h, const double *const *b, double *const *x, double tol, int32_t maxit,
                       pcg_stats *stats);
 
-/* Work tiles, tile height chosen by the setup's timing, grid size and the timings (ms[2]:
- * 32-row and 64-row tiles) of a batch. All outputs HOST and nullable. */
+/* Work tiles, tile height chosen by the setup's timing, grid size and the timings of the
+ * six kernel variants (tune_ms[6]: 32-row tiles with registers for 2, 4, 6 CTAs per SM, then
+ * 64-row tiles likewise) of a batch. All outputs HOST and nullable. */
 int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid, float *tune_ms);
 
 void bjac_batch_destroy(bjac_batch *h);

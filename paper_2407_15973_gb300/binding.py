@@ -340,7 +340,7 @@ class Batch:
 
     def info(self):
         nt, tr, g = C.c_int32(), C.c_int32(), C.c_int32()
-        ms = (C.c_float * 2)()
+        ms = (C.c_float * 6)()
         _check(lib().bjac_batch_info(self.h, C.byref(nt), C.byref(tr), C.byref(g), ms))
         return dict(ntiles=nt.value, tile_rows=tr.value, grid=g.value, tune_ms=list(ms))
 

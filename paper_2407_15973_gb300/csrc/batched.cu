@@ -221,8 +221,8 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
     __syncwarp();
 }
 
-template <int TR>
-__global__ void __launch_bounds__(kNT, 3) k_pcg_batched(BatchDev d) {
+template <int TR, int MINB>
+__global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
     __shared__ __align__(16) float s_rh[kWarps][TR];
     __shared__ __align__(16) double s_r[kWarps][TR];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -448,7 +448,8 @@ struct bjac_batch {
     double *sval = nullptr;
     std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
     int grid = 0;
-    float tune_ms[2] = {0, 0};
+    float tune_ms[6] = {0, 0, 0, 0, 0, 0};   // timings of the kernel variants
+    int variant = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double tol_cached = -1.0;
@@ -530,8 +531,13 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     return d;
 }
 
-template <int TR>
-static int launch_batched(bjac_batch *h, const BatchDev &d, cudaStream_t st, int grid) {
+// kernel variants the setup times: tile height x CTAs per SM the registers are sized for
+constexpr int kBatchVariants = 6;
+constexpr int kVarTR[kBatchVariants] = {32, 32, 32, 64, 64, 64};
+constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6};
+
+template <int TR, int MINB>
+static int launch_batched_t(const BatchDev &d, cudaStream_t st, int grid) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kNT);
@@ -542,15 +548,40 @@ static int launch_batched(bjac_batch *h, const BatchDev &d, cudaStream_t st, int
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MPB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batched<TR>, d));
+    MPB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batched<TR, MINB>, d));
     return MPBJAC_OK;
 }
 
-static int max_coresident(int tr) {
+static int launch_batched(int variant, const BatchDev &d, cudaStream_t st, int grid) {
+    switch (variant) {
+        case 0: return launch_batched_t<32, 2>(d, st, grid);
+        case 1: return launch_batched_t<32, 4>(d, st, grid);
+        case 2: return launch_batched_t<32, 6>(d, st, grid);
+        case 3: return launch_batched_t<64, 2>(d, st, grid);
+        case 4: return launch_batched_t<64, 4>(d, st, grid);
+        default: return launch_batched_t<64, 6>(d, st, grid);
+    }
+}
+
+template <int TR, int MINB>
+static int per_sm_of() {
     int per = 0;
-    cudaError_t e = tr == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<32>, kNT, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<64>, kNT, 0);
-    if (e != cudaSuccess || per < 1) per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<TR, MINB>, kNT, 0) != cudaSuccess || per < 1)
+        per = 1;
+    return per;
+}
+
+// CTAs of a variant that are co-resident on the GPU (the cooperative grid)
+static int max_coresident(int variant) {
+    int per = 1;
+    switch (variant) {
+        case 0: per = per_sm_of<32, 2>(); break;
+        case 1: per = per_sm_of<32, 4>(); break;
+        case 2: per = per_sm_of<32, 6>(); break;
+        case 3: per = per_sm_of<64, 2>(); break;
+        case 4: per = per_sm_of<64, 4>(); break;
+        default: per = per_sm_of<64, 6>(); break;
+    }
     return sm_count() * per;
 }
 
@@ -655,7 +686,7 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
 static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bool use_graph) {
     BatchDev d = batch_dev(h, tol, maxit);
     MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned int), st));
-    if (!use_graph) return h->tile_rows == 32 ? launch_batched<32>(h, d, st, h->grid) : launch_batched<64>(h, d, st, h->grid);
+    if (!use_graph) return launch_batched(h->variant, d, st, h->grid);
     if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
         if (h->graph) cudaGraphDestroy(h->graph);
@@ -664,7 +695,7 @@ static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bo
         cudaStream_t cs;
         MPB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         MPB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        int rc = h->tile_rows == 32 ? launch_batched<32>(h, d, cs, h->grid) : launch_batched<64>(h, d, cs, h->grid);
+        int rc = launch_batched(h->variant, d, cs, h->grid);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -817,17 +848,22 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     BTRY(cudaMalloc(&h->si, sizeof(int32_t) * 4 * nsys));
     BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 6));
     BTRY(cudaMalloc(&h->d_sys_tile, sizeof(int32_t) * (nsys + 1)));
-    // autotuner: tile height (32 or 64 rows per warp task) timed on 20 iterations of this batch
+    // autotuner: tile height (32 or 64 rows per warp task) and CTAs per SM (2, 4, 6: the
+    // register budget of the kernel) timed on 20 iterations of this batch
     {
         BTRY(cudaMemsetAsync(h->b, 0, sizeof(double) * n_tot, st));
         std::vector<double> ones(n_tot, 1.0);
         BTRY(cudaMemcpy(h->b, ones.data(), sizeof(double) * n_tot, cudaMemcpyHostToDevice));
         float best = 1e30f;
-        int best_tr = 32;
-        for (int tr : {32, 64}) {
-            rc = build_tiles(h, tr, bp);
-            if (rc) return bail(rc);
-            h->grid = max_coresident(tr);
+        int best_v = 0;
+        for (int v = 0; v < kBatchVariants; ++v) {
+            const int tr = kVarTR[v];
+            if (v == 0 || kVarTR[v - 1] != tr) {
+                rc = build_tiles(h, tr, bp);
+                if (rc) return bail(rc);
+            }
+            h->variant = v;
+            h->grid = max_coresident(v);
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 BTRY(cudaMemsetAsync(h->x, 0, sizeof(double) * n_tot, st));
@@ -843,12 +879,15 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
                 cudaEventDestroy(e2);
                 if (rep > 0) t = std::min(t, ms);
             }
-            h->tune_ms[tr == 32 ? 0 : 1] = t;
-            if (t < best) { best = t; best_tr = tr; }
+            h->tune_ms[v] = t;
+            if (t < best) { best = t; best_v = v; }
         }
-        rc = build_tiles(h, best_tr, bp);
-        if (rc) return bail(rc);
-        h->grid = max_coresident(best_tr);
+        if (kVarTR[best_v] != kVarTR[kBatchVariants - 1]) {
+            rc = build_tiles(h, kVarTR[best_v], bp);
+            if (rc) return bail(rc);
+        }
+        h->variant = best_v;
+        h->grid = max_coresident(best_v);
     }
 #undef BTRY
     cudaEventRecord(e1, st);
@@ -930,9 +969,7 @@ extern "C" int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *ti
     if (ntiles) *ntiles = h->ntiles;
     if (tile_rows) *tile_rows = h->tile_rows;
     if (grid) *grid = h->grid;
-    if (tune_ms) {
-        tune_ms[0] = h->tune_ms[0];
-        tune_ms[1] = h->tune_ms[1];
-    }
+    if (tune_ms)
+        for (int v = 0; v < kBatchVariants; ++v) tune_ms[v] = h->tune_ms[v];
     return MPBJAC_OK;
 }
