@@ -50,6 +50,8 @@ struct BatchDev {
     const int32_t *tile_sys;     // [ntiles] owning system
     const int32_t *tile_blk;     // [ntiles] first block of each tile
     const int32_t *sys_tile;     // [nsys+1] first tile of each system
+    const int4 *tinfo;           // [2 * ntiles] per tile: r0, r1, system, first block, common
+                                 // block size (0 if mixed), slice offsets so0, so1, so2
     const int32_t *soff;         // [ntiles * TR/32 + 1] first stored entry of each 32-row slice
     const int32_t *scol;         // sliced-ELLPACK column indices (-1: padding)
     const double *sval;          // sliced-ELLPACK values
@@ -96,43 +98,56 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
     return *((volatile int32_t *)d.err) == 0;
 }
 
+// a tile's description, read with two 16-byte loads
+struct TileInfo {
+    int r0, r1, sys, blk0, ubs, so0, so1, so2;
+};
+
+__device__ __forceinline__ TileInfo load_tile(const BatchDev &d, int t) {
+    const int4 a = __ldg(d.tinfo + 2 * t), b = __ldg(d.tinfo + 2 * t + 1);
+    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
+// U entries of one sliced-ELLPACK row: loads, then gathers, then the FMA chain in order
+template <int U>
+__device__ __forceinline__ void ell_part(const double *__restrict__ pv, const int32_t *__restrict__ pc, int cnt,
+                                         const double *xin, double &acc) {
+    double v[U], xv[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (u < cnt) {
+            v[u] = __ldcs(pv + 32 * u);
+            c[u] = __ldcs(pc + 32 * u);
+        } else {
+            v[u] = 0.0;
+            c[u] = -1;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldcg(xin + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+}
+
 // q or r rows of a tile: each lane owns one row of each of the tile's 32-row slices
 template <int TR>
-__device__ __forceinline__ void tile_spmv(const BatchDev &d, int t, const double *xin, int mode,
+__device__ __forceinline__ void tile_spmv(const BatchDev &d, const TileInfo &ti, const double *xin, int mode,
                                           double &part_a, double &part_b) {
     // mode 0: q = A p, part_a += p.q ; mode 1: r = b - A x, part_a += r.r, part_b += b.b
     const int lane = threadIdx.x & 31;
-    const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
 #pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
-        if (r0 + h * 32 >= r1) break;                    // same in every lane
-        const int row = r0 + h * 32 + lane;
-        const int sl = t * (TR / 32) + h;
-        const int o0 = d.soff[sl];
-        const int len = (d.soff[sl + 1] - o0) >> 5;
+        if (ti.r0 + h * 32 >= ti.r1) break;              // same in every lane
+        const int row = ti.r0 + h * 32 + lane;
+        const int o0 = h == 0 ? ti.so0 : ti.so1;
+        const int len = ((h == 0 ? ti.so1 : ti.so2) - o0) >> 5;
         const double *pv = d.sval + o0 + lane;
         const int32_t *pc = d.scol + o0 + lane;
         double acc = 0.0;
-        for (int j = 0; j < len; j += 4) {
-            double v[4], xv[4];
-            int c[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (j + u < len) {
-                    v[u] = __ldcs(pv + 32 * (j + u));
-                    c[u] = __ldcs(pc + 32 * (j + u));
-                } else {
-                    v[u] = 0.0;
-                    c[u] = -1;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldcg(xin + c[u]) : 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
-        }
-        if (row >= r1) continue;
+        for (int j = 0; j < len; j += 8) ell_part<8>(pv + 32 * j, pc + 32 * j, len - j, xin, acc);
+        if (row >= ti.r1) continue;
         if (mode == 0) {
             d.q[row] = acc;
             part_a = fma(acc, __ldcg(xin + row), part_a);
@@ -149,10 +164,10 @@ __device__ __forceinline__ void tile_spmv(const BatchDev &d, int t, const double
 // z = M^-1 r on a tile (blocks lie inside tiles). mode 0: plain (with p = z when init);
 // mode 1: r -= alpha q first. part_a += r.z, part_b += r.r.
 template <int TR>
-__device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alpha, int fused, int init,
+__device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti, double alpha, int fused, int init,
                                            float *s_rh, double *s_r, double &part_a, double &part_b) {
     const int lane = threadIdx.x & 31;
-    const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
+    const int r0 = ti.r0, r1 = ti.r1;
 #pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
@@ -172,10 +187,19 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, int t, double alph
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
         if (row < r1) {
-            // this row's block
-            int bk = d.tile_blk[t];
-            while (d.block_ptr[bk + 1] <= row) ++bk;
-            const int bs0 = d.block_ptr[bk], bs = d.block_ptr[bk + 1] - bs0;
+            // this row's block: arithmetic when the tile's blocks share one size
+            int bk, bs0, bs;
+            if (ti.ubs > 0) {
+                const int k = (row - r0) / ti.ubs;
+                bk = ti.blk0 + k;
+                bs = ti.ubs;
+                bs0 = r0 + k * bs;
+            } else {
+                bk = ti.blk0;
+                while (d.block_ptr[bk + 1] <= row) ++bk;
+                bs0 = d.block_ptr[bk];
+                bs = d.block_ptr[bk + 1] - bs0;
+            }
             const int i = row - bs0, off = bs0 - r0;
             const int f = d.fmt[bk];
             const uint8_t *base = d.pool + d.qoff[bk];
@@ -230,8 +254,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
 
     auto per_tile = [&](auto &&fn) {
         for (int t = gw; t < d.ntiles; t += nw) {
+            const TileInfo ti = load_tile(d, t);
             double a = 0.0, b2 = 0.0;
-            fn(t, a, b2);
+            fn(t, ti, a, b2);
             a = warp_sum(a);
             b2 = warp_sum(b2);
             if (lane == 0) {
@@ -240,19 +265,28 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
         }
     };
-    // the same per-tile work over the list of running tiles (built by build_list)
-    auto per_listed = [&](int cnt_slot, auto &&fn) {
+    // the same per-tile work over the list of running tiles (built by build_list); the next
+    // listed tile's description is loaded while the current one is processed
+    auto per_listed = [&](int cnt_slot, bool partials, auto &&fn) {
         const int cnt = __ldcg(d.nlist + cnt_slot);
+        const int32_t *lst = d.alist + (size_t)cnt_slot * d.ntiles;
+        int t = gw < cnt ? __ldcg(lst + gw) : 0;
+        TileInfo ti = load_tile(d, gw < cnt ? t : 0);
         for (int i = gw; i < cnt; i += nw) {
-            const int t = __ldcg(d.alist + (size_t)cnt_slot * d.ntiles + i);
+            const int tn = i + nw < cnt ? __ldcg(lst + i + nw) : t;
+            const TileInfo tin = load_tile(d, tn);
             double a = 0.0, b2 = 0.0;
-            fn(t, a, b2);
-            a = warp_sum(a);
-            b2 = warp_sum(b2);
-            if (lane == 0) {
-                d.part[2 * t] = a;
-                d.part[2 * t + 1] = b2;
+            fn(t, ti, a, b2);
+            if (partials) {
+                a = warp_sum(a);
+                b2 = warp_sum(b2);
+                if (lane == 0) {
+                    d.part[2 * t] = a;
+                    d.part[2 * t + 1] = b2;
+                }
             }
+            t = tn;
+            ti = tin;
         }
     };
     // List of the tiles whose system is running, appended (in any order) to list `sl`, whose
@@ -275,10 +309,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
     int slot = 0;
     // ---- start: r = b - A x, relres, then z = M^-1 r, p = z, rho ----------------------
     for (int restart = 0; restart < 3; ++restart) {
-        per_tile([&](int t, double &a, double &b2) {
-            const int s = d.tile_sys[t];
-            if (restart > 0 && __ldcg(d.state + s) != kRunning) return;
-            tile_spmv<TR>(d, t, d.x, 1, a, b2);
+        per_tile([&](int, const TileInfo &ti, double &a, double &b2) {
+            if (restart > 0 && __ldcg(d.state + ti.sys) != kRunning) return;
+            tile_spmv<TR>(d, ti, d.x, 1, a, b2);
         });
         if (!grid_barrier(d)) return;
         for (int s = gw; s < d.nsys; s += nw) {
@@ -303,9 +336,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
         }
         if (!grid_barrier(d)) return;
-        per_tile([&](int t, double &a, double &b2) {
-            if (__ldcg(d.state + d.tile_sys[t]) != kRunning) return;
-            tile_apply<TR>(d, t, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
+        per_tile([&](int, const TileInfo &ti, double &a, double &b2) {
+            if (__ldcg(d.state + ti.sys) != kRunning) return;
+            tile_apply<TR>(d, ti, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
         });
         if (!grid_barrier(d)) return;
         for (int s = gw; s < d.nsys; s += nw) {
@@ -324,7 +357,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         // ---- iterations --------------------------------------------------------------
         while (*((volatile int32_t *)d.active) != 0) {
             // A: q = A p, p.q
-            per_listed(slot, [&](int t, double &a, double &b2) { tile_spmv<TR>(d, t, d.p, 0, a, b2); });
+            per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
+                tile_spmv<TR>(d, ti, d.p, 0, a, b2);
+            });
             if (!grid_barrier(d)) return;
             // B: alpha per system; the previous iteration's x updates are done
             if (blockIdx.x == 0 && threadIdx.x == 0) d.nlist[slot ^ 1] = 0;
@@ -339,10 +374,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
             if (!grid_barrier(d)) return;
             // C: r -= alpha q, z = M^-1 r, r.r and r.z
-            per_listed(slot, [&](int t, double &a, double &b2) {
-                const int s = d.tile_sys[t];
-                if (__ldcg(d.state + s) != kRunning) return;          // sigma broke down in B
-                tile_apply<TR>(d, t, __ldcg(d.alpha + s), 1, 0, s_rh[warp], s_r[warp], a, b2);
+            per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
+                if (__ldcg(d.state + ti.sys) != kRunning) return;     // sigma broke down in B
+                tile_apply<TR>(d, ti, __ldcg(d.alpha + ti.sys), 1, 0, s_rh[warp], s_r[warp], a, b2);
             });
             if (!grid_barrier(d)) return;
             // D: convergence and beta per system; count the systems still running
@@ -371,13 +405,12 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             if (!grid_barrier(d)) return;
             if (lane == 0 && my_active) atomicOr(d.active, 1);
             // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped)
-            per_listed(slot, [&](int t, double &, double &) {
-                const int s = d.tile_sys[t];
+            per_listed(slot, false, [&](int, const TileInfo &ti, double &, double &) {
+                const int s = ti.sys;
                 const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
                 if (!xp && !run) return;
                 const double al = __ldcg(d.alpha + s), be = __ldcg(d.beta + s);
-                const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1];
-                for (int row = r0 + lane; row < r1; row += 32) {
+                for (int row = ti.r0 + lane; row < ti.r1; row += 32) {
                     const double pi = d.p[row];
                     if (xp) d.x[row] = fma(al, pi, d.x[row]);
                     if (run) d.p[row] = fma(be, pi, d.z[row]);
@@ -390,10 +423,9 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         for (int s = gw; s < d.nsys; s += nw)
             if (lane == 0) d.xpend[s] = 0;
         // ---- true residual of the converged systems; restart those that miss tol -----
-        per_tile([&](int t, double &a, double &b2) {
-            const int s = d.tile_sys[t];
-            if (__ldcg(d.state + s) != kConverged) return;
-            tile_spmv<TR>(d, t, d.x, 1, a, b2);
+        per_tile([&](int, const TileInfo &ti, double &a, double &b2) {
+            if (__ldcg(d.state + ti.sys) != kConverged) return;
+            tile_spmv<TR>(d, ti, d.x, 1, a, b2);
         });
         if (!grid_barrier(d)) return;
         int again = 0;
@@ -445,6 +477,7 @@ struct bjac_batch {
     int32_t *si = nullptr;         // per-system ints: iter state xpend restarts
     unsigned int *ctl = nullptr;   // barrier count, generation, err, active, list lengths [2]
     int32_t *soff = nullptr, *scol = nullptr, *alist = nullptr;   // sliced-ELLPACK tiles, tile lists
+    int4 *tinfo = nullptr;          // per-tile descriptions (two int4 each)
     double *sval = nullptr;
     std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
     int grid = 0;
@@ -465,7 +498,7 @@ static void free_batch(bjac_batch *h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     void *ptrs[] = {h->rowptr, h->colidx, h->val, h->block_ptr, h->goff, h->fmt, h->scale, h->qoff, h->pool, h->feat,
                     h->kap, h->status, h->tile_row, h->tile_sys, h->tile_blk, h->d_sys_tile, h->b, h->x, h->r, h->z,
-                    h->p, h->q, h->part, h->sd, h->si, h->ctl, h->soff, h->scol, h->sval, h->alist};
+                    h->p, h->q, h->part, h->sd, h->si, h->ctl, h->soff, h->scol, h->sval, h->alist, h->tinfo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -525,6 +558,7 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     d.active = reinterpret_cast<int32_t *>(h->ctl + 3);
     d.nlist = reinterpret_cast<int32_t *>(h->ctl + 4);
     d.soff = h->soff;
+    d.tinfo = h->tinfo;
     d.scol = h->scol;
     d.sval = h->sval;
     d.alist = h->alist;
@@ -661,6 +695,26 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
         }
     }
     so[nsl] = (int32_t)acc;
+    // tile descriptions: rows, system, first block, common block size, slice offsets
+    std::vector<int32_t> ti((size_t)h->ntiles * 8);
+    for (int t = 0; t < h->ntiles; ++t) {
+        int32_t *e = &ti[(size_t)t * 8];
+        e[0] = trow[t];
+        e[1] = trow[t + 1];
+        e[2] = tsys[t];
+        e[3] = tblk[t];
+        int ubs = bp[tblk[t] + 1] - bp[tblk[t]];
+        for (int k = tblk[t]; k < h->nb_tot && bp[k] < trow[t + 1]; ++k)
+            if (bp[k + 1] - bp[k] != ubs) ubs = 0;
+        e[4] = ubs;
+        e[5] = so[(size_t)t * spt];
+        e[6] = so[(size_t)t * spt + 1];
+        e[7] = spt > 1 ? so[(size_t)t * spt + 2] : e[6];
+    }
+    cudaFree(h->tinfo);
+    h->tinfo = nullptr;
+    MPB_CUDA(cudaMalloc(&h->tinfo, sizeof(int32_t) * ti.size()));
+    MPB_CUDA(cudaMemcpy(h->tinfo, ti.data(), sizeof(int32_t) * ti.size(), cudaMemcpyHostToDevice));
     cudaFree(h->soff);
     cudaFree(h->scol);
     cudaFree(h->sval);
