@@ -298,10 +298,23 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             if (__ldcg(d.state + d.tile_sys[t]) == kRunning)
                 d.alist[(size_t)sl * d.ntiles + atomicAdd(d.nlist + sl, 1)] = t;
     };
-    auto sys_sum = [&](int s, int which) {     // fixed-order sum of system s's tile partials
-        double v = 0.0;
-        for (int t = d.sys_tile[s] + lane; t < d.sys_tile[s + 1]; t += 32) v += __ldcg(d.part + 2 * t + which);
-        return warp_sum(v);
+    // Fixed-order sums of system s's tile partials by the whole CTA (every thread of the CTA
+    // must call it; the results are valid in every thread). One CTA per system keeps the
+    // largest systems' sums short.
+    __shared__ double s_sum[kWarps];
+    auto sys_sum2 = [&](int s, double &a, double &b2) {
+        double va = 0.0, vb = 0.0;
+        for (int t = d.sys_tile[s] + threadIdx.x; t < d.sys_tile[s + 1]; t += kNT) {
+            va += __ldcg(d.part + 2 * t);
+            vb += __ldcg(d.part + 2 * t + 1);
+        }
+        a = block_sum<kNT>(va, s_sum);
+        b2 = block_sum<kNT>(vb, s_sum);
+    };
+    auto sys_sum = [&](int s) {
+        double va = 0.0;
+        for (int t = d.sys_tile[s] + threadIdx.x; t < d.sys_tile[s + 1]; t += kNT) va += __ldcg(d.part + 2 * t);
+        return block_sum<kNT>(va, s_sum);
     };
 
     // which list length is current: it alternates at every list build; the loop ends with an
@@ -314,10 +327,11 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             tile_spmv<TR>(d, ti, d.x, 1, a, b2);
         });
         if (!grid_barrier(d)) return;
-        for (int s = gw; s < d.nsys; s += nw) {
-            if (restart > 0 && d.state[s] != kRunning) continue;
-            const double rr = sys_sum(s, 0), bb = sys_sum(s, 1);
-            if (lane == 0) {
+        for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
+            if (restart > 0 && __ldcg(d.state + s) != kRunning) continue;
+            double rr, bb;
+            sys_sum2(s, rr, bb);
+            if (threadIdx.x == 0) {
                 if (restart == 0) {
                     d.bnorm[s] = sqrt(bb);
                     d.iter[s] = 0;
@@ -341,10 +355,10 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             tile_apply<TR>(d, ti, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
         });
         if (!grid_barrier(d)) return;
-        for (int s = gw; s < d.nsys; s += nw) {
-            if (d.state[s] != kRunning) continue;
-            const double rz = sys_sum(s, 0);
-            if (lane == 0) {
+        for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
+            if (__ldcg(d.state + s) != kRunning) continue;
+            const double rz = sys_sum(s);
+            if (threadIdx.x == 0) {
                 d.rho[s] = rz;
                 if (!finite_pos(rz)) d.state[s] = kBreakdown;
             }
@@ -363,11 +377,11 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             if (!grid_barrier(d)) return;
             // B: alpha per system; the previous iteration's x updates are done
             if (blockIdx.x == 0 && threadIdx.x == 0) d.nlist[slot ^ 1] = 0;
-            for (int s = gw; s < d.nsys; s += nw) {
-                if (lane == 0) d.xpend[s] = 0;
-                if (d.state[s] != kRunning) continue;
-                const double sigma = sys_sum(s, 0);
-                if (lane == 0) {
+            for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
+                if (threadIdx.x == 0) d.xpend[s] = 0;
+                if (__ldcg(d.state + s) != kRunning) continue;
+                const double sigma = sys_sum(s);
+                if (threadIdx.x == 0) {
                     if (!finite_pos(sigma)) d.state[s] = kBreakdownSigma;
                     else d.alpha[s] = d.rho[s] / sigma;
                 }
@@ -381,10 +395,11 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             if (!grid_barrier(d)) return;
             // D: convergence and beta per system; count the systems still running
             int my_active = 0;
-            for (int s = gw; s < d.nsys; s += nw) {
-                if (d.state[s] != kRunning) continue;
-                const double rz = sys_sum(s, 0), rr = sys_sum(s, 1);
-                if (lane == 0) {
+            for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
+                if (__ldcg(d.state + s) != kRunning) continue;
+                double rz, rr;
+                sys_sum2(s, rz, rr);
+                if (threadIdx.x == 0) {
                     const int it = d.iter[s] + 1;
                     d.iter[s] = it;
                     d.xpend[s] = 1;
@@ -403,7 +418,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
             if (!grid_barrier(d)) return;
-            if (lane == 0 && my_active) atomicOr(d.active, 1);
+            if (threadIdx.x == 0 && my_active) atomicOr(d.active, 1);
             // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped)
             per_listed(slot, false, [&](int, const TileInfo &ti, double &, double &) {
                 const int s = ti.sys;
@@ -420,8 +435,8 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             build_list(slot);
             if (!grid_barrier(d)) return;
         }
-        for (int s = gw; s < d.nsys; s += nw)
-            if (lane == 0) d.xpend[s] = 0;
+        for (int s = blockIdx.x; s < d.nsys; s += gridDim.x)
+            if (threadIdx.x == 0) d.xpend[s] = 0;
         // ---- true residual of the converged systems; restart those that miss tol -----
         per_tile([&](int, const TileInfo &ti, double &a, double &b2) {
             if (__ldcg(d.state + ti.sys) != kConverged) return;
@@ -429,10 +444,10 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         });
         if (!grid_barrier(d)) return;
         int again = 0;
-        for (int s = gw; s < d.nsys; s += nw) {
-            if (d.state[s] != kConverged) continue;
-            const double rr = sys_sum(s, 0);
-            if (lane == 0) {
+        for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
+            if (__ldcg(d.state + s) != kConverged) continue;
+            const double rr = sys_sum(s);
+            if (threadIdx.x == 0) {
                 const double rel = d.bnorm[s] > 0.0 ? sqrt(rr) / d.bnorm[s] : 0.0;
                 d.true_relres[s] = rel;
                 if (rel > d.tol && d.iter[s] < d.maxit && restart < 2) {
@@ -444,7 +459,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
         if (!grid_barrier(d)) return;
-        if (lane == 0 && again) atomicOr(d.active, 1);
+        if (threadIdx.x == 0 && again) atomicOr(d.active, 1);
         if (!grid_barrier(d)) return;
         if (*((volatile int32_t *)d.active) == 0) return;
     }
