@@ -56,6 +56,11 @@ extern "C" {
 #define BJAC_SELECT_MLP 3       /* learned 12-64-64-3 selector, then promoted until          */
                                 /* kappa_1 u_f <= safety_theta                               */
 #define BJAC_SELECT_GIVEN 4     /* every block the format policy.block_fmt[b] names          */
+#define BJAC_SELECT_KT 5        /* the paper's inexact BJAC(k, t) of Eq. 3-2 / 3-3: no block   */
+                                /* inverses; kt_inner Jacobi sweeps inside the blocks and      */
+                                /* kt_outer block-Jacobi sweeps on A per application, blocks of */
+                                /* any size (the paper: 32 blocks, k = t = 2); fixed_fmt FP32   */
+                                /* keeps a binary32 set (fMP, aMP), FP64 only the binary64 one  */
 
 /* ---- residual-driven switching (the paper's aMP-BJAC) ------------------------------- */
 #define BJAC_TEMPORAL_NONE 0
@@ -97,6 +102,8 @@ typedef struct bjac_policy {
                                arrays, 2 the SELL-32 copy, one slice at a time per warp, 3 the
                                SELL-32 copy with the next slice's first entries prefetched.
                                Every layout sums each row in CSR order: same result bits.  */
+    int32_t kt_outer;       /* BJAC_SELECT_KT: outer sweeps k (0: 2)                        */
+    int32_t kt_inner;       /* BJAC_SELECT_KT: inner Jacobi sweeps t (0: 2)                 */
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
 

@@ -73,6 +73,9 @@ def lib():
                 "orc_mlp_nparam": (i32, []),
                 "orc_mlp_forward": (None, [i32, P, P, P]),
                 "orc_mlp_loss_grad": (f64, [i32, P, P, P, P]),
+                "orc_kt_dinv": (i32, [i32, P, P, P, P]),
+                "orc_kt_apply": (i32, [i32, P, P, P, i32, P, i32, i32, i32, P, P]),
+                "orc_pcg_kt": (i32, [i32, P, P, P, i32, P, i32, i32, i32, f64, P, P, f64, i32, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(_lib, name)
@@ -222,6 +225,34 @@ def pcg(A, P: Preconditioner, b, x0=None, tol=1e-10, maxit=1000, policy=POLICY_U
     k = st.iters
     return dict(x=x, iters=k, converged=bool(st.converged), status=st.status, relres=st.relres,
                 true_relres=st.true_relres, restarts=st.restarts, hist=hist[:k + 1], low_used=low[:k + 1],
+                low_applies=st.low_applies, high_applies=st.high_applies)
+
+
+def kt_apply(A, block_ptr, k, t, r, prec=0):
+    """z = M-hat^-1 r of BJAC(k, t) (Eq. 3-2 / 3-3); prec 0 binary64, 1 binary32 (Algorithm 3.1)."""
+    r = _c(r, np.float64)
+    bp = _c(block_ptr, np.int32)
+    z = np.empty(A.n)
+    rc = lib().orc_kt_apply(A.n, _p(A.rowptr), _p(A.colidx), _p(A.val), len(bp) - 1, _p(bp), k, t, prec, _p(r),
+                            _p(z))
+    if rc != 0:
+        raise ValueError("a diagonal entry is not positive")
+    return z
+
+
+def pcg_kt(A, block_ptr, b, k=2, t=2, x0=None, tol=1e-10, maxit=1000, policy=POLICY_UNIFORM, adp_tol=10.0):
+    """Oracle PCG with BJAC(k, t); policy as in pcg (the low set is the binary32 one)."""
+    b = _c(b, np.float64)
+    bp = _c(block_ptr, np.int32)
+    x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    hist = np.full(maxit + 1, np.nan)
+    low = np.zeros(maxit + 1, dtype=np.uint8)
+    st = Stats()
+    lib().orc_pcg_kt(A.n, _p(A.rowptr), _p(A.colidx), _p(A.val), len(bp) - 1, _p(bp), k, t, policy, adp_tol,
+                     _p(b), _p(x), tol, maxit, _p(hist), _p(low), C.byref(st))
+    it = st.iters
+    return dict(x=x, iters=it, converged=bool(st.converged), status=st.status, relres=st.relres,
+                true_relres=st.true_relres, restarts=st.restarts, hist=hist[:it + 1], low_used=low[:it + 1],
                 low_applies=st.low_applies, high_applies=st.high_applies)
 
 

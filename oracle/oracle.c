@@ -23,6 +23,9 @@
  *                          (Algorithm 3.3), convergence test of Section 4.2
  *   multiscale / features / selection rule / MLP -- per-block quantities (Eq. 4-5,
  *                          Section 4.5.2) and the block-format selectors
+ *   BJAC(k, t)          -- the inexact block Jacobi of Eq. 3-2 / 3-3 (inner Jacobi sweeps
+ *                          inside the blocks, outer block-Jacobi sweeps), in binary64 or
+ *                          binary32 (Algorithm 3.1), and PCG with it
  */
 #include <math.h>
 #include <stdint.h>
@@ -670,4 +673,235 @@ double orc_mlp_loss_grad(int32_t m, const double *w, const double *xin, const in
         }
     }
     return loss / m;
+}
+
+/* ====================================================================================== */
+/* BJAC(k, t), Eq. 3-2 and Eq. 3-3. A_bd is the block-diagonal part of A (entries whose     */
+/* row and column lie in the same block of block_ptr), D = diag(A):                        */
+/*   D-hat^-1 w = sum_{i<t} (I - D^-1 A_bd)^i D^-1 w     (t Jacobi sweeps inside the blocks) */
+/*   M-hat^-1 r = sum_{j<k} (I - D-hat^-1 A)^j D-hat^-1 r (k block-Jacobi sweeps)            */
+/* Both sums are what the stationary iterations produce from a zero start, so they are      */
+/* evaluated as                                                                            */
+/*   z = 0; for j < k: { w = r - A z; y = 0; for i < t: y = y + D^-1 (w - A_bd y); z += y }  */
+/* with, for every row, the product sum as one FMA chain in CSR order starting from 0, then  */
+/* the difference, then y_i + dinv_i * u_i as one FMA.                                     */
+/* prec 0: binary64 throughout. prec 1: Algorithm 3.1 with p_l = binary32: r-hat = RN32(r),   */
+/* the values of A and dinv_i = RN32(1 / a_ii) (the reciprocal formed in binary64) stored in */
+/* binary32, every operation in binary32, z widened exactly.                               */
+/* ====================================================================================== */
+static int32_t block_of_row(int32_t nb, const int32_t *block_ptr, int32_t i) {
+    int32_t b = 0;
+    while (b + 1 < nb && block_ptr[b + 1] <= i) ++b;
+    return b;
+}
+
+/* dinv (binary64) from the diagonal; returns the first row without a positive diagonal, or -1 */
+int32_t orc_kt_dinv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, double *dinv) {
+    for (int32_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (colidx[k] == i) d += val[k];
+        if (!(d > 0.0)) return i;
+        dinv[i] = 1.0 / d;
+    }
+    return -1;
+}
+
+static void kt_apply64(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                       const int32_t *block_ptr, const int32_t *rblk, int32_t k, int32_t t, const double *dinv,
+                       const double *r, double *z, double *w, double *y, double *y2) {
+    for (int32_t i = 0; i < n; ++i) z[i] = 0.0;
+    for (int32_t j = 0; j < k; ++j) {
+        for (int32_t i = 0; i < n; ++i) {                      /* w = r - A z */
+            double sum = 0.0;
+            for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) sum = fma(val[e], z[colidx[e]], sum);
+            w[i] = r[i] - sum;
+        }
+        for (int32_t i = 0; i < n; ++i) y[i] = 0.0;
+        for (int32_t s = 0; s < t; ++s) {                      /* y = y + D^-1 (w - A_bd y) */
+            for (int32_t i = 0; i < n; ++i) {
+                const int32_t b = rblk[i];
+                double sum = 0.0;
+                for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                    const int32_t c = colidx[e];
+                    if (c >= block_ptr[b] && c < block_ptr[b + 1]) sum = fma(val[e], y[c], sum);
+                }
+                const double u = w[i] - sum;
+                y2[i] = fma(dinv[i], u, y[i]);
+            }
+            for (int32_t i = 0; i < n; ++i) y[i] = y2[i];
+        }
+        for (int32_t i = 0; i < n; ++i) z[i] = z[i] + y[i];
+    }
+    (void)nb;
+}
+
+static void kt_apply32(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val32, int32_t nb,
+                       const int32_t *block_ptr, const int32_t *rblk, int32_t k, int32_t t, const float *dinv32,
+                       const double *r, double *z, float *rh, float *zf, float *w, float *y, float *y2) {
+    for (int32_t i = 0; i < n; ++i) rh[i] = as_float(orc_round_f32_bits(r[i]));
+    for (int32_t i = 0; i < n; ++i) zf[i] = 0.0f;
+    for (int32_t j = 0; j < k; ++j) {
+        for (int32_t i = 0; i < n; ++i) {
+            float sum = 0.0f;
+            for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) sum = fmaf(val32[e], zf[colidx[e]], sum);
+            w[i] = rh[i] - sum;
+        }
+        for (int32_t i = 0; i < n; ++i) y[i] = 0.0f;
+        for (int32_t s = 0; s < t; ++s) {
+            for (int32_t i = 0; i < n; ++i) {
+                const int32_t b = rblk[i];
+                float sum = 0.0f;
+                for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                    const int32_t c = colidx[e];
+                    if (c >= block_ptr[b] && c < block_ptr[b + 1]) sum = fmaf(val32[e], y[c], sum);
+                }
+                const float u = w[i] - sum;
+                y2[i] = fmaf(dinv32[i], u, y[i]);
+            }
+            for (int32_t i = 0; i < n; ++i) y[i] = y2[i];
+        }
+        for (int32_t i = 0; i < n; ++i) zf[i] = zf[i] + y[i];
+    }
+    for (int32_t i = 0; i < n; ++i) z[i] = (double)zf[i];
+    (void)nb;
+}
+
+typedef struct {
+    int32_t n, nb, k, t;
+    const int32_t *rowptr, *colidx, *block_ptr;
+    const double *val;
+    int32_t *rblk;
+    double *dinv, *w, *y, *y2;
+    float *val32, *dinv32, *rh, *zf, *wf, *yf, *y2f;
+} kt_state;
+
+static int kt_init(kt_state *K, int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                   int32_t nb, const int32_t *block_ptr, int32_t k, int32_t t) {
+    memset(K, 0, sizeof(*K));
+    K->n = n; K->nb = nb; K->k = k; K->t = t;
+    K->rowptr = rowptr; K->colidx = colidx; K->block_ptr = block_ptr; K->val = val;
+    const int32_t nnz = rowptr[n];
+    K->rblk = malloc(sizeof(int32_t) * (size_t)n);
+    K->dinv = malloc(sizeof(double) * (size_t)n);
+    K->w = malloc(sizeof(double) * (size_t)n);
+    K->y = malloc(sizeof(double) * (size_t)n);
+    K->y2 = malloc(sizeof(double) * (size_t)n);
+    K->val32 = malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    K->dinv32 = malloc(sizeof(float) * (size_t)n);
+    K->rh = malloc(sizeof(float) * (size_t)n);
+    K->zf = malloc(sizeof(float) * (size_t)n);
+    K->wf = malloc(sizeof(float) * (size_t)n);
+    K->yf = malloc(sizeof(float) * (size_t)n);
+    K->y2f = malloc(sizeof(float) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) K->rblk[i] = block_of_row(nb, block_ptr, i);
+    if (orc_kt_dinv(n, rowptr, colidx, val, K->dinv) >= 0) return -1;
+    for (int32_t i = 0; i < n; ++i) K->dinv32[i] = as_float(orc_round_f32_bits(K->dinv[i]));
+    for (int32_t e = 0; e < nnz; ++e) K->val32[e] = as_float(orc_round_f32_bits(val[e]));
+    return 0;
+}
+
+static void kt_free(kt_state *K) {
+    void *ptrs[] = {K->rblk, K->dinv, K->w, K->y, K->y2, K->val32, K->dinv32, K->rh, K->zf, K->wf, K->yf, K->y2f};
+    for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
+}
+
+static void kt_apply(const kt_state *K, int32_t prec, const double *r, double *z) {
+    if (prec == 0)
+        kt_apply64(K->n, K->rowptr, K->colidx, K->val, K->nb, K->block_ptr, K->rblk, K->k, K->t, K->dinv, r, z,
+                   K->w, K->y, K->y2);
+    else
+        kt_apply32(K->n, K->rowptr, K->colidx, K->val32, K->nb, K->block_ptr, K->rblk, K->k, K->t, K->dinv32, r, z,
+                   K->rh, K->zf, K->wf, K->yf, K->y2f);
+}
+
+/* z = M-hat^-1 r; returns -1 if a diagonal entry is not positive */
+int32_t orc_kt_apply(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                     const int32_t *block_ptr, int32_t k, int32_t t, int32_t prec, const double *r, double *z) {
+    kt_state K;
+    if (kt_init(&K, n, rowptr, colidx, val, nb, block_ptr, k, t)) { kt_free(&K); return -1; }
+    kt_apply(&K, prec, r, z);
+    kt_free(&K);
+    return 0;
+}
+
+/* PCG as orc_pcg with M-hat^-1 of BJAC(k, t): policy 0 binary64, 1 fMP (binary32), 2 hl, 3 lh */
+int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                   const int32_t *block_ptr, int32_t kk, int32_t tt, int32_t policy, double adp_tol,
+                   const double *b, double *x, double tol, int32_t maxit, double *hist, uint8_t *low_used,
+                   orc_stats *st) {
+    memset(st, 0, sizeof(*st));
+    kt_state K;
+    if (kt_init(&K, n, rowptr, colidx, val, nb, block_ptr, kk, tt)) {
+        kt_free(&K);
+        st->status = ORC_BREAKDOWN;
+        return ORC_BREAKDOWN;
+    }
+    precond P = {nb, block_ptr, NULL, NULL, NULL, NULL, NULL, NULL, policy, adp_tol, 1};
+    double *r = malloc(sizeof(double) * (size_t)n);
+    double *z = malloc(sizeof(double) * (size_t)n);
+    double *p = malloc(sizeof(double) * (size_t)n);
+    double *q = malloc(sizeof(double) * (size_t)n);
+    double bnorm = sqrt(orc_dot(n, b, b));
+    int32_t k = 0, status = ORC_OK;
+#define KT_PRECONDITION(rel, flag)                                  \
+    do {                                                            \
+        const int lo_ = use_low(&P, (rel));                         \
+        kt_apply(&K, lo_, r, z);                                    \
+        if (lo_) st->low_applies++; else st->high_applies++;        \
+        if (flag) *(flag) = (uint8_t)lo_;                           \
+    } while (0)
+    if (bnorm == 0.0) {
+        for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+        st->converged = 1; st->relres = 0.0; st->true_relres = 0.0;
+        goto done;
+    }
+    orc_residual(n, rowptr, colidx, val, b, x, r);
+    double relres = sqrt(orc_dot(n, r, r)) / bnorm;
+    st->true_relres = relres;
+    if (hist) hist[0] = relres;
+    for (;;) {
+        if (relres <= tol) break;
+        KT_PRECONDITION(relres, low_used ? &low_used[k] : NULL);
+        double rho = orc_dot(n, r, z);
+        if (!(rho > 0.0) || !isfinite(rho)) { status = ORC_BREAKDOWN; break; }
+        for (int32_t i = 0; i < n; ++i) p[i] = z[i];
+        while (k < maxit) {
+            orc_spmv(n, rowptr, colidx, val, p, q);
+            double sigma = orc_dot(n, p, q);
+            if (!(sigma > 0.0) || !isfinite(sigma)) { status = ORC_BREAKDOWN; break; }
+            double alpha = rho / sigma;
+            for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+            ++k;
+            relres = sqrt(orc_dot(n, r, r)) / bnorm;
+            if (hist) hist[k] = relres;
+            if (!isfinite(relres)) { status = ORC_BREAKDOWN; break; }
+            if (relres <= tol) break;
+            if (k >= maxit) break;
+            KT_PRECONDITION(relres, low_used ? &low_used[k] : NULL);
+            double rho_new = orc_dot(n, r, z);
+            if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = ORC_BREAKDOWN; break; }
+            double beta = rho_new / rho;
+            for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+            rho = rho_new;
+        }
+        if (status != ORC_OK) break;
+        orc_residual(n, rowptr, colidx, val, b, x, r);
+        double tr = sqrt(orc_dot(n, r, r)) / bnorm;
+        st->true_relres = tr;
+        if (tr <= tol || k >= maxit || st->restarts >= 8) break;
+        st->restarts++;
+        relres = tr;
+    }
+    st->relres = relres;
+    st->converged = (status == ORC_OK && relres <= tol && st->true_relres <= tol) ? 1 : 0;
+    if (status == ORC_OK && !st->converged) status = ORC_NOT_CONVERGED;
+#undef KT_PRECONDITION
+done:
+    st->iters = k;
+    st->status = status;
+    free(r); free(z); free(p); free(q);
+    kt_free(&K);
+    return status;
 }

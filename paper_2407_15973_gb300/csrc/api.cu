@@ -11,6 +11,7 @@
 
 #include "apply.cuh"
 #include "common.cuh"
+#include "kt.cuh"
 #include "mlp.cuh"
 #include "sell.cuh"
 #include "setup.cuh"
@@ -131,6 +132,7 @@ struct bjac_handle {
     int use_sell = 0;                     // loop SpMV on the SELL-32 copy
     float spmv_ms[3] = {0, 0, 0};         // timed y = A x: CSR, SELL-32, SELL-32 with prefetch
     int body_launches[2] = {0, 0};        // kernels in one body of each solve graph
+    KtSet kt;                             // BJAC(k, t) of Eq. 3-2 / 3-3 (select KT)
     long long launches = 0;               // kernels launched by the last solve
 };
 
@@ -147,6 +149,7 @@ static void free_handle(bjac_handle *h) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     sell_free(&h->sell);
+    kt_free(&h->kt);
     if (h->h_S) cudaFreeHost(h->h_S);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -382,16 +385,25 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     if (!block_ptr || nb < 1) return fail(MPBJAC_ERR_INVALID_ARG, "need nb >= 1 blocks");
     if (block_ptr[0] != 0 || block_ptr[nb] != A->n)
         return fail(MPBJAC_ERR_INVALID_ARG, "block_ptr must start at 0 and end at n");
+    const bjac_policy &P = *policy;
+    if (P.select < BJAC_SELECT_UNIFORM || P.select > BJAC_SELECT_KT)
+        return fail(MPBJAC_ERR_INVALID_ARG, "unknown select");
+    const bool kt = P.select == BJAC_SELECT_KT;
     int bs_max = 0, ubs = block_ptr[1] - block_ptr[0];
     for (int b = 0; b < nb; ++b) {
         const int bs = block_ptr[b + 1] - block_ptr[b];
-        if (bs < 1 || bs > 128) return fail(MPBJAC_ERR_INVALID_ARG, "every block needs 1..128 rows");
+        if (bs < 1 || (!kt && bs > 128)) return fail(MPBJAC_ERR_INVALID_ARG, "every block needs 1..128 rows");
         bs_max = std::max(bs_max, bs);
         if (bs != ubs) ubs = 0;
     }
-    const bjac_policy &P = *policy;
-    if (P.select < BJAC_SELECT_UNIFORM || P.select > BJAC_SELECT_GIVEN)
-        return fail(MPBJAC_ERR_INVALID_ARG, "unknown select");
+    if (kt) {
+        if (P.fixed_fmt != BJAC_FP64 && P.fixed_fmt != BJAC_FP32)
+            return fail(MPBJAC_ERR_INVALID_ARG, "BJAC(k,t) takes fixed_fmt FP64 or FP32");
+        if (P.temporal != BJAC_TEMPORAL_NONE && P.fixed_fmt != BJAC_FP32)
+            return fail(MPBJAC_ERR_INVALID_ARG, "aMP switching needs the binary32 BJAC(k,t) set");
+        if (P.kt_outer < 0 || P.kt_inner < 0 || P.kt_outer > 64 || P.kt_inner > 64)
+            return fail(MPBJAC_ERR_INVALID_ARG, "kt_outer and kt_inner must be 0..64 (0: 2)");
+    }
     if (P.select == BJAC_SELECT_GIVEN) {
         if (!P.block_fmt) return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_GIVEN needs block_fmt");
         for (int b = 0; b < nb; ++b)
@@ -425,140 +437,168 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     MPB_TRY(cudaEventCreate(&h->ev1) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "cudaEventCreate"));
     if (cudaEventRecord(h->ev0, st) != cudaSuccess) { free_handle(h); return cuda_fail(cudaGetLastError(), "event"); }
 
+    if (kt) {
+        // BJAC(k, t) of Eq. 3-2 / 3-3: no block inverses; diag(A), block ids and the SELL-32 copy
+        h->h_goff.assign(nb + 1, 0);
+        h->have_hi = true;
+        h->have_lo = P.fixed_fmt == BJAC_FP32;
+        h->blocks_per_fmt[h->have_lo ? BJAC_FP32 : BJAC_FP64] = nb;
+        MPB_TRY(dalloc(&h->d_block_ptr, nb + 1));
+        MPB_TRY(dalloc(&h->d_status, 2));
+        MPB_TRY(cudaMemcpyAsync(h->d_block_ptr, block_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy block_ptr"));
+        MPB_TRY(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) == cudaSuccess
+                    ? 0 : cuda_fail(cudaGetLastError(), "memset"));
+        k_validate_csr<<<std::max(1, std::min(sm_count() * 4, (A->nnz + 255) / 256)), 256, 0, st>>>(
+            A->n, A->nnz, A->rowptr, A->colidx, h->d_status);
+        int vstat[2] = {0, 0};
+        MPB_TRY(cudaMemcpyAsync(vstat, h->d_status, sizeof(vstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
+        MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "validate csr"));
+        if (vstat[0] != 0) {
+            free_handle(h);
+            return fail(MPBJAC_ERR_INVALID_ARG, "CSR arrays are inconsistent (rowptr not monotone / column out of range)");
+        }
+        int bad = -1;
+        MPB_TRY(kt_build(*A, h->d_block_ptr, nb, P.kt_outer > 0 ? P.kt_outer : 2, P.kt_inner > 0 ? P.kt_inner : 2,
+                         h->have_lo, &h->kt, &bad, st));
+        MPB_TRY(prepare_spmv(*A));
+    } else {
     // geometry
-    h->h_goff.resize(nb + 1);
-    h->h_goff[0] = 0;
-    for (int b = 0; b < nb; ++b) {
-        const int64_t bs = block_ptr[b + 1] - block_ptr[b];
-        h->h_goff[b + 1] = h->h_goff[b] + bs * bs;
-    }
-    const bool fixed_now = P.select == BJAC_SELECT_FIXED || P.select == BJAC_SELECT_UNIFORM ||
-                           P.select == BJAC_SELECT_GIVEN;
-    h->have_hi = P.select == BJAC_SELECT_UNIFORM || P.temporal != BJAC_TEMPORAL_NONE || P.fp64_fallback ||
-                 !fixed_now;
-    h->have_lo = P.select != BJAC_SELECT_UNIFORM;
-
-    MPB_TRY(dalloc(&h->d_block_ptr, nb + 1));
-    MPB_TRY(dalloc(&h->d_goff, nb + 1));
-    MPB_TRY(dalloc(&h->d_status, 2));
-    MPB_TRY(dalloc(&h->d_fmt, nb));
-    MPB_TRY(dalloc(&h->d_scale, nb));
-    MPB_TRY(dalloc(&h->d_qoff, nb + 1));
-    MPB_TRY(dalloc(&h->d_kap, 2 * (size_t)nb));
-    MPB_TRY(dalloc(&h->d_feat, 12 * (size_t)nb));
-    if (h->have_hi) MPB_TRY(dalloc(&h->d_G, (size_t)h->h_goff[nb]));
-    MPB_TRY(cudaMemcpyAsync(h->d_block_ptr, block_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
-                    cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy block_ptr"));
-    MPB_TRY(cudaMemcpyAsync(h->d_goff, h->h_goff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
-                    cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy goff"));
-    MPB_TRY(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) == cudaSuccess ? 0
-                                                                                : cuda_fail(cudaGetLastError(), "memset"));
-    k_validate_csr<<<std::max(1, std::min(sm_count() * 4, (A->nnz + 255) / 256)), 256, 0, st>>>(
-        A->n, A->nnz, A->rowptr, A->colidx, h->d_status);
-    int hstat[2] = {0, 0};
-    MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
-                ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
-    MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "validate csr"));
-    if (hstat[0] != 0) {
-        free_handle(h);
-        return fail(MPBJAC_ERR_INVALID_ARG, "CSR arrays are inconsistent (rowptr not monotone / column out of range)");
-    }
-
-    // low-precision pool offsets known now for fixed formats
-    int fixed_fmt = P.select == BJAC_SELECT_UNIFORM ? BJAC_FP64 : P.fixed_fmt;
-    auto set_qoff = [&](const std::vector<uint8_t> &fmts) {
-        h->h_qoff.assign(nb + 1, 0);
+        h->h_goff.resize(nb + 1);
+        h->h_goff[0] = 0;
         for (int b = 0; b < nb; ++b) {
             const int64_t bs = block_ptr[b + 1] - block_ptr[b];
-            int64_t bytes = bs * bs * fmt_bytes(fmts.empty() ? fixed_fmt : fmts[b]);
-            bytes = (bytes + 15) & ~int64_t(15);
-            h->h_qoff[b + 1] = h->h_qoff[b] + bytes;
+            h->h_goff[b + 1] = h->h_goff[b] + bs * bs;
         }
-        h->pool_bytes = h->h_qoff[nb];
-    };
-    SetupArgs a{};
-    a.n = A->n;
-    a.rowptr = A->rowptr;
-    a.colidx = A->colidx;
-    a.val = A->val;
-    a.block_ptr = h->d_block_ptr;
-    a.nb = nb;
-    a.goff = h->d_goff;
-    a.G = h->d_G;
-    a.select = P.select;
-    a.fixed_fmt = fixed_fmt;
-    a.theta = h->pol.theta;
-    a.fmt = h->d_fmt;
-    a.scale = h->d_scale;
-    a.feat = h->d_feat;
-    a.kap = h->d_kap;
-    a.status = h->d_status;
-    if (h->have_lo && fixed_now) {
-        if (P.select == BJAC_SELECT_GIVEN) {
-            std::vector<uint8_t> given(P.block_fmt, P.block_fmt + nb);
-            set_qoff(given);
-            MPB_TRY(cudaMemcpyAsync(h->d_fmt, P.block_fmt, nb, cudaMemcpyHostToDevice, st) == cudaSuccess
-                        ? 0 : cuda_fail(cudaGetLastError(), "copy block_fmt"));
-            a.given = h->d_fmt;
+        const bool fixed_now = P.select == BJAC_SELECT_FIXED || P.select == BJAC_SELECT_UNIFORM ||
+                               P.select == BJAC_SELECT_GIVEN;
+        h->have_hi = P.select == BJAC_SELECT_UNIFORM || P.temporal != BJAC_TEMPORAL_NONE || P.fp64_fallback ||
+                     !fixed_now;
+        h->have_lo = P.select != BJAC_SELECT_UNIFORM;
+
+        MPB_TRY(dalloc(&h->d_block_ptr, nb + 1));
+        MPB_TRY(dalloc(&h->d_goff, nb + 1));
+        MPB_TRY(dalloc(&h->d_status, 2));
+        MPB_TRY(dalloc(&h->d_fmt, nb));
+        MPB_TRY(dalloc(&h->d_scale, nb));
+        MPB_TRY(dalloc(&h->d_qoff, nb + 1));
+        MPB_TRY(dalloc(&h->d_kap, 2 * (size_t)nb));
+        MPB_TRY(dalloc(&h->d_feat, 12 * (size_t)nb));
+        if (h->have_hi) MPB_TRY(dalloc(&h->d_G, (size_t)h->h_goff[nb]));
+        MPB_TRY(cudaMemcpyAsync(h->d_block_ptr, block_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy block_ptr"));
+        MPB_TRY(cudaMemcpyAsync(h->d_goff, h->h_goff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy goff"));
+        MPB_TRY(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) == cudaSuccess ? 0
+                                                                                    : cuda_fail(cudaGetLastError(), "memset"));
+        k_validate_csr<<<std::max(1, std::min(sm_count() * 4, (A->nnz + 255) / 256)), 256, 0, st>>>(
+            A->n, A->nnz, A->rowptr, A->colidx, h->d_status);
+        int hstat[2] = {0, 0};
+        MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
+        MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "validate csr"));
+        if (hstat[0] != 0) {
+            free_handle(h);
+            return fail(MPBJAC_ERR_INVALID_ARG, "CSR arrays are inconsistent (rowptr not monotone / column out of range)");
+        }
+
+        // low-precision pool offsets known now for fixed formats
+        int fixed_fmt = P.select == BJAC_SELECT_UNIFORM ? BJAC_FP64 : P.fixed_fmt;
+        auto set_qoff = [&](const std::vector<uint8_t> &fmts) {
+            h->h_qoff.assign(nb + 1, 0);
+            for (int b = 0; b < nb; ++b) {
+                const int64_t bs = block_ptr[b + 1] - block_ptr[b];
+                int64_t bytes = bs * bs * fmt_bytes(fmts.empty() ? fixed_fmt : fmts[b]);
+                bytes = (bytes + 15) & ~int64_t(15);
+                h->h_qoff[b + 1] = h->h_qoff[b] + bytes;
+            }
+            h->pool_bytes = h->h_qoff[nb];
+        };
+        SetupArgs a{};
+        a.n = A->n;
+        a.rowptr = A->rowptr;
+        a.colidx = A->colidx;
+        a.val = A->val;
+        a.block_ptr = h->d_block_ptr;
+        a.nb = nb;
+        a.goff = h->d_goff;
+        a.G = h->d_G;
+        a.select = P.select;
+        a.fixed_fmt = fixed_fmt;
+        a.theta = h->pol.theta;
+        a.fmt = h->d_fmt;
+        a.scale = h->d_scale;
+        a.feat = h->d_feat;
+        a.kap = h->d_kap;
+        a.status = h->d_status;
+        if (h->have_lo && fixed_now) {
+            if (P.select == BJAC_SELECT_GIVEN) {
+                std::vector<uint8_t> given(P.block_fmt, P.block_fmt + nb);
+                set_qoff(given);
+                MPB_TRY(cudaMemcpyAsync(h->d_fmt, P.block_fmt, nb, cudaMemcpyHostToDevice, st) == cudaSuccess
+                            ? 0 : cuda_fail(cudaGetLastError(), "copy block_fmt"));
+                a.given = h->d_fmt;
+            } else {
+                set_qoff({});
+            }
+            MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
+            MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                                    st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
+            a.qoff = h->d_qoff;
+            a.pool = h->d_pool;
+        }
+        MPB_TRY(prepare_spmv(*A));
+        MPB_TRY(launch_setup_blocks(a, bs_max, h->h_block_ptr.data(), st));
+        if (P.select == BJAC_SELECT_MLP) {
+            MPB_TRY(launch_mlp_select(P.mlp_params, nb, h->d_feat, h->d_kap, h->pol.safety_theta, h->d_fmt, st));
+        }
+        std::vector<uint8_t> hfmt(nb);
+        MPB_TRY(cudaMemcpyAsync(hfmt.data(), h->d_fmt, nb, cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? 0 : cuda_fail(cudaGetLastError(), "copy fmt"));
+        MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
+        MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "setup kernel"));
+        if (hstat[0] != 0) {
+            free_handle(h);
+            return fail(MPBJAC_ERR_NOT_SPD, "diagonal block " + std::to_string(hstat[1]) +
+                                                " has a non-positive pivot (not positive definite)");
+        }
+        if (h->have_lo && !fixed_now) {     // per-block formats: compact pool, second pass
+            set_qoff(hfmt);
+            MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
+            MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                                    st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
+            MPB_TRY(launch_pack(nb, h->d_block_ptr, h->d_goff, h->d_G, h->d_fmt, h->d_qoff, h->d_pool, h->d_scale, st));
+        }
+        int ufmt = -1;
+        if (h->have_lo) {
+            ufmt = hfmt[0];
+            for (int b = 0; b < nb; ++b) {
+                h->blocks_per_fmt[hfmt[b] & 3] += 1;
+                if (hfmt[b] != ufmt) ufmt = -1;
+            }
+            h->lo = make_pset(h, h->d_fmt, h->d_scale, h->d_qoff, h->d_pool, ufmt);
+            if (tma_supported(h->lo, h->n)) MPB_TRY(prepare_apply_tma(h->lo));
+            MPB_TRY(choose_apply_kind(h));
         } else {
-            set_qoff({});
+            h->blocks_per_fmt[BJAC_FP64] = nb;
         }
-        MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
-        MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
-                                st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
-        a.qoff = h->d_qoff;
-        a.pool = h->d_pool;
-    }
-    MPB_TRY(prepare_spmv(*A));
-    MPB_TRY(launch_setup_blocks(a, bs_max, h->h_block_ptr.data(), st));
-    if (P.select == BJAC_SELECT_MLP) {
-        MPB_TRY(launch_mlp_select(P.mlp_params, nb, h->d_feat, h->d_kap, h->pol.safety_theta, h->d_fmt, st));
-    }
-    std::vector<uint8_t> hfmt(nb);
-    MPB_TRY(cudaMemcpyAsync(hfmt.data(), h->d_fmt, nb, cudaMemcpyDeviceToHost, st) == cudaSuccess
-                ? 0 : cuda_fail(cudaGetLastError(), "copy fmt"));
-    MPB_TRY(cudaMemcpyAsync(hstat, h->d_status, sizeof(hstat), cudaMemcpyDeviceToHost, st) == cudaSuccess
-                ? 0 : cuda_fail(cudaGetLastError(), "copy status"));
-    MPB_TRY(cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "setup kernel"));
-    if (hstat[0] != 0) {
-        free_handle(h);
-        return fail(MPBJAC_ERR_NOT_SPD, "diagonal block " + std::to_string(hstat[1]) +
-                                            " has a non-positive pivot (not positive definite)");
-    }
-    if (h->have_lo && !fixed_now) {     // per-block formats: compact pool, second pass
-        set_qoff(hfmt);
-        MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));
-        MPB_TRY(cudaMemcpyAsync(h->d_qoff, h->h_qoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
-                                st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy qoff"));
-        MPB_TRY(launch_pack(nb, h->d_block_ptr, h->d_goff, h->d_G, h->d_fmt, h->d_qoff, h->d_pool, h->d_scale, st));
-    }
-    int ufmt = -1;
-    if (h->have_lo) {
-        ufmt = hfmt[0];
-        for (int b = 0; b < nb; ++b) {
-            h->blocks_per_fmt[hfmt[b] & 3] += 1;
-            if (hfmt[b] != ufmt) ufmt = -1;
+        if (h->have_hi) {
+            std::vector<int64_t> qhi(nb + 1);
+            for (int b = 0; b <= nb; ++b) qhi[b] = h->h_goff[b] * 8;
+            std::vector<float> ones(nb, 1.0f);
+            MPB_TRY(dalloc(&h->d_fmt_hi, nb));
+            MPB_TRY(dalloc(&h->d_scale_hi, nb));
+            MPB_TRY(dalloc(&h->d_qoff_hi, nb + 1));
+            MPB_TRY(cudaMemsetAsync(h->d_fmt_hi, 0, nb, st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "memset"));
+            MPB_TRY(cudaMemcpyAsync(h->d_scale_hi, ones.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, st) ==
+                            cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
+            MPB_TRY(cudaMemcpyAsync(h->d_qoff_hi, qhi.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
+                            cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
+            h->hi = make_pset(h, h->d_fmt_hi, h->d_scale_hi, h->d_qoff_hi, reinterpret_cast<uint8_t *>(h->d_G),
+                              BJAC_FP64);
         }
-        h->lo = make_pset(h, h->d_fmt, h->d_scale, h->d_qoff, h->d_pool, ufmt);
-        if (tma_supported(h->lo, h->n)) MPB_TRY(prepare_apply_tma(h->lo));
-        MPB_TRY(choose_apply_kind(h));
-    } else {
-        h->blocks_per_fmt[BJAC_FP64] = nb;
-    }
-    if (h->have_hi) {
-        std::vector<int64_t> qhi(nb + 1);
-        for (int b = 0; b <= nb; ++b) qhi[b] = h->h_goff[b] * 8;
-        std::vector<float> ones(nb, 1.0f);
-        MPB_TRY(dalloc(&h->d_fmt_hi, nb));
-        MPB_TRY(dalloc(&h->d_scale_hi, nb));
-        MPB_TRY(dalloc(&h->d_qoff_hi, nb + 1));
-        MPB_TRY(cudaMemsetAsync(h->d_fmt_hi, 0, nb, st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "memset"));
-        MPB_TRY(cudaMemcpyAsync(h->d_scale_hi, ones.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, st) ==
-                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
-        MPB_TRY(cudaMemcpyAsync(h->d_qoff_hi, qhi.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st) ==
-                        cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "copy"));
-        h->hi = make_pset(h, h->d_fmt_hi, h->d_scale_hi, h->d_qoff_hi, reinterpret_cast<uint8_t *>(h->d_G),
-                          BJAC_FP64);
     }
     // solve workspace
     const size_t n = (size_t)A->n;
@@ -632,11 +672,32 @@ static int launch_apply_select(bjac_handle *h, int mode, cudaStream_t st, bool l
     return launch_apply_generic(mode, lo, hi, io, h->d_S, st);
 }
 
+
 #define MPB_TRY_RC(expr)          \
     do {                          \
         const int rc_ = (expr);   \
         if (rc_) return rc_;      \
     } while (0)
+
+// The first preconditioner application of a (re)start: z = M^-1 r, p = z, rho = r.z.
+static int launch_init_apply(bjac_handle *h, bool temporal, bool low_only, bool high_only, cudaStream_t st,
+                             long long *launches) {
+    if (h->pol.select == BJAC_SELECT_KT) {
+        ApplyIO io = base_io(h);
+        int n = 0;
+        if (temporal) {
+            MPB_TRY_RC(launch_kt_apply(kApplyInit, 1, true, h->kt, io, h->d_S, st, &n));
+            MPB_TRY_RC(launch_kt_apply(kApplyInit, 0, true, h->kt, io, h->d_S, st, &n));
+        } else {
+            MPB_TRY_RC(launch_kt_apply(kApplyInit, low_only ? 1 : 0, false, h->kt, io, h->d_S, st, &n));
+        }
+        *launches += n;
+        return MPBJAC_OK;
+    }
+    MPB_TRY_RC(launch_apply_select(h, kApplyInit, st, low_only, high_only));
+    *launches += (lo_uses_tma(h) && !high_only && !low_only) ? 2 : 1;
+    return MPBJAC_OK;
+}
 
 // Iterations per body of the device-side while loop. After convergence the remaining copies
 // of the body return at once; the loop condition is evaluated once per body.
@@ -663,6 +724,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     const bool temporal = (which == 0) && h->pol.temporal != BJAC_TEMPORAL_NONE;
     const bool use_low = (which == 0) && h->have_lo;
     const bool pdl = ev == nullptr;
+    const bool kt = h->pol.select == BJAC_SELECT_KT;
     if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
     pdl_set(pdl && pdl_first);
     int rc = launch_loop_spmv(h, cs);
@@ -670,7 +732,19 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     *launches += 1;
     pdl_set(pdl);
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
-    if (temporal) {
+    if (kt) {
+        // r -= alpha q and the convergence test first, then the sweeps of the set in use
+        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
+        *launches += 1;
+        if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
+        ApplyIO io = base_io(h);
+        if (temporal) {
+            MPB_TRY_RC(launch_kt_apply(kApplyTemporal, 1, true, h->kt, io, h->d_S, cs, launches));
+            MPB_TRY_RC(launch_kt_apply(kApplyTemporal, 0, true, h->kt, io, h->d_S, cs, launches));
+        } else {
+            MPB_TRY_RC(launch_kt_apply(kApplyTemporal, use_low ? 1 : 0, false, h->kt, io, h->d_S, cs, launches));
+        }
+    } else if (temporal) {
         MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
@@ -759,9 +833,8 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
     for (int pass = 0; pass < 9; ++pass) {
         const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
         const bool low_only = !temporal && hs.low_default == 1, high_only = !temporal && hs.low_default == 0;
-        rc = launch_apply_select(h, kApplyInit, st, low_only, high_only);
+        rc = launch_init_apply(h, temporal, low_only, high_only, st, &h->launches);
         if (rc) return rc;
-        h->launches += (lo_uses_tma(h) && !high_only && !low_only) ? 2 : 1;
         if (eager) {
             // the same loop body, enqueued from the host in batches of 32 iterations; once the
             // state leaves "running" every kernel returns at once
@@ -930,6 +1003,8 @@ extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *
     io.p = nullptr;
     io.out = rz;
     io.set = set;
+    if (h->pol.select == BJAC_SELECT_KT) return launch_kt_apply(kApplyStandalone, set, false, h->kt, io, nullptr,
+                                                                h->stream, nullptr);
     // bulk copies need 16-byte aligned sources
     const bool aligned = (reinterpret_cast<uintptr_t>(r) & 15) == 0;
     if (set == 1 && lo_uses_tma(h) && (aligned || h->apply_kind == kApplyKindReg)) {
@@ -978,6 +1053,7 @@ extern "C" int bjac_info(const bjac_handle *h, int32_t *nb, int64_t *pool_bytes,
 extern "C" int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *qoff, uint8_t *pool, double *G,
                            double *feat) {
     if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
+    if (h->pol.select == BJAC_SELECT_KT) return fail(MPBJAC_ERR_UNSUPPORTED, "BJAC(k,t) keeps no block inverses");
     cudaStream_t st = h->stream;
     const int nb = h->nb;
     if (fmt) MPB_CUDA(cudaMemcpyAsync(fmt, h->have_lo ? h->d_fmt : h->d_fmt_hi, nb, cudaMemcpyDeviceToHost, st));
@@ -996,6 +1072,7 @@ extern "C" int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *
 
 extern "C" int bjac_import_inverse(bjac_handle *h, const double *G) {
     if (!h || !G) return fail(MPBJAC_ERR_INVALID_ARG, "handle and G must be non-NULL");
+    if (h->pol.select == BJAC_SELECT_KT) return fail(MPBJAC_ERR_UNSUPPORTED, "BJAC(k,t) keeps no block inverses");
     if (!h->have_hi) return fail(MPBJAC_ERR_UNSUPPORTED, "this handle keeps no binary64 set");
     cudaStream_t st = h->stream;
     MPB_CUDA(cudaMemcpyAsync(h->d_G, G, sizeof(double) * (size_t)h->h_goff[h->nb], cudaMemcpyHostToDevice, st));
@@ -1029,7 +1106,9 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;
     const bool temporal = hs.temporal != BJAC_TEMPORAL_NONE;
-    rc = launch_apply_select(h, kApplyInit, st, !temporal && hs.low_default == 1, !temporal && hs.low_default == 0);
+    long long init_launches = 0;
+    rc = launch_init_apply(h, temporal, !temporal && hs.low_default == 1, !temporal && hs.low_default == 0, st,
+                           &init_launches);
     if (rc) return rc;
     const int cap = maxit < 64 ? maxit : 64;
     std::vector<cudaEvent_t> ev((size_t)cap * 5);

@@ -24,40 +24,6 @@
 namespace mpbjac {
 
 // ----------------------------------------------------------------------------------------
-// epilogue shared by both kernels: the last CTA turns the partial sums into solver scalars
-// ----------------------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyIO &io, SolverState *S,
-                                             int used_low) {
-    if (MODE == kApplyStandalone) {
-        if (io.out) *io.out = rho;
-        return;
-    }
-    if (used_low) S->low_applies += 1;
-    else S->high_applies += 1;
-    if (MODE == kApplyInit) {
-        S->rho = rho;
-        if (!finite_pos(rho)) S->state = kBreakdown;
-        return;
-    }
-    if (MODE == kApplyFused) {
-        S->iter += 1;
-        S->x_pending = 1;
-        const double rel = sqrt(rr) / S->bnorm;
-        S->relres = rel;
-        S->rr = rr;
-        if (S->hist) S->hist[S->iter] = rel;
-        if (!(rel < 1.0e308)) { S->state = kBreakdown; return; }
-        if (rel <= S->tol) { S->state = kConverged; return; }
-        if (S->iter >= S->maxit) { S->state = kMaxit; return; }
-    }
-    // kApplyTemporal and kApplyFused (still running): beta = rho_new / rho_old
-    if (!finite_pos(rho)) { S->state = kBreakdown; return; }
-    S->beta = rho / S->rho;
-    S->rho = rho;
-}
-
-// ----------------------------------------------------------------------------------------
 // generic: one warp per block
 // ----------------------------------------------------------------------------------------
 template <typename QT>

@@ -543,3 +543,112 @@ def test_mlp_softmax_ce_closed_form(oracle):
     assert np.allclose(g[-3:], p - onehot, atol=1e-15)
     assert loss == pytest.approx(-np.mean(np.log(p[y])), rel=1e-14)
     assert np.allclose(oracle.mlp_forward(w, x), np.tile(b3, (5, 1)), atol=0)
+
+
+# ------------------------------------------------------------------------------------------
+# BJAC(k, t) of Eq. 3-2 / 3-3 (inner Jacobi sweeps inside the blocks, outer sweeps on A)
+# ------------------------------------------------------------------------------------------
+def _spd_blocks(n=24, bs=8, seed=3, dominance=1.5):
+    """Random sparse symmetric matrix with positive diagonal, diagonally dominant by `dominance`."""
+    rng = np.random.default_rng(seed)
+    M = np.zeros((n, n))
+    for _ in range(3 * n):
+        i, j = rng.integers(0, n, 2)
+        if i != j:
+            v = -rng.uniform(0.1, 1.0)
+            M[i, j] += v
+            M[j, i] += v
+    np.fill_diagonal(M, dominance * np.abs(M).sum(axis=1) + rng.uniform(0.5, 1.5, n))
+    from gpu_util import csr_from_dense
+    return M, csr_from_dense(M), np.arange(0, n + 1, bs, dtype=np.int32)
+
+
+def _dense_kt(M, bp, k, t):
+    """M-hat^-1 of Eq. 3-2 / 3-3 as explicit matrix polynomials."""
+    n = M.shape[0]
+    D = np.diag(np.diag(M))
+    Dinv = np.diag(1.0 / np.diag(M))
+    Abd = np.zeros_like(M)
+    for b in range(len(bp) - 1):
+        s, e = bp[b], bp[b + 1]
+        Abd[s:e, s:e] = M[s:e, s:e]
+    I = np.eye(n)
+    Dh = sum(np.linalg.matrix_power(I - Dinv @ Abd, i) for i in range(t)) @ Dinv
+    return sum(np.linalg.matrix_power(I - Dh @ M, j) for j in range(k)) @ Dh
+
+
+def test_kt_k1_t1_is_diagonal_scaling(oracle):
+    # Eq. 3-2 with k = t = 1 degenerates to D^-1 (Section 3.1)
+    pr = PB.make_problem("subcube3d", seed=2, m=10, bs=32)
+    r = PB.solution(pr.A.n, 4)
+    z = oracle.kt_apply(pr.A, pr.block_ptr, 1, 1, r)
+    d = np.array([pr.A.val[pr.A.rowptr[i]:pr.A.rowptr[i + 1]][pr.A.colidx[pr.A.rowptr[i]:pr.A.rowptr[i + 1]] == i].sum()
+                  for i in range(pr.A.n)])
+    assert np.array_equal(z, (1.0 / d) * r)
+
+
+@pytest.mark.parametrize("k,t", [(1, 2), (2, 1), (2, 2), (3, 2), (2, 3), (4, 4)])
+def test_kt_matches_dense_matrix_polynomials(oracle, k, t):
+    M, A, bp = _spd_blocks()
+    r = np.random.default_rng(k * 10 + t).standard_normal(M.shape[0])
+    ref = _dense_kt(M, bp, k, t) @ r
+    z = oracle.kt_apply(A, bp, k, t, r)
+    assert np.max(np.abs(z - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_kt_many_inner_sweeps_reach_the_exact_block_inverse(oracle):
+    # t -> inf: D-hat^-1 -> A_bd^-1 when the inner Jacobi converges; with k = 1 this is the
+    # exact block Jacobi of the rest of the oracle (LU inverses)
+    M, A, bp = _spd_blocks(dominance=3.0)
+    r = np.random.default_rng(9).standard_normal(M.shape[0])
+    z = oracle.kt_apply(A, bp, 1, 60, r)
+    P = oracle.Preconditioner(A, bp)
+    ref = oracle.apply_fp64(bp, P.G, P.goff, r)
+    assert np.max(np.abs(z - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_kt_preconditioner_is_symmetric(oracle):
+    pr = PB.make_problem("subcube3d", seed=3, m=12, bs=32)
+    bp = np.linspace(0, pr.A.n, 5).astype(np.int32)
+    r1, r2 = PB.solution(pr.A.n, 5), PB.solution(pr.A.n, 6)
+    a = np.dot(r1, oracle.kt_apply(pr.A, bp, 2, 2, r2))
+    b = np.dot(r2, oracle.kt_apply(pr.A, bp, 2, 2, r1))
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_kt_binary32_emulation(oracle):
+    pr = PB.make_problem("subcube3d", seed=4, m=12, bs=32)
+    bp = np.linspace(0, pr.A.n, 5).astype(np.int32)
+    r = PB.solution(pr.A.n, 7)
+    z64 = oracle.kt_apply(pr.A, bp, 2, 2, r, prec=0)
+    z32 = oracle.kt_apply(pr.A, bp, 2, 2, r, prec=1)
+    assert np.all(z32 == z32.astype(np.float32).astype(np.float64))      # binary32 values
+    assert np.max(np.abs(z32 - z64)) <= 1e-5 * np.max(np.abs(z64))
+    # k = t = 1: RN32(RN32(1/a_ii) * RN32(r_i)), one rounding per operation
+    z1 = oracle.kt_apply(pr.A, bp, 1, 1, r, prec=1)
+    d = np.array([pr.A.val[pr.A.rowptr[i]:pr.A.rowptr[i + 1]][pr.A.colidx[pr.A.rowptr[i]:pr.A.rowptr[i + 1]] == i].sum()
+                  for i in range(pr.A.n)])
+    ref = ((1.0 / d).astype(np.float32) * r.astype(np.float32)).astype(np.float64)
+    assert np.array_equal(z1, ref)
+
+
+def test_kt_pcg_point_jacobi_equals_blocks_of_one(oracle):
+    pr = PB.make_problem("poisson2d", seed=0)
+    b = oracle.spmv(pr.A, pr.x_star)
+    ref = oracle.pcg(pr.A, oracle.Preconditioner(pr.A, np.arange(pr.A.n + 1, dtype=np.int32)), b, maxit=2000)
+    got = oracle.pcg_kt(pr.A, pr.block_ptr, b, k=1, t=1, maxit=2000)
+    assert got["iters"] == ref["iters"] and np.array_equal(got["x"], ref["x"])
+
+
+def test_kt_pcg_policy_limits(oracle):
+    # Section 4.3.2: hl -> uniform as adp_tol -> 0 and -> fMP as adp_tol -> inf; lh the reverse
+    pr = PB.make_problem("subcube3d", seed=5, m=12, bs=32)
+    bp = np.linspace(0, pr.A.n, 9).astype(np.int32)
+    b = oracle.spmv(pr.A, pr.x_star)
+    uni = oracle.pcg_kt(pr.A, bp, b, policy=oracle.POLICY_UNIFORM, maxit=3000)
+    fmp = oracle.pcg_kt(pr.A, bp, b, policy=oracle.POLICY_FMP, maxit=3000)
+    assert uni["converged"] and fmp["converged"] and uni["true_relres"] <= 1e-10
+    for pol, tol, ref in ((oracle.POLICY_HL, 1e-30, uni), (oracle.POLICY_HL, 1e30, fmp),
+                          (oracle.POLICY_LH, 1e-30, fmp), (oracle.POLICY_LH, 1e30, uni)):
+        got = oracle.pcg_kt(pr.A, bp, b, policy=pol, adp_tol=tol, maxit=3000)
+        assert got["iters"] == ref["iters"] and np.array_equal(got["x"], ref["x"])
