@@ -66,6 +66,12 @@ def test_kt_pcg_vs_oracle(B, layout):
         st = h.solve(cuda(b), x, tol=TOL, maxit=5000)
         h.close()
         ref = O.pcg_kt(pr.A, bp, b, k=2, t=2, policy=pol, tol=TOL, maxit=5000)
+        if not ref["converged"]:
+            # the Jacobi sweeps diverge on this (non-M-matrix) operator, M-hat^-1 is not positive
+            # definite and PCG breaks down at once; the library reports the same
+            assert ref["status"] == -5 and st["status"] == B.ERR_BREAKDOWN and not st["converged"]
+            assert st["iters"] == ref["iters"]
+            continue
         assert st["converged"] and st["true_relres"] <= TOL
         slack = 2 if fmt == B.FP64 else max(3, 0.05 * ref["iters"])
         assert abs(st["iters"] - ref["iters"]) <= slack, (layout, fmt, st["iters"], ref["iters"])
