@@ -191,19 +191,21 @@ def run_ours(args, rank, world, dist):
             st = step(pol)
         barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         stats = []
-        e0.record(stream)
-        for _ in range(k):
+        ev[0].record(stream)
+        for i in range(k):
             stats.append(step(pol))
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / k
+        ms = ev[0].elapsed_time(ev[k]) / k
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k)]
         if dist is not None:
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
+        timed.last_steps = per
         return ms, stats
 
     spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
@@ -220,6 +222,7 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(dev) as clk:
         ms_mixed, st_mixed = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
+    step_ms = list(timed.last_steps)
     ms_fp64, st_fp64 = timed(dict(select=B.SELECT_UNIFORM, graph_mode=head["graph_mode"],
                                   spmv_format=layout_pin), args.steps, args.warmup)
     sm = st_mixed[-1]
@@ -367,6 +370,8 @@ def run_ours(args, rank, world, dist):
         "fp64_uniform": {"ms": round(ms_fp64, 4), "iters": s64["iters"], "true_relres": s64["true_relres"],
                          "setup_ms": round(s64["setup_ms"], 3), "solve_ms": round(s64["solve_ms"], 3)},
         "speedup_vs_fp64": round(ms_fp64 / ms_mixed, 3),
+        "step_ms": {"median": round(statistics.median(step_ms), 4), "min": round(min(step_ms), 4),
+                    "max": round(max(step_ms), 4)},
         "modes": modes,
         "roofline": roofline,
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -434,6 +439,29 @@ def other_configs():
                     "modes": res,
                     "speedup_vs_fp64": {m: round(base / r["ms"], 3) for m, r in res.items() if base}}
         del dA, b, xs
+
+    # the paper's own configuration: BJAC(k = 2, t = 2) of Eq. 3-2 / 3-3 with 32 blocks on the
+    # Diff3D laws of Section 4.1.1 (Table 4.2 / Figure 4.3 report 148 -> 165 iterations for
+    # Const and 185 -> 211 for Dis(1000), uniform -> fp32 fMP, on CPUs with an unstated b)
+    paper = {}
+    for law in ("const", "ani", "dis", "rand"):
+        pr = PB.make_problem(f"diff3d-{law}", seed=0, m=128)
+        bp = np.linspace(0, pr.A.n, 33).astype(np.int32)
+        dA = B.DeviceCSR(pr.A)
+        xs = torch.as_tensor(pr.x_star).cuda()
+        b = torch.empty(pr.A.n, dtype=torch.float64, device="cuda")
+        B.bjac_spmv(dA, xs, b)
+        pols = {"uniform-fp64": dict(select=B.SELECT_KT, fixed_fmt=FMT["fp64"]),
+                "fmp-fp32": dict(select=B.SELECT_KT, fixed_fmt=FMT["fp32"]),
+                "amp-hl10-fp32": dict(select=B.SELECT_KT, fixed_fmt=FMT["fp32"], temporal=B.TEMPORAL_HL,
+                                      adp_tol=10.0)}
+        timed_step(dA, bp, b, pols["fmp-fp32"])
+        res = {m: timed_step(dA, bp, b, p)[0] for m, p in pols.items()}
+        paper[f"diff3d-{law}-128^3"] = {m: {k: r[k] for k in ("ms", "setup_ms", "solve_ms", "iters", "true_relres",
+                                                             "converged")} for m, r in res.items()}
+        paper[f"diff3d-{law}-128^3"]["speedup_fmp_vs_fp64"] = round(res["uniform-fp64"]["ms"] / res["fmp-fp32"]["ms"], 3)
+        del dA, b, xs
+    out["paper_bjac_k2t2_32blocks"] = paper
 
     # 256 independent 2D systems in one persistent launch vs one after another
     t0 = time.time()

@@ -311,6 +311,18 @@ def fem2d_q1_9pt(ke: np.ndarray) -> CSR:
 # ----------------------------------------------------------------------------------------
 # Block partitions
 # ----------------------------------------------------------------------------------------
+def diag_boost(A: CSR, pdiag: float) -> CSR:
+    """Input of the diagonal-dominance experiment of Section 4.5.2: every diagonal entry grows by
+    pdiag times the sum of the magnitudes of the row's off-diagonal entries."""
+    val = np.array(A.val, dtype=np.float64, copy=True)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = A.colidx == rows
+    off = np.zeros(A.n)
+    np.add.at(off, rows[~diag], np.abs(val[~diag]))
+    val[diag] += pdiag * off[rows[diag]]
+    return CSR(A.n, A.rowptr, A.colidx, val)
+
+
 def uniform_blocks(n: int, bs: int) -> np.ndarray:
     """Contiguous blocks of bs rows; the last block takes the ragged remainder."""
     bp = np.arange(0, n, bs, dtype=np.int64)

@@ -86,3 +86,31 @@ def test_full_size_iterations_match_oracle(full, policy):
     assert abs(st["iters"] - r["iters"]) <= slack, (st["iters"], r["iters"])
     err = float(torch.linalg.norm(x - cuda(pr.x_star)) / torch.linalg.norm(cuda(pr.x_star)))
     assert err <= 10 * r["x_rel_err"] + 1e-9
+
+
+KT_REF = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "kt_reference.json")
+
+
+@pytest.mark.parametrize("law", ["const", "ani", "dis", "rand"])
+def test_full_size_paper_bjac_k2t2_vs_oracle(law):
+    """The paper's configuration (BJAC(2, 2) with 32 blocks, Diff3D laws at 128^3) against the
+    oracle's full-size solves in oracle/kt_reference.json (written by oracle/kt_reference_runs.py)."""
+    B = need_gpu()
+    with open(KT_REF) as f:
+        ref = json.load(f)
+    pr = PB.make_problem(f"diff3d-{law}", seed=0, m=128)
+    bp = np.linspace(0, pr.A.n, 33).astype(np.int32)
+    dA = B.DeviceCSR(pr.A)
+    b = torch.empty(pr.A.n, dtype=torch.float64, device="cuda")
+    B.bjac_spmv(dA, cuda(pr.x_star), b)
+    for fmt, pol in ((B.FP64, "uniform"), (B.FP32, "fp32")):
+        r = ref[f"{law}_m128_nb32_k2t2_{pol}"]
+        h = B.bjac_setup(dA, bp, select=B.SELECT_KT, fixed_fmt=fmt)
+        x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+        st = h.solve(b, x, tol=1e-10, maxit=5000)
+        h.close()
+        assert st["converged"] and st["true_relres"] <= 1e-10
+        slack = 2 if pol == "uniform" else max(3, 0.05 * r["iters"])
+        assert abs(st["iters"] - r["iters"]) <= slack, (law, pol, st["iters"], r["iters"])
+        err = float(torch.linalg.norm(x - cuda(pr.x_star)) / np.linalg.norm(pr.x_star))
+        assert err <= 10 * r["x_rel_err"] + 1e-12

@@ -652,3 +652,12 @@ def test_kt_pcg_policy_limits(oracle):
                           (oracle.POLICY_LH, 1e-30, fmp), (oracle.POLICY_LH, 1e30, uni)):
         got = oracle.pcg_kt(pr.A, bp, b, policy=pol, adp_tol=tol, maxit=3000)
         assert got["iters"] == ref["iters"] and np.array_equal(got["x"], ref["x"])
+
+
+def test_diag_boost_input_matches_oracle_definition(oracle):
+    # Section 4.5.2: a_ii += P_diag * sum_{j != i} |a_ij| (input of the P_diag experiment)
+    pr = PB.make_problem("subcube3d", seed=8, m=10)
+    for pd in (0.0, 1.0, 8.0):
+        got = PB.diag_boost(pr.A, pd)
+        ref = oracle.diag_boost(pr.A, pd)
+        assert np.allclose(got.val, ref.val, rtol=1e-15, atol=0)
