@@ -163,7 +163,7 @@ __device__ __forceinline__ void tile_spmv(const BatchDev &d, const TileInfo &ti,
 
 // z = M^-1 r on a tile (blocks lie inside tiles). mode 0: plain (with p = z when init);
 // mode 1: r -= alpha q first. part_a += r.z, part_b += r.r.
-template <int TR>
+template <int TR, int FMT>
 __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti, double alpha, int fused, int init,
                                            float *s_rh, double *s_r, double &part_a, double &part_b) {
     const int lane = threadIdx.x & 31;
@@ -201,7 +201,7 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
                 bs = d.block_ptr[bk + 1] - bs0;
             }
             const int i = row - bs0, off = bs0 - r0;
-            const int f = d.fmt[bk];
+            const int f = FMT >= 0 ? FMT : d.fmt[bk];      // a batch of one format knows it at compile time
             const uint8_t *base = d.pool + d.qoff[bk];
             const int eb = f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2;
             double zi;
@@ -245,7 +245,7 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
     __syncwarp();
 }
 
-template <int TR, int MINB>
+template <int TR, int MINB, int FMT>
 __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
     __shared__ __align__(16) float s_rh[kWarps][TR];
     __shared__ __align__(16) double s_r[kWarps][TR];
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         if (!grid_barrier(d)) return;
         per_tile([&](int, const TileInfo &ti, double &a, double &b2) {
             if (__ldcg(d.state + ti.sys) != kRunning) return;
-            tile_apply<TR>(d, ti, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
+            tile_apply<TR, FMT>(d, ti, 0.0, 0, 1, s_rh[warp], s_r[warp], a, b2);
         });
         if (!grid_barrier(d)) return;
         for (int s = blockIdx.x; s < d.nsys; s += gridDim.x) {
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             // C: r -= alpha q, z = M^-1 r, r.r and r.z
             per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
                 if (__ldcg(d.state + ti.sys) != kRunning) return;     // sigma broke down in B
-                tile_apply<TR>(d, ti, __ldcg(d.alpha + ti.sys), 1, 0, s_rh[warp], s_r[warp], a, b2);
+                tile_apply<TR, FMT>(d, ti, __ldcg(d.alpha + ti.sys), 1, 0, s_rh[warp], s_r[warp], a, b2);
             });
             if (!grid_barrier(d)) return;
             // D: convergence and beta per system; count the systems still running
@@ -498,6 +498,7 @@ struct bjac_batch {
     int grid = 0;
     float tune_ms[6] = {0, 0, 0, 0, 0, 0};   // timings of the kernel variants
     int variant = 0;
+    bool fp32_only = false;                  // every block binary32: the kernels for that format
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double tol_cached = -1.0;
@@ -580,12 +581,14 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     return d;
 }
 
-// kernel variants the setup times: tile height x CTAs per SM the registers are sized for
+// kernel variants the setup times: tile height x CTAs per SM the registers are sized for; a
+// batch whose blocks are all binary32 (the usual batched format) also gets kernels compiled for
+// that format alone, which need fewer registers
 constexpr int kBatchVariants = 6;
 constexpr int kVarTR[kBatchVariants] = {32, 32, 32, 64, 64, 64};
 constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6};
 
-template <int TR, int MINB>
+template <int TR, int MINB, int FMT>
 static int launch_batched_t(const BatchDev &d, cudaStream_t st, int grid) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
@@ -597,41 +600,50 @@ static int launch_batched_t(const BatchDev &d, cudaStream_t st, int grid) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MPB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batched<TR, MINB>, d));
+    MPB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batched<TR, MINB, FMT>, d));
     return MPBJAC_OK;
 }
 
-static int launch_batched(int variant, const BatchDev &d, cudaStream_t st, int grid) {
+template <int FMT>
+static int launch_batched_f(int variant, const BatchDev &d, cudaStream_t st, int grid) {
     switch (variant) {
-        case 0: return launch_batched_t<32, 2>(d, st, grid);
-        case 1: return launch_batched_t<32, 4>(d, st, grid);
-        case 2: return launch_batched_t<32, 6>(d, st, grid);
-        case 3: return launch_batched_t<64, 2>(d, st, grid);
-        case 4: return launch_batched_t<64, 4>(d, st, grid);
-        default: return launch_batched_t<64, 6>(d, st, grid);
+        case 0: return launch_batched_t<32, 2, FMT>(d, st, grid);
+        case 1: return launch_batched_t<32, 4, FMT>(d, st, grid);
+        case 2: return launch_batched_t<32, 6, FMT>(d, st, grid);
+        case 3: return launch_batched_t<64, 2, FMT>(d, st, grid);
+        case 4: return launch_batched_t<64, 4, FMT>(d, st, grid);
+        default: return launch_batched_t<64, 6, FMT>(d, st, grid);
     }
 }
 
-template <int TR, int MINB>
+static int launch_batched(int variant, bool fp32_only, const BatchDev &d, cudaStream_t st, int grid) {
+    return fp32_only ? launch_batched_f<BJAC_FP32>(variant, d, st, grid) : launch_batched_f<-1>(variant, d, st, grid);
+}
+
+template <int TR, int MINB, int FMT>
 static int per_sm_of() {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<TR, MINB>, kNT, 0) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batched<TR, MINB, FMT>, kNT, 0) != cudaSuccess ||
+        per < 1)
         per = 1;
     return per;
 }
 
-// CTAs of a variant that are co-resident on the GPU (the cooperative grid)
-static int max_coresident(int variant) {
-    int per = 1;
+template <int FMT>
+static int per_sm_f(int variant) {
     switch (variant) {
-        case 0: per = per_sm_of<32, 2>(); break;
-        case 1: per = per_sm_of<32, 4>(); break;
-        case 2: per = per_sm_of<32, 6>(); break;
-        case 3: per = per_sm_of<64, 2>(); break;
-        case 4: per = per_sm_of<64, 4>(); break;
-        default: per = per_sm_of<64, 6>(); break;
+        case 0: return per_sm_of<32, 2, FMT>();
+        case 1: return per_sm_of<32, 4, FMT>();
+        case 2: return per_sm_of<32, 6, FMT>();
+        case 3: return per_sm_of<64, 2, FMT>();
+        case 4: return per_sm_of<64, 4, FMT>();
+        default: return per_sm_of<64, 6, FMT>();
     }
-    return sm_count() * per;
+}
+
+// CTAs of a variant that are co-resident on the GPU (the cooperative grid)
+static int max_coresident(int variant, bool fp32_only) {
+    return sm_count() * (fp32_only ? per_sm_f<BJAC_FP32>(variant) : per_sm_f<-1>(variant));
 }
 
 // one warp per 32-row slice of a tile: its rows' entries column-major, padded with (0, -1)
@@ -755,7 +767,7 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
 static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bool use_graph) {
     BatchDev d = batch_dev(h, tol, maxit);
     MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned int), st));
-    if (!use_graph) return launch_batched(h->variant, d, st, h->grid);
+    if (!use_graph) return launch_batched(h->variant, h->fp32_only, d, st, h->grid);
     if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
         if (h->graph) cudaGraphDestroy(h->graph);
@@ -764,7 +776,7 @@ static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bo
         cudaStream_t cs;
         MPB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         MPB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_batched(h->variant, d, cs, h->grid);
+        int rc = launch_batched(h->variant, h->fp32_only, d, cs, h->grid);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -905,6 +917,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     BTRY(cudaStreamSynchronize(st));
     if (hstat[0] != 0) return bail(fail(MPBJAC_ERR_NOT_SPD, "a diagonal block of the batch is not positive definite"));
     for (uint8_t f : hf) h->blocks_per_fmt[f & 3] += 1;
+    h->fp32_only = h->blocks_per_fmt[BJAC_FP32] == nb_tot;
     (void)big;
     // vectors and per-system state
     BTRY(cudaMalloc(&h->b, sizeof(double) * n_tot));
@@ -932,7 +945,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
                 if (rc) return bail(rc);
             }
             h->variant = v;
-            h->grid = max_coresident(v);
+            h->grid = max_coresident(v, h->fp32_only);
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 BTRY(cudaMemsetAsync(h->x, 0, sizeof(double) * n_tot, st));
@@ -956,7 +969,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
             if (rc) return bail(rc);
         }
         h->variant = best_v;
-        h->grid = max_coresident(best_v);
+        h->grid = max_coresident(best_v, h->fp32_only);
     }
 #undef BTRY
     cudaEventRecord(e1, st);
