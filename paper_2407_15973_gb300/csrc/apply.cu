@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
 // computed (two blocks in flight per warp). No TMA, no shared-memory copy of Q, no CTA sync.
 // ----------------------------------------------------------------------------------------
 template <typename QT, int BS, int MODE>
-__global__ void __launch_bounds__(kNT, 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
+__global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
     pdl_enter();
     using Geo = RegGeom<QT, BS>;
     constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
