@@ -646,6 +646,21 @@ static int max_coresident(int variant, bool fp32_only) {
     return sm_count() * (fp32_only ? per_sm_f<BJAC_FP32>(variant) : per_sm_f<-1>(variant));
 }
 
+// variant chosen per batch shape (systems, rows, nonzeros, blocks, all binary32)
+struct BatchTuneKey {
+    int nsys, n, nnz, nb;
+    bool fp32_only;
+    bool operator==(const BatchTuneKey &o) const {
+        return nsys == o.nsys && n == o.n && nnz == o.nnz && nb == o.nb && fp32_only == o.fp32_only;
+    }
+};
+struct BatchTune {
+    BatchTuneKey key;
+    int variant;
+    float ms[kBatchVariants];
+};
+static std::vector<BatchTune> g_batch_tune;
+
 // one warp per 32-row slice of a tile: its rows' entries column-major, padded with (0, -1)
 __global__ void k_batch_ell(int nslices, int spt, const int32_t *__restrict__ tile_row,
                             const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
@@ -931,8 +946,19 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 6));
     BTRY(cudaMalloc(&h->d_sys_tile, sizeof(int32_t) * (nsys + 1)));
     // autotuner: tile height (32 or 64 rows per warp task) and CTAs per SM (2, 4, 6: the
-    // register budget of the kernel) timed on 20 iterations of this batch
-    {
+    // register budget of the kernel) timed on 20 iterations of this batch; the choice is kept
+    // per batch shape for the life of the process
+    const BatchTuneKey key{nsys, (int)n_tot, (int)nnz_tot, (int)nb_tot, h->fp32_only};
+    const BatchTune *cached = nullptr;
+    for (const auto &e : g_batch_tune)
+        if (e.key == key) cached = &e;
+    if (cached) {
+        for (int v = 0; v < kBatchVariants; ++v) h->tune_ms[v] = cached->ms[v];
+        rc = build_tiles(h, kVarTR[cached->variant], bp);
+        if (rc) return bail(rc);
+        h->variant = cached->variant;
+        h->grid = max_coresident(cached->variant, h->fp32_only);
+    } else {
         BTRY(cudaMemsetAsync(h->b, 0, sizeof(double) * n_tot, st));
         std::vector<double> ones(n_tot, 1.0);
         BTRY(cudaMemcpy(h->b, ones.data(), sizeof(double) * n_tot, cudaMemcpyHostToDevice));
@@ -970,6 +996,9 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         }
         h->variant = best_v;
         h->grid = max_coresident(best_v, h->fp32_only);
+        BatchTune e{key, best_v, {}};
+        for (int v = 0; v < kBatchVariants; ++v) e.ms[v] = h->tune_ms[v];
+        g_batch_tune.push_back(e);
     }
 #undef BTRY
     cudaEventRecord(e1, st);
