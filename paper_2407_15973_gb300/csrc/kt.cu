@@ -23,7 +23,7 @@
 namespace mpbjac {
 
 struct KtArgs {
-    int n, nslices;
+    int n, nslices, nb;
     const int32_t *off, *col;
     const void *val;          // T[entries]
     const void *dinv;         // T[n]
@@ -93,11 +93,19 @@ __device__ __forceinline__ T kt_row_sum(const T *pv, const int32_t *pc, int len,
     return acc;
 }
 
+constexpr int kKtSmemBlocks = 1024;      // block offsets kept in shared memory up to this many blocks
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSpNT) k_kt_sweep(KtArgs a, SolverState *S) {
     pdl_enter();
     constexpr int NW = kSpNT / 32;
     __shared__ double red[NW];
+    __shared__ int32_t s_bp[kKtSmemBlocks + 1];
+    const bool bp_smem = a.nb <= kKtSmemBlocks;
+    if (!a.first && bp_smem) {
+        for (int i = threadIdx.x; i <= a.nb; i += kSpNT) s_bp[i] = a.block_ptr[i];
+        __syncthreads();
+    }
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (a.from_state && S->use_low != a.prec) return;
@@ -131,9 +139,21 @@ __global__ void __launch_bounds__(kSpNT) k_kt_sweep(KtArgs a, SolverState *S) {
         } else {
             int blo = 0, bhi = 0;
             if (row < a.n) {
-                const int b = a.rblk[row];
-                blo = __ldg(a.block_ptr + b);
-                bhi = __ldg(a.block_ptr + b + 1);
+                if (bp_smem) {
+                    // the row's block by bisection of the offsets in shared memory
+                    int lo = 0, hi = a.nb;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_bp[mid] <= row) lo = mid;
+                        else hi = mid;
+                    }
+                    blo = s_bp[lo];
+                    bhi = s_bp[lo + 1];
+                } else {
+                    const int b = a.rblk[row];
+                    blo = __ldg(a.block_ptr + b);
+                    bhi = __ldg(a.block_ptr + b + 1);
+                }
             }
             const T sum = kt_row_sum<T, true>(pv, pc, len, yin, blo, bhi);
             if (row < a.n) yi = fma_t<T>(dinv[row], w[row] - sum, yin[row]);
@@ -289,6 +309,7 @@ int launch_kt_apply(int mode, int prec, bool from_state, const KtSet &K, const A
     if (prec == 1 && !K.val32) return fail(MPBJAC_ERR_UNSUPPORTED, "no binary32 BJAC(k,t) set");
     KtArgs a{};
     a.n = K.n;
+    a.nb = K.nb;
     a.nslices = K.sell.nslices;
     a.off = K.sell.off;
     a.col = K.sell.col;

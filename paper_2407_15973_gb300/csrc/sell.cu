@@ -143,7 +143,7 @@ __device__ __forceinline__ void sell_head(int s, int nslices, int lane, const in
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kSpNT, 4) k_spmv_sell(int n, int nslices, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ col, const double *__restrict__ val,
                                                        const double *__restrict__ x, const double *__restrict__ b,
                                                        double *__restrict__ y, double *part, unsigned int *ticket,
