@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workload configurations (27-point anisotropic 160^3, 256 batched "
                          "2D systems, Voronoi 256^3)")
+    ap.add_argument("--profile-kt", action="store_true",
+                    help="with --profile-iters: profile fMP BJAC(2, 2) with 32 blocks on the 128^3 Diff3D-Const "
+                         "system instead of the headline policy")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only set up the headline policy and run this many eager PCG iterations "
                          "(a short, fixed launch sequence for ncu)")
@@ -215,8 +218,18 @@ def run_ours(args, rank, world, dist):
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
                 graph_mode=1 if args.eager else 0, spmv_format=layout_pin)
     if args.profile_iters:
-        h = B.bjac_setup(dA, pr.block_ptr, **head)
-        prof = h.profile(b, x, tol=TOL, maxit=args.profile_iters)
+        if args.profile_kt:
+            pk = PB.make_problem("diff3d-const", seed=0, m=args.m)
+            dK = B.DeviceCSR(pk.A)
+            bk = torch.empty(pk.A.n, dtype=torch.float64, device="cuda")
+            B.bjac_spmv(dK, torch.as_tensor(pk.x_star).cuda(), bk)
+            xk = torch.zeros(pk.A.n, dtype=torch.float64, device="cuda")
+            h = B.bjac_setup(dK, np.linspace(0, pk.A.n, 33).astype(np.int32), select=B.SELECT_KT,
+                             fixed_fmt=FMT["fp32"], graph_mode=head["graph_mode"])
+            prof = h.profile(bk, xk, tol=TOL, maxit=args.profile_iters)
+        else:
+            h = B.bjac_setup(dA, pr.block_ptr, **head)
+            prof = h.profile(b, x, tol=TOL, maxit=args.profile_iters)
         h.close()
         return {"profile": prof}
     with ClockSampler(dev) as clk:
