@@ -11,8 +11,7 @@
 // bitwise what the general formulas give.
 //
 // One launch per sweep: the first sweep of an outer step also forms w (with one SpMV of A on
-// z when j > 0), the others run one SpMV of A_bd on y; the first sweep of all (w = r-hat,
-// y = RN(dinv w)) is folded into the second, which recomputes y_j for the gathered columns. Every launch walks the SELL-32 copy of
+// z when j > 0), the others run one SpMV of A_bd on y. Every launch walks the SELL-32 copy of
 // A (slices of 32 rows, column-major, one warp per slice); out-of-block entries are skipped
 // by comparing the column with the row's block bounds. The last sweep widens z into the PCG
 // vector and reduces r.z like the other apply kernels.
@@ -38,7 +37,6 @@ struct KtArgs {
     int prec, from_state;
     int outer;                // 1: this sweep forms w = r-hat - A z first (j > 0)
     int first;                // 1: this sweep is the first inner sweep (y = 0 before it)
-    int fuse0;                // 1: second inner sweep of the first outer step, the first folded in
     int acc;                  // 1: last inner sweep of an outer step: z = z + y
     int zero_z;               // 1: z is zero before this accumulation (j = 0)
     int final_;               // 1: last sweep of the apply: widen z, r.z
@@ -55,13 +53,10 @@ template <typename T> __device__ __forceinline__ double widen(T v);
 template <> __device__ __forceinline__ double widen<float>(float v) { return f32_to_f64(v); }
 template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
 
-// U entries of this lane's row: loads, gathers, then the chain over the included entries.
-// F0: the gathered value is the first inner sweep's y_j = RN(dinv_j r-hat_j), recomputed from
-// r and dinv (bitwise what that sweep stores), instead of a load of x.
-template <typename T, bool BD, bool F0, int U>
+// U entries of this lane's row: loads, gathers, then the chain over the included entries
+template <typename T, bool BD, int U>
 __device__ __forceinline__ void kt_part(const T *__restrict__ pv, const int32_t *__restrict__ pc,
-                                        const T *__restrict__ x, int blo, int bhi, const T *__restrict__ dinv,
-                                        const double *__restrict__ r, T &acc) {
+                                        const T *__restrict__ x, int blo, int bhi, T &acc) {
     T v[U], xv[U];
     int c[U];
 #pragma unroll
@@ -73,28 +68,26 @@ __device__ __forceinline__ void kt_part(const T *__restrict__ pv, const int32_t 
     for (int u = 0; u < U; ++u) {
         const bool in = c[u] >= 0 && (!BD || (c[u] >= blo && c[u] < bhi));
         c[u] = in ? c[u] : -1;
-        if (F0) xv[u] = in ? fma_t<T>(__ldg(dinv + c[u]), rhat<T>(__ldg(r + c[u])) - T(0), T(0)) : T(0);
-        else xv[u] = in ? __ldg(x + c[u]) : T(0);
+        xv[u] = in ? __ldg(x + c[u]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (c[u] >= 0) acc = fma_t<T>(v[u], xv[u], acc);
 }
 
-template <typename T, bool BD, bool F0 = false>
-__device__ __forceinline__ T kt_row_sum(const T *pv, const int32_t *pc, int len, const T *x, int blo, int bhi,
-                                        const T *dinv = nullptr, const double *r = nullptr) {
+template <typename T, bool BD>
+__device__ __forceinline__ T kt_row_sum(const T *pv, const int32_t *pc, int len, const T *x, int blo, int bhi) {
     T acc = T(0);
     int j = 0;
-    for (; j + 8 <= len; j += 8) kt_part<T, BD, F0, 8>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc);
+    for (; j + 8 <= len; j += 8) kt_part<T, BD, 8>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc);
     switch (len - j) {
-        case 1: kt_part<T, BD, F0, 1>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 2: kt_part<T, BD, F0, 2>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 3: kt_part<T, BD, F0, 3>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 4: kt_part<T, BD, F0, 4>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 5: kt_part<T, BD, F0, 5>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 6: kt_part<T, BD, F0, 6>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
-        case 7: kt_part<T, BD, F0, 7>(pv + 32 * j, pc + 32 * j, x, blo, bhi, dinv, r, acc); break;
+        case 1: kt_part<T, BD, 1>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 2: kt_part<T, BD, 2>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 3: kt_part<T, BD, 3>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 4: kt_part<T, BD, 4>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 5: kt_part<T, BD, 5>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 6: kt_part<T, BD, 6>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
+        case 7: kt_part<T, BD, 7>(pv + 32 * j, pc + 32 * j, x, blo, bhi, acc); break;
         default: break;
     }
     return acc;
@@ -162,19 +155,8 @@ __global__ void __launch_bounds__(kSpNT) k_kt_sweep(KtArgs a, SolverState *S) {
                     bhi = __ldg(a.block_ptr + b + 1);
                 }
             }
-            if (a.fuse0) {
-                // second inner sweep of the first outer step with the first folded in: w = r-hat
-                // and y_j = RN(dinv_j r-hat_j) are formed here
-                const T sum = kt_row_sum<T, true, true>(pv, pc, len, nullptr, blo, bhi, dinv, a.r);
-                if (row < a.n) {
-                    const T wi0 = rhat<T>(a.r[row]);
-                    w[row] = wi0;
-                    yi = fma_t<T>(dinv[row], wi0 - sum, fma_t<T>(dinv[row], wi0 - T(0), T(0)));
-                }
-            } else {
-                const T sum = kt_row_sum<T, true>(pv, pc, len, yin, blo, bhi);
-                if (row < a.n) yi = fma_t<T>(dinv[row], w[row] - sum, yin[row]);
-            }
+            const T sum = kt_row_sum<T, true>(pv, pc, len, yin, blo, bhi);
+            if (row < a.n) yi = fma_t<T>(dinv[row], w[row] - sum, yin[row]);
         }
         if (row >= a.n) continue;
         yout[row] = yi;
@@ -347,9 +329,7 @@ int launch_kt_apply(int mode, int prec, bool from_state, const KtSet &K, const A
         a.zin = zbuf[(j + 1) & 1];
         a.zout = zbuf[j & 1];
         for (int i = 0; i < K.t; ++i) {
-            if (j == 0 && i == 0 && K.t >= 2) continue;     // folded into the next sweep
             a.first = i == 0;
-            a.fuse0 = (j == 0 && i == 1) ? 1 : 0;
             a.outer = (i == 0 && j > 0) ? 1 : 0;
             a.yin = ybuf[cur];
             a.yout = ybuf[cur ^ 1];
