@@ -51,7 +51,7 @@ def parse():
                     help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
     ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell", "sell-pf"],
                     help="pin the loop SpMV's matrix layout instead of the timed choice")
-    ap.add_argument("--apply-kernel", default="auto", choices=["auto", "generic", "tma", "reg"],
+    ap.add_argument("--apply-kernel", default="auto", choices=["auto", "generic", "tma", "reg", "mix"],
                     help="pin the low-precision apply kernel instead of the timed choice")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven loop instead of the CUDA graph (the profiler sees every kernel)")
@@ -213,7 +213,7 @@ def run_ours(args, rank, world, dist):
 
     spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
     B.bjac_spmv_kernel(spmv_pin)
-    apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3}[args.apply_kernel]
+    apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3, "mix": 4}[args.apply_kernel]
     layout_pin = {"auto": 0, "csr": 1, "sell": 2, "sell-pf": 3}[args.spmv_layout]
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
                 graph_mode=1 if args.eager else 0, spmv_format=layout_pin)
@@ -313,7 +313,8 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         hl.close()
         layout_ms[name] = round(ev0.elapsed_time(ev1) / 20, 5)
-    apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg"}[apply_kernel]
+    apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg",
+                  "mixed": "k_apply_mix32"}[apply_kernel]
     csr_name = {"tma": "k_spmv", "warp": "k_spmv_warp", "pipe": "k_spmv_pipe", "wtma": "k_spmv_wtma"}[
         B.bjac_spmv_tuning(dA)[0]]
     spmv_name = {"sell32": "k_spmv_sell", "sell32-prefetch": "k_spmv_sell_pf"}.get(layout["format"], csr_name)

@@ -90,8 +90,9 @@ typedef struct bjac_policy {
     double safety_theta;    /* MLP promotion threshold on kappa_1 * u_f (0.5 if <= 0)      */
     const float *mlp_params;/* HOST pointer, bjac_mlp_param_count() floats, for SELECT_MLP */
     const uint8_t *block_fmt;/* HOST pointer, nb formats, for SELECT_GIVEN                  */
-    int32_t apply_variant;  /* low-precision apply kernel: 0 autotuned (uniform sets), 1 generic
-                               warp-per-block, 2 TMA-staged, 3 register-direct (bs 32)        */
+    int32_t apply_variant;  /* low-precision apply kernel: 0 autotuned, 1 generic warp-per-
+                               block, 2 TMA-staged, 3 register-direct (bs 32, one format),
+                               4 register-direct for 32-row blocks of mixed formats           */
     int32_t graph_mode;     /* 0: each solve runs as one CUDA graph with a device-side while
                                loop (default); 1: the host enqueues the same kernels in
                                batches of 32 iterations and checks the state between batches */
@@ -260,8 +261,8 @@ int bjac_export(bjac_handle *h, uint8_t *fmt, float *scale, int64_t *qoff, uint8
 int bjac_import_inverse(bjac_handle *h, const double *G);
 
 /* Kernel the handle uses for the low-precision apply (0 generic, 1 TMA-staged, 2
- * register-direct) and, when the autotuner ran, its timings in ms (tune_ms[3], HOST,
- * nullable; 0 for kernels not timed). */
+ * register-direct, 3 register-direct for mixed formats) and, when the autotuner ran, its
+ * timings in ms (tune_ms[4], HOST, nullable; 0 for kernels not timed). */
 int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
 /* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):

@@ -264,9 +264,9 @@ class Handle:
     def apply_kernel(self):
         """(kernel name, autotuner timings in ms) of the low-precision apply."""
         k = C.c_int32()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         _check(lib().bjac_apply_kernel(self.h, C.byref(k), ms))
-        return {0: "generic", 1: "tma", 2: "register"}[k.value], list(ms)
+        return {0: "generic", 1: "tma", 2: "register", 3: "mixed"}[k.value], list(ms)
 
     def info(self):
         nb, pb, ge = C.c_int32(), C.c_int64(), C.c_int64()

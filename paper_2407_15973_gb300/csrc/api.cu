@@ -44,7 +44,7 @@ int sm_count() {
 static int fmt_bytes(int f) { return f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2; }
 
 // kernels that can apply the low-precision set (the binary64 set always uses the generic one)
-enum ApplyKind { kApplyKindGeneric = 0, kApplyKindTma = 1, kApplyKindReg = 2 };
+enum ApplyKind { kApplyKindGeneric = 0, kApplyKindTma = 1, kApplyKindReg = 2, kApplyKindMix = 3 };
 
 // ----------------------------------------------------------------------------------------
 // vector kernels of the PCG loop
@@ -127,7 +127,7 @@ struct bjac_handle {
     float setup_ms = 0.0f;
     int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
     int apply_kind = kApplyKindGeneric;   // kernel used for the low-precision set
-    float tune_ms[3] = {0, 0, 0};         // autotuner timings (generic, TMA, register)
+    float tune_ms[4] = {0, 0, 0, 0};      // autotuner timings (generic, TMA, register, mixed register)
     SellMat sell{};                       // SELL-32 copy of A (val NULL if not kept)
     int use_sell = 0;                     // loop SpMV on the SELL-32 copy
     float spmv_ms[3] = {0, 0, 0};         // timed y = A x: CSR, SELL-32, SELL-32 with prefetch
@@ -208,22 +208,24 @@ struct TuneKey {
 };
 struct TuneResult {
     int kind;
-    float ms[3];
+    float ms[4];
 };
 static std::vector<std::pair<TuneKey, TuneResult>> g_tune_cache;
 
 static int choose_apply_kind(bjac_handle *h) {
     const bool tma_ok = tma_supported(h->lo, h->n);
     const bool reg_ok = reg_supported(h->lo, h->n);
+    const bool mix_ok = mix_supported(h->lo, h->n);
     const int v = h->pol.apply_variant;
-    if (v == 1 || !tma_ok) { h->apply_kind = kApplyKindGeneric; return MPBJAC_OK; }
-    if (v == 2) { h->apply_kind = kApplyKindTma; return MPBJAC_OK; }
-    if (v == 3) { h->apply_kind = reg_ok ? kApplyKindReg : kApplyKindTma; return MPBJAC_OK; }
+    if (v == 4) { h->apply_kind = mix_ok ? kApplyKindMix : kApplyKindGeneric; return MPBJAC_OK; }
+    if (v == 1 || (!tma_ok && !mix_ok)) { h->apply_kind = kApplyKindGeneric; return MPBJAC_OK; }
+    if (v == 2) { h->apply_kind = tma_ok ? kApplyKindTma : kApplyKindGeneric; return MPBJAC_OK; }
+    if (v == 3) { h->apply_kind = reg_ok ? kApplyKindReg : tma_ok ? kApplyKindTma : kApplyKindGeneric; return MPBJAC_OK; }
     const TuneKey key{h->lo.ufmt, h->lo.ubs, h->nb};
     for (auto &e : g_tune_cache)
         if (e.first == key) {
             h->apply_kind = e.second.kind;
-            for (int i = 0; i < 3; ++i) h->tune_ms[i] = e.second.ms[i];
+            for (int i = 0; i < 4; ++i) h->tune_ms[i] = e.second.ms[i];
             return MPBJAC_OK;
         }
     cudaStream_t st = h->stream;
@@ -247,14 +249,19 @@ static int choose_apply_kind(bjac_handle *h) {
     MPB_CUDA(cudaEventCreate(&e1));
     // interleaved rounds over the candidate kernels, median of 7 after a warm-up round
     constexpr int kRounds = 8;
-    float t[3][kRounds] = {};
+    float t[4][kRounds] = {};
+    auto usable = [&](int k) {
+        return k == kApplyKindGeneric || (k == kApplyKindTma && tma_ok) || (k == kApplyKindReg && reg_ok) ||
+               (k == kApplyKindMix && mix_ok);
+    };
     for (int rep = 0; rep < kRounds; ++rep) {
-        for (int k = 0; k < 3; ++k) {
-            if (k == kApplyKindReg && !reg_ok) continue;
+        for (int k = 0; k < 4; ++k) {
+            if (!usable(k)) continue;
             MPB_CUDA(cudaEventRecord(e0, st));
             int rc = k == kApplyKindGeneric ? launch_apply_generic(kApplyStandalone, h->lo, h->lo, io, nullptr, st)
                      : k == kApplyKindTma   ? launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, st)
-                                            : launch_apply_reg(kApplyStandalone, h->lo, io, nullptr, st);
+                     : k == kApplyKindReg   ? launch_apply_reg(kApplyStandalone, h->lo, io, nullptr, st)
+                                            : launch_apply_mix(kApplyStandalone, h->lo, io, nullptr, st);
             if (rc) return rc;
             MPB_CUDA(cudaEventRecord(e1, st));
             MPB_CUDA(cudaEventSynchronize(e1));
@@ -262,9 +269,9 @@ static int choose_apply_kind(bjac_handle *h) {
         }
     }
     float best = 1e30f;
-    int best_kind = kApplyKindTma;
-    for (int k = 0; k < 3; ++k) {
-        if (k == kApplyKindReg && !reg_ok) continue;
+    int best_kind = kApplyKindGeneric;
+    for (int k = 0; k < 4; ++k) {
+        if (!usable(k)) continue;
         std::sort(t[k] + 1, t[k] + kRounds);
         const float med = t[k][1 + (kRounds - 1) / 2];
         h->tune_ms[k] = med;
@@ -276,7 +283,7 @@ static int choose_apply_kind(bjac_handle *h) {
     cudaFree(z);
     cudaFree(part);
     h->apply_kind = best_kind;
-    g_tune_cache.push_back({key, TuneResult{best_kind, {h->tune_ms[0], h->tune_ms[1], h->tune_ms[2]}}});
+    g_tune_cache.push_back({key, TuneResult{best_kind, {h->tune_ms[0], h->tune_ms[1], h->tune_ms[2], h->tune_ms[3]}}});
     return MPBJAC_OK;
 }
 
@@ -653,6 +660,7 @@ static bool lo_uses_tma(const bjac_handle *h) { return h->have_lo && h->apply_ki
 // launch the low-precision set's specialised kernel (TMA-staged or register-direct)
 static int launch_lo_special(const bjac_handle *h, int mode, const ApplyIO &io, cudaStream_t st) {
     if (h->apply_kind == kApplyKindReg) return launch_apply_reg(mode, h->lo, io, h->d_S, st);
+    if (h->apply_kind == kApplyKindMix) return launch_apply_mix(mode, h->lo, io, h->d_S, st);
     return launch_apply_tma(mode, h->lo, io, h->d_S, h->n, st);
 }
 
@@ -1007,8 +1015,9 @@ extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *
                                                                 h->stream, nullptr);
     // bulk copies need 16-byte aligned sources
     const bool aligned = (reinterpret_cast<uintptr_t>(r) & 15) == 0;
-    if (set == 1 && lo_uses_tma(h) && (aligned || h->apply_kind == kApplyKindReg)) {
+    if (set == 1 && lo_uses_tma(h) && (aligned || h->apply_kind >= kApplyKindReg)) {
         if (h->apply_kind == kApplyKindReg) return launch_apply_reg(kApplyStandalone, h->lo, io, nullptr, h->stream);
+        if (h->apply_kind == kApplyKindMix) return launch_apply_mix(kApplyStandalone, h->lo, io, nullptr, h->stream);
         return launch_apply_tma(kApplyStandalone, h->lo, io, nullptr, h->n, h->stream);
     }
     return launch_apply_generic(kApplyStandalone, h->have_lo ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
@@ -1138,6 +1147,6 @@ extern "C" int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tun
     if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "handle is NULL");
     if (kind) *kind = h->apply_kind;
     if (tune_ms)
-        for (int i = 0; i < 3; ++i) tune_ms[i] = h->tune_ms[i];
+        for (int i = 0; i < 4; ++i) tune_ms[i] = h->tune_ms[i];
     return MPBJAC_OK;
 }

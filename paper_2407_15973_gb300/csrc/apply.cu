@@ -427,6 +427,108 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
 }
 
 // ----------------------------------------------------------------------------------------
+// register kernel for 32-row blocks of mixed formats (per-block rule or learned selection):
+// one block per warp iteration, the block's format the same for the whole warp. Every lane
+// issues all loads of its own row (row i of a symmetric block is its column i) before it
+// touches r, so one memory round trip serves the block; binary64 blocks of such a set read
+// their rows two vectors at a time. Same arithmetic, in the same order, as the other kernels.
+// ----------------------------------------------------------------------------------------
+template <typename QT>
+__device__ __forceinline__ float mix_row(const uint4 (&q)[8], const float *rh) {
+    constexpr int EPV = 16 / (int)sizeof(QT);
+    constexpr int VPR = 32 / EPV;
+    const float4 *rh4 = reinterpret_cast<const float4 *>(rh);
+    float a = 0.0f;
+#pragma unroll
+    for (int v = 0; v < VPR; ++v) {
+#pragma unroll
+        for (int e4 = 0; e4 < EPV; e4 += 4) {
+            const float4 r4 = rh4[(v * EPV + e4) >> 2];
+            a = fmaf(vec_entry<QT>(q[v], e4 + 0), r4.x, a);
+            a = fmaf(vec_entry<QT>(q[v], e4 + 1), r4.y, a);
+            a = fmaf(vec_entry<QT>(q[v], e4 + 2), r4.z, a);
+            a = fmaf(vec_entry<QT>(q[v], e4 + 3), r4.w, a);
+        }
+    }
+    return a;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, SolverState *S) {
+    pdl_enter();
+    __shared__ __align__(16) float s_rh[kWarps][32];
+    __shared__ __align__(16) double s_r[kWarps][32];
+    __shared__ double s_red[2][kWarps];
+    if (MODE != kApplyStandalone) {
+        if (S->state != kRunning) return;
+        if (MODE == kApplyTemporal || MODE == kApplyInit) {
+            if (!S->use_low) return;     // the binary64 set runs in the generic kernel
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    double rho = 0.0, rr = 0.0;
+    for (int blk = gw; blk < P.nb; blk += nw) {
+        const int f = __ldg(P.fmt + blk);
+        const uint4 *base = reinterpret_cast<const uint4 *>(P.pool + __ldg(P.qoff + blk));
+        const float sc = __ldg(P.scale + blk);
+        const size_t row = (size_t)blk * 32 + lane;
+        uint4 q[8];
+        const int vpr = f == BJAC_FP32 ? 8 : 4;
+        if (f != BJAC_FP64) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                if (v < vpr) q[v] = __ldcs(base + (size_t)lane * vpr + v);
+        }
+        double v = io.r[row];
+        if (MODE == kApplyFused) v = fma(-alpha, io.q[row], v);
+        s_r[warp][lane] = v;
+        s_rh[warp][lane] = f64_to_f32_rn(v);
+        __syncwarp();
+        double zi;
+        if (f == BJAC_FP64) {
+            zi = vec_row_f64(base + (size_t)lane * 16, 16, s_r[warp]);
+        } else {
+            float acc;
+            if (f == BJAC_FP32) acc = mix_row<float>(q, s_rh[warp]);
+            else if (f == BJAC_BF16) acc = mix_row<__nv_bfloat16>(q, s_rh[warp]);
+            else acc = mix_row<__half>(q, s_rh[warp]);
+            zi = f32_to_f64(acc * sc);
+        }
+        io.z[row] = zi;
+        if (MODE == kApplyInit) io.p[row] = zi;
+        if (MODE == kApplyFused) {
+            io.r_out[row] = v;
+            rr = fma(v, v, rr);
+        }
+        rho = fma(v, zi, rho);
+        __syncwarp();
+    }
+    rho = warp_sum(rho);
+    rr = warp_sum(rr);
+    if (lane == 0) {
+        s_red[0][warp] = rho;
+        s_red[1][warp] = rr;
+    }
+    __syncthreads();
+    if (MODE == kApplyStandalone && io.out == nullptr) return;
+    if (threadIdx.x == 0) {
+        double b1 = 0.0, b2 = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            b1 += s_red[0][w];
+            b2 += s_red[1][w];
+        }
+        io.part[2 * blockIdx.x] = b1;
+        io.part[2 * blockIdx.x + 1] = b2;
+    }
+    if (!last_cta(io.ticket)) return;
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red[0]);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red[1]);
+    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
+}
+
+// ----------------------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------------------
 // resident CTAs of the generic kernel (one wave), at most the blocks' warps
@@ -510,6 +612,35 @@ static int launch_reg_mode(const PSet &P, const ApplyIO &io, SolverState *S, cud
         case BJAC_BF16 * 1000 + 32: return launch_reg_t<__nv_bfloat16, 32, MODE>(P, io, S, st);
         case BJAC_FP16S * 1000 + 32: return launch_reg_t<__half, 32, MODE>(P, io, S, st);
         default: return fail(MPBJAC_ERR_UNSUPPORTED, "no register apply kernel for this format / block size");
+    }
+}
+
+template <int MODE>
+static int launch_mix_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_mix32<MODE>, kNT, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v;
+    }
+    int g = sm_count() * per_sm;
+    const int need = (P.nb + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    if (g < 1) g = 1;
+    MPB_CUDA(launch_kernel(k_apply_mix32<MODE>, g, kNT, 0, st, P, io, S));
+    return MPBJAC_OK;
+}
+
+bool mix_supported(const PSet &P, int n) { return P.ubs == 32 && (long long)P.nb * 32 == n; }
+
+int launch_apply_mix(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    switch (mode) {
+        case kApplyStandalone: return launch_mix_t<kApplyStandalone>(P, io, S, st);
+        case kApplyInit: return launch_mix_t<kApplyInit>(P, io, S, st);
+        case kApplyTemporal: return launch_mix_t<kApplyTemporal>(P, io, S, st);
+        default: return launch_mix_t<kApplyFused>(P, io, S, st);
     }
 }
 

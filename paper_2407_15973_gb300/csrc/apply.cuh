@@ -63,6 +63,8 @@ bool tma_supported(const PSet &P, int n);
 int prepare_apply_tma(const PSet &P);   // set kernel attributes (call before any capture)
 int launch_apply_tma(int mode, const PSet &P, const ApplyIO &io, SolverState *S, int n, cudaStream_t st);
 bool reg_supported(const PSet &P, int n);
+bool mix_supported(const PSet &P, int n);     // every block 32 rows: the mixed-format register kernel
+int launch_apply_mix(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st);
 int launch_apply_reg(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st);
 int launch_apply_generic(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S,
                          cudaStream_t st);

@@ -313,3 +313,67 @@ def test_invalid_inputs_rejected(B):
     with pytest.raises(B.MpbjacError) as e:
         B.bjac_setup(B.DeviceCSR(bad), PB.uniform_blocks(A.n, 8))
     assert e.value.code == B.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("m", [16, 32])
+def test_mixed_format_register_apply_bitwise(B, m):
+    """Per-block formats (as the kappa rule or the learned selector assign them) on 32-row blocks:
+    the mixed-format register kernel gives the generic kernel's z bit for bit, and both give the
+    oracle's z bit for bit on the low-precision blocks (binary32 products in natural order) and
+    within the binary64 dot-product bound on the binary64 blocks (the kernels contract with FMA)."""
+    pr = PB.make_problem("subcube3d", seed=30 + m, m=m, bs=32)
+    fmt = np.random.default_rng(m).integers(0, 4, len(pr.block_ptr) - 1).astype(np.uint8)
+    fmt[:4] = [0, 1, 2, 3]
+    P = O.Preconditioner(pr.A, pr.block_ptr, fmt=fmt)
+    dA = B.DeviceCSR(pr.A)
+    r = _hard_residual(pr.A.n)
+    zo = O.apply(P.block_ptr, P.fmt, P.pool, P.qoff, P.scale, r, mode=1)
+    row_fmt = np.repeat(fmt, 32)
+    low = row_fmt != 0
+    bound = np.zeros(pr.A.n)
+    for b in np.nonzero(fmt == 0)[0]:
+        s, e = pr.block_ptr[b], pr.block_ptr[b + 1]
+        bound[s:e] = 2 * 32 * 2.0 ** -53 * (np.abs(O.block_of(P.G, P.goff, pr.block_ptr, b)) @ np.abs(r[s:e]))
+    kinds, outs = [], []
+    for variant in (4, 1, 0):
+        h = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_GIVEN, block_fmt=fmt, apply_variant=variant,
+                         fp64_fallback=True)    # keeps the binary64 set that import_inverse overwrites
+        try:
+            h.import_inverse(P.G)
+            kinds.append(h.apply_kernel()[0])
+            z = torch.empty(pr.A.n, dtype=torch.float64, device="cuda")
+            rz = torch.zeros(1, dtype=torch.float64, device="cuda")
+            h.apply(cuda(r), z, set=1, rz=rz)
+            zd = host(z)
+            assert np.array_equal(zd[low], zo[low], equal_nan=True), variant
+            assert np.all(np.abs(zd[~low] - zo[~low]) <= bound[~low]), variant
+            fin = np.isfinite(zo)
+            if fin.all():
+                assert abs(host(rz)[0] - O.dot(r, zo)) <= 1e-13 * np.sum(np.abs(r * zo))
+            outs.append(zd)
+        finally:
+            h.close()
+    assert kinds[:2] == ["mixed", "generic"], kinds
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o, equal_nan=True)
+
+
+def test_mixed_format_register_pcg(B):
+    """PCG with per-block formats through the mixed-format register kernel against the oracle."""
+    pr = PB.make_problem("subcube3d", seed=44, m=24, bs=32)
+    fmt = np.random.default_rng(3).integers(0, 4, len(pr.block_ptr) - 1).astype(np.uint8)
+    P = O.Preconditioner(pr.A, pr.block_ptr, fmt=fmt)
+    b = O.spmv(pr.A, pr.x_star)
+    ref = O.pcg(pr.A, P, b, tol=1e-10, maxit=5000, policy=O.POLICY_FMP)
+    dA = B.DeviceCSR(pr.A)
+    iters = []
+    for variant in (4, 1):
+        h = B.bjac_setup(dA, pr.block_ptr, select=B.SELECT_GIVEN, block_fmt=fmt, apply_variant=variant)
+        x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+        st = h.solve(cuda(b), x, tol=1e-10, maxit=5000)
+        h.close()
+        assert st["converged"] and st["true_relres"] <= 1e-10
+        iters.append(st["iters"])
+    assert ref["converged"]
+    for it in iters:
+        assert abs(it - ref["iters"]) <= max(3, 0.02 * ref["iters"]), (iters, ref["iters"])
