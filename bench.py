@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--profile-kt", action="store_true",
                     help="with --profile-iters: profile fMP BJAC(2, 2) with 32 blocks on the 128^3 Diff3D-Const "
                          "system instead of the headline policy")
+    ap.add_argument("--l2-residency", default="on", choices=["on", "off"],
+                    help="evict_last L2 policy on the PCG vectors in the loop kernels (default on)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only set up the headline policy and run this many eager PCG iterations "
                          "(a short, fixed launch sequence for ncu)")
@@ -70,7 +72,8 @@ def parse():
 def workload_config(args):
     return {"workload": f"diffusion3d-7pt-{args.m}^3-subcube8-logU[1e-3,1e3]-dt1e-2",
             "n": args.m ** 3, "block_size": args.bs, "mixed_format": args.fmt, "tol": TOL,
-            "step": "bjac_setup + pcg_solve + bjac_destroy", "l2": "inputs larger than L2 (no flush)"}
+            "step": "bjac_setup + pcg_solve + bjac_destroy", "l2": "inputs larger than L2 (no flush)",
+            "l2_residency": args.l2_residency}
 
 
 # ------------------------------------------------------------------------------------------
@@ -213,6 +216,7 @@ def run_ours(args, rank, world, dist):
 
     spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
     B.bjac_spmv_kernel(spmv_pin)
+    B.bjac_l2_residency(1 if args.l2_residency == "on" else 0)
     apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3, "mix": 4}[args.apply_kernel]
     layout_pin = {"auto": 0, "csr": 1, "sell": 2, "sell-pf": 3}[args.spmv_layout]
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,

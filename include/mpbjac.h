@@ -274,6 +274,14 @@ int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
  * setting, or INVALID_ARG. Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 
+/* Process-wide L2 residency of the PCG vectors in the solver loop: 1 (default) = the loop's
+ * SpMV, apply and update kernels load and store r, z, p, q and x with an evict_last L2 policy
+ * while the matrix and the block inverses stream with evict-first loads, so the vectors
+ * (5 n doubles) stay in the L2 (129 MB) from one kernel to the next; 0 = plain vector accesses.
+ * Applies to solves started afterwards; results are the same either way. Returns the previous
+ * setting, or INVALID_ARG. Not thread-safe. */
+int bjac_l2_residency(int32_t keep);
+
 /* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined, 4
  * per-warp TMA) and, if the timing ran for it, the four median times in ms (ms[4], HOST,
  * nullable). */

@@ -82,6 +82,7 @@ def lib():
                 "pcg_profile": (C.c_int, [P, P, P, f64, i32, P, C.POINTER(i32)]),
                 "bjac_apply_kernel": (C.c_int, [P, C.POINTER(i32), P]),
                 "bjac_spmv_kernel": (C.c_int, [i32]),
+                "bjac_l2_residency": (C.c_int, [i32]),
                 "bjac_spmv_tuning": (C.c_int, [C.POINTER(bjac_csr), C.POINTER(i32), P]),
                 "bjac_spmv_noalloc": (C.c_int, [C.POINTER(bjac_csr), P, P, P, P]),
                 "bjac_batch_setup": (C.c_int, [i32, P, P, P, C.POINTER(bjac_policy), C.POINTER(P)]),
@@ -148,6 +149,12 @@ def bjac_spmv_noalloc(A: DeviceCSR, x, y, xy, stream=None):
     not overlap on the GPU; at most 16,777,216 rows)."""
     _require_cuda(x, y, xy)
     _check(lib().bjac_spmv_noalloc(C.byref(A.c), _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
+
+
+def bjac_l2_residency(keep: int) -> int:
+    """Evict-last L2 policy for the PCG vectors in the solver loop (1, default) or plain
+    accesses (0); returns the previous setting."""
+    return _check(lib().bjac_l2_residency(int(keep)), allow_positive=True)
 
 
 def bjac_spmv_kernel(variant: int) -> int:

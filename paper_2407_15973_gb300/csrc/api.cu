@@ -814,6 +814,9 @@ static int build_graph(bjac_handle *h, int which) {
     return MPBJAC_OK;
 }
 
+// Process-wide: loop kernels give the PCG vectors an evict_last L2 policy (bjac_l2_residency).
+static int g_l2_keep = 1;
+
 // One full solve with preconditioner selection `which` (0 = policy, 1 = binary64 fallback).
 static int run_solve(bjac_handle *h, int which, const double *b, double *x, double tol, int maxit, double *hist,
                      int *graph_launches) {
@@ -827,6 +830,7 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
     hs.maxit = maxit;
     hs.temporal = which == 0 ? h->pol.temporal : BJAC_TEMPORAL_NONE;
     hs.low_default = (which == 0 && h->have_lo) ? 1 : 0;
+    hs.l2_keep = g_l2_keep;
     MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;
@@ -1024,6 +1028,13 @@ extern "C" int bjac_apply(bjac_handle *h, int32_t set, const double *r, double *
                                 nullptr, h->stream);
 }
 
+extern "C" int bjac_l2_residency(int32_t keep) {
+    if (keep != 0 && keep != 1) return fail(MPBJAC_ERR_INVALID_ARG, "keep must be 0 or 1");
+    const int old = g_l2_keep;
+    g_l2_keep = keep;
+    return old;
+}
+
 extern "C" int bjac_handle_spmv(bjac_handle *h, const double *x, double *y, double *xy) {
     if (!h || !x || !y) return fail(MPBJAC_ERR_INVALID_ARG, "handle, x and y must be non-NULL");
     unsigned int *ticket = &h->d_S->tickets[kTicketSpmv];
@@ -1111,6 +1122,7 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     hs.maxit = maxit;
     hs.temporal = h->pol.temporal;
     hs.low_default = h->have_lo ? 1 : 0;
+    hs.l2_keep = g_l2_keep;
     MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;

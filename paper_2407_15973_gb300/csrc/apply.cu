@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
     const int nb = P.nb;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
     const size_t blk_bytes = (size_t)BS * BS * sizeof(QT);
 
     uint4 qc[RPL][VPR], qn[RPL][VPR];
@@ -343,8 +344,8 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
             const int row = h * 32 + lane;
 #pragma unroll
             for (int v = 0; v < VPR; ++v) qv[h][v] = __ldcs(base + (size_t)row * VPR + v);
-            rv[h] = io.r[(size_t)blk * BS + row];
-            if (MODE == kApplyFused) qq[h] = io.q[(size_t)blk * BS + row];
+            rv[h] = ld_vec(io.r + (size_t)blk * BS + row, pol);
+            if (MODE == kApplyFused) qq[h] = ld_vec(io.q + (size_t)blk * BS + row, pol);
         }
         if (sizeof(QT) == 2) sc = __ldg(P.scale + blk);
     };
@@ -385,10 +386,10 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
         for (int h = 0; h < RPL; ++h) {
             const size_t row = (size_t)blk * BS + h * 32 + lane;
             const double zi = f32_to_f64(acc[h] * sc_c);
-            io.z[row] = zi;
-            if (MODE == kApplyInit) io.p[row] = zi;
+            st_vec(io.z + row, zi, pol);
+            if (MODE == kApplyInit) st_vec(io.p + row, zi, pol);
             if (MODE == kApplyFused) {
-                io.r_out[row] = rv[h];
+                st_vec(io.r_out + row, rv[h], pol);
                 rr = fma(rv[h], rv[h], rr);
             }
             rho = fma(rv[h], zi, rho);
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
     double rho = 0.0, rr = 0.0;
     for (int blk = gw; blk < P.nb; blk += nw) {
         const int f = __ldg(P.fmt + blk);
@@ -481,8 +483,8 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
             for (int v = 0; v < 8; ++v)
                 if (v < vpr) q[v] = __ldcs(base + (size_t)lane * vpr + v);
         }
-        double v = io.r[row];
-        if (MODE == kApplyFused) v = fma(-alpha, io.q[row], v);
+        double v = ld_vec(io.r + row, pol);
+        if (MODE == kApplyFused) v = fma(-alpha, ld_vec(io.q + row, pol), v);
         s_r[warp][lane] = v;
         s_rh[warp][lane] = f64_to_f32_rn(v);
         __syncwarp();
@@ -496,10 +498,10 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
             else acc = mix_row<__half>(q, s_rh[warp]);
             zi = f32_to_f64(acc * sc);
         }
-        io.z[row] = zi;
-        if (MODE == kApplyInit) io.p[row] = zi;
+        st_vec(io.z + row, zi, pol);
+        if (MODE == kApplyInit) st_vec(io.p + row, zi, pol);
         if (MODE == kApplyFused) {
-            io.r_out[row] = v;
+            st_vec(io.r_out + row, v, pol);
             rr = fma(v, v, rr);
         }
         rho = fma(v, zi, rho);

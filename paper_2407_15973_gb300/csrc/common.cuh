@@ -45,6 +45,42 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ----------------------------------------------------------------------------------------
+// L2 residency. The PCG vectors (r, z, p, q, x: n doubles each) are read again by the next
+// kernel of the same iteration, while the matrix and the block inverses are streamed once per
+// iteration (their loads use ld.global.cs, evict-first). With keep set, the loop kernels give
+// their vector loads and stores an evict_last policy so that the streams evict each other
+// rather than the vectors; without it the policy is evict_normal (a plain access).
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t vec_policy(int keep) {
+    uint64_t p;
+    if (keep) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ld_vec(const double *a, uint64_t pol) {
+    double v;
+    asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ldg_vec(const double *a, uint64_t pol) {     // read-only in the kernel
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_vec2(const double2 *a, uint64_t pol) {
+    double2 v;
+    asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_vec(double *a, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_vec2(double2 *a, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // Host: whether launches made by this thread now carry the programmatic attribute (set
 // around the PCG loop body only).
 bool pdl_on();
@@ -88,7 +124,7 @@ struct SolverState {
     int32_t maxit;
     int32_t temporal;      // BJAC_TEMPORAL_*
     int32_t low_default;   // set used when temporal == NONE: 1 low, 0 binary64
-    int32_t pad0;
+    int32_t l2_keep;       // PCG vectors accessed with an evict_last L2 policy (vec_policy)
     // dynamic state
     double bnorm;
     double rho, sigma, alpha, beta, rr, relres, true_relres;

@@ -92,7 +92,7 @@ __global__ void k_sell_fill(int n, int nslices, const int32_t *__restrict__ rowp
 // gathers, then the FMA chain (padding skipped)
 template <int U>
 __device__ __forceinline__ void sell_part(const double *__restrict__ pv, const int32_t *__restrict__ pc,
-                                          const double *__restrict__ x, double &acc) {
+                                          const double *__restrict__ x, uint64_t pol, double &acc) {
     double vv[U], xv[U];
     int cc[U];
 #pragma unroll
@@ -101,7 +101,7 @@ __device__ __forceinline__ void sell_part(const double *__restrict__ pv, const i
         cc[u] = __ldcs(pc + 32 * u);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0;
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? ldg_vec(x + cc[u], pol) : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (cc[u] >= 0) acc = fma(vv[u], xv[u], acc);
@@ -110,10 +110,10 @@ __device__ __forceinline__ void sell_part(const double *__restrict__ pv, const i
 // gathers and FMA chain of U entries already loaded into registers
 template <int U>
 __device__ __forceinline__ void sell_fma(const double (&vv)[8], const int (&cc)[8], const double *__restrict__ x,
-                                         double &acc) {
+                                         uint64_t pol, double &acc) {
     double xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0;
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? ldg_vec(x + cc[u], pol) : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (cc[u] >= 0) acc = fma(vv[u], xv[u], acc);
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
         if (S->state != kRunning) return;
     }
+    const uint64_t pol = vec_policy(KIND == kSpPcg ? S->l2_keep : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
     double acc1 = 0.0, acc2 = 0.0;
@@ -168,31 +169,31 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
         double xr = 0.0, bi = 0.0;
         if (row < n) {
             if (RES) bi = b[row];
-            else if (KIND != kSpY) xr = __ldg(x + row);
+            else if (KIND != kSpY) xr = ldg_vec(x + row, pol);
         }
         const double *pv = val + o0 + lane;
         const int32_t *pc = col + o0 + lane;
         double acc = 0.0;
         int j = 0;
-        for (; j + 8 <= len; j += 8) sell_part<8>(pv + 32 * j, pc + 32 * j, x, acc);
+        for (; j + 8 <= len; j += 8) sell_part<8>(pv + 32 * j, pc + 32 * j, x, pol, acc);
         switch (len - j) {
-            case 1: sell_part<1>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 2: sell_part<2>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 3: sell_part<3>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 4: sell_part<4>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 5: sell_part<5>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, acc); break;
-            case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, acc); break;
+            case 1: sell_part<1>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 2: sell_part<2>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 3: sell_part<3>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 4: sell_part<4>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 5: sell_part<5>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+            case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
             default: break;
         }
         if (row < n) {
             if (RES) {
                 const double ri = bi - acc;
-                y[row] = ri;
+                st_vec(y + row, ri, pol);
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
-                y[row] = acc;
+                st_vec(y + row, acc, pol);
                 if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
         if (S->state != kRunning) return;
     }
+    const uint64_t pol = vec_policy(KIND == kSpPcg ? S->l2_keep : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
     double acc1 = 0.0, acc2 = 0.0;
@@ -250,44 +252,44 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
         double xr = 0.0, bi = 0.0;
         if (row < n) {
             if (RES) bi = b[row];
-            else if (KIND != kSpY) xr = __ldg(x + row);
+            else if (KIND != kSpY) xr = ldg_vec(x + row, pol);
         }
         double acc = 0.0;
         switch (len < 8 ? len : 8) {
-            case 1: sell_fma<1>(cv, cc, x, acc); break;
-            case 2: sell_fma<2>(cv, cc, x, acc); break;
-            case 3: sell_fma<3>(cv, cc, x, acc); break;
-            case 4: sell_fma<4>(cv, cc, x, acc); break;
-            case 5: sell_fma<5>(cv, cc, x, acc); break;
-            case 6: sell_fma<6>(cv, cc, x, acc); break;
-            case 7: sell_fma<7>(cv, cc, x, acc); break;
-            case 8: sell_fma<8>(cv, cc, x, acc); break;
+            case 1: sell_fma<1>(cv, cc, x, pol, acc); break;
+            case 2: sell_fma<2>(cv, cc, x, pol, acc); break;
+            case 3: sell_fma<3>(cv, cc, x, pol, acc); break;
+            case 4: sell_fma<4>(cv, cc, x, pol, acc); break;
+            case 5: sell_fma<5>(cv, cc, x, pol, acc); break;
+            case 6: sell_fma<6>(cv, cc, x, pol, acc); break;
+            case 7: sell_fma<7>(cv, cc, x, pol, acc); break;
+            case 8: sell_fma<8>(cv, cc, x, pol, acc); break;
             default: break;
         }
         if (len > 8) {
             const double *pv = val + o0 + lane;
             const int32_t *pc = col + o0 + lane;
             int j = 8;
-            for (; j + 8 <= len; j += 8) sell_part<8>(pv + 32 * j, pc + 32 * j, x, acc);
+            for (; j + 8 <= len; j += 8) sell_part<8>(pv + 32 * j, pc + 32 * j, x, pol, acc);
             switch (len - j) {
-                case 1: sell_part<1>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 2: sell_part<2>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 3: sell_part<3>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 4: sell_part<4>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 5: sell_part<5>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, acc); break;
-                case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, acc); break;
+                case 1: sell_part<1>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 2: sell_part<2>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 3: sell_part<3>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 4: sell_part<4>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 5: sell_part<5>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 6: sell_part<6>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
+                case 7: sell_part<7>(pv + 32 * j, pc + 32 * j, x, pol, acc); break;
                 default: break;
             }
         }
         if (row < n) {
             if (RES) {
                 const double ri = bi - acc;
-                y[row] = ri;
+                st_vec(y + row, ri, pol);
                 acc1 = fma(ri, ri, acc1);
                 acc2 = fma(bi, bi, acc2);
             } else {
-                y[row] = acc;
+                st_vec(y + row, acc, pol);
                 if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
             }
         }

@@ -21,17 +21,18 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
     __shared__ double red[kWarps];
     if (S->state != kRunning) return;
     const double alpha = S->alpha;
+    const uint64_t pol = vec_policy(S->l2_keep);
     double rr = 0.0;
     const int n2 = n >> 1;
     const double2 *q2 = reinterpret_cast<const double2 *>(q);
     double2 *r2 = reinterpret_cast<double2 *>(r);
 #pragma unroll 2
     for (int i = blockIdx.x * kNT + threadIdx.x; i < n2; i += gridDim.x * kNT) {
-        const double2 qv = q2[i];
-        double2 rv = r2[i];
+        const double2 qv = ld_vec2(q2 + i, pol);
+        double2 rv = ld_vec2(r2 + i, pol);
         rv.x = fma(-alpha, qv.x, rv.x);
         rv.y = fma(-alpha, qv.y, rv.y);
-        r2[i] = rv;
+        st_vec2(r2 + i, rv, pol);
         rr = fma(rv.x, rv.x, rr);
         rr = fma(rv.y, rv.y, rr);
     }
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
     const int run = S->state == kRunning;
     double *__restrict__ x = S->x;
     const double alpha = S->alpha, beta = S->beta;
+    const uint64_t pol = vec_policy(S->l2_keep);
     const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
     if ((xp | run) && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
         const int n2 = n >> 1;
@@ -76,16 +78,16 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
         double2 *x2 = reinterpret_cast<double2 *>(x);
 #pragma unroll 2
         for (int i = gid; i < n2; i += stride) {
-            const double2 pv = p2[i];
+            const double2 pv = ld_vec2(p2 + i, pol);
             if (xp) {
-                double2 xv = x2[i];
+                double2 xv = ld_vec2(x2 + i, pol);
                 xv.x = fma(alpha, pv.x, xv.x);
                 xv.y = fma(alpha, pv.y, xv.y);
-                x2[i] = xv;
+                st_vec2(x2 + i, xv, pol);
             }
             if (run) {
-                const double2 zv = z2[i];
-                p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+                const double2 zv = ld_vec2(z2 + i, pol);
+                st_vec2(p2 + i, make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y)), pol);
             }
         }
         if ((n & 1) && gid == 0) {

@@ -54,6 +54,8 @@ def test_host_side_validation_without_gpu(libpath):
     assert L.bjac_setup(ctypes.byref(csr), None, 1, ctypes.byref(pol), ctypes.byref(out)) == B.ERR_INVALID_ARG
     assert L.pcg_solve(None, None, None, 1e-10, 10, None, None) == B.ERR_INVALID_ARG
     assert L.bjac_mlp_param_count() == 5187 + 24
+    assert L.bjac_l2_residency(2) == B.ERR_INVALID_ARG
+    assert L.bjac_l2_residency(0) == 1 and L.bjac_l2_residency(1) == 0     # default on; restored
 
 
 def _c_layout(struct, fields, tmp_path):

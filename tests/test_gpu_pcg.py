@@ -157,6 +157,29 @@ def test_repeat_solves_identical(B):
     assert np.array_equal(xs[0][1], xs[1][1]) and np.array_equal(xs[0][1], xs[2][1])
 
 
+@pytest.mark.parametrize("select", ["bf16", "rule", "hl"])
+def test_l2_residency_changes_no_bits(B, select):
+    # the evict_last policy on the loop's vector accesses is a cache hint: same iterates
+    pr, b, P = _problem("subcube24_bs32")
+    dA = B.DeviceCSR(pr.A)
+    pol = {"bf16": dict(select=B.SELECT_FIXED, fixed_fmt=B.BF16), "rule": dict(select=B.SELECT_RULE),
+           "hl": dict(select=B.SELECT_FIXED, fixed_fmt=B.FP32, temporal=B.TEMPORAL_HL, adp_tol=1e-4)}[select]
+    h = B.bjac_setup(dA, pr.block_ptr, **pol)
+    out = []
+    try:
+        for keep in (0, 1):
+            old = B.bjac_l2_residency(keep)
+            x = torch.zeros(pr.A.n, dtype=torch.float64, device="cuda")
+            st = h.solve(cuda(b), x)
+            B.bjac_l2_residency(old)
+            out.append((st["iters"], st["low_applies"], host(x)))
+    finally:
+        h.close()
+    assert out[0][:2] == out[1][:2] and np.array_equal(out[0][2], out[1][2])
+    with pytest.raises(B.MpbjacError):
+        B.bjac_l2_residency(2)
+
+
 @pytest.mark.parametrize("temporal", [0, 1])
 def test_eager_loop_matches_graph(B, temporal):
     # the host-driven loop enqueues exactly the kernels of the graph's loop body
