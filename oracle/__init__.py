@@ -64,7 +64,7 @@ def lib():
                 "orc_pack": (None, [i32, P, P, P, P, P, P, P]),
                 "orc_apply": (None, [i32, P, P, P, P, P, P, P, i32]),
                 "orc_apply_fp64": (None, [i32, P, P, P, P, P]),
-                "orc_pcg": (i32, [i32, P, P, P, i32, P, P, P, P, P, P, P, i32, f64, i32,
+                "orc_pcg": (i32, [i32, P, P, P, i32, P, P, P, P, P, P, P, i32, f64, i32, i32,
                                   P, P, f64, i32, P, P, P]),
                 "orc_multiscale": (None, [i32, P, P, P, P]),
                 "orc_diag_boost": (None, [i32, P, P, P, f64]),
@@ -75,7 +75,7 @@ def lib():
                 "orc_mlp_loss_grad": (f64, [i32, P, P, P, P]),
                 "orc_kt_dinv": (i32, [i32, P, P, P, P]),
                 "orc_kt_apply": (i32, [i32, P, P, P, i32, P, i32, i32, i32, P, P]),
-                "orc_pcg_kt": (i32, [i32, P, P, P, i32, P, i32, i32, i32, f64, P, P, f64, i32, P, P, P]),
+                "orc_pcg_kt": (i32, [i32, P, P, P, i32, P, i32, i32, i32, f64, i32, P, P, f64, i32, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(_lib, name)
@@ -209,8 +209,9 @@ class Preconditioner:
 
 
 def pcg(A, P: Preconditioner, b, x0=None, tol=1e-10, maxit=1000, policy=POLICY_UNIFORM,
-        adp_tol=10.0, mode=1):
-    """Oracle PCG. Returns dict(x, iters, converged, status, relres, true_relres, hist, low_used)."""
+        adp_tol=10.0, mode=1, flexible=False):
+    """Oracle PCG. Returns dict(x, iters, converged, status, relres, true_relres, hist, low_used).
+    flexible: the Polak-Ribiere beta of flexible CG instead of rho_new / rho."""
     b = _c(b, np.float64)
     x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     hist = np.full(maxit + 1, np.nan)
@@ -220,7 +221,7 @@ def pcg(A, P: Preconditioner, b, x0=None, tol=1e-10, maxit=1000, policy=POLICY_U
         raise ValueError("policy needs a low-precision set")
     lib().orc_pcg(A.n, _p(A.rowptr), _p(A.colidx), _p(A.val), P.nb, _p(P.block_ptr), _p(P.G), _p(P.goff),
                   _p(P.fmt), _p(getattr(P, "pool", None)), _p(getattr(P, "qoff", None)),
-                  _p(getattr(P, "scale", None)), policy, adp_tol, mode, _p(b), _p(x), tol, maxit,
+                  _p(getattr(P, "scale", None)), policy, adp_tol, mode, int(bool(flexible)), _p(b), _p(x), tol, maxit,
                   _p(hist), _p(low), C.byref(st))
     k = st.iters
     return dict(x=x, iters=k, converged=bool(st.converged), status=st.status, relres=st.relres,
@@ -240,7 +241,8 @@ def kt_apply(A, block_ptr, k, t, r, prec=0):
     return z
 
 
-def pcg_kt(A, block_ptr, b, k=2, t=2, x0=None, tol=1e-10, maxit=1000, policy=POLICY_UNIFORM, adp_tol=10.0):
+def pcg_kt(A, block_ptr, b, k=2, t=2, x0=None, tol=1e-10, maxit=1000, policy=POLICY_UNIFORM, adp_tol=10.0,
+           flexible=False):
     """Oracle PCG with BJAC(k, t); policy as in pcg (the low set is the binary32 one)."""
     b = _c(b, np.float64)
     bp = _c(block_ptr, np.int32)
@@ -249,7 +251,7 @@ def pcg_kt(A, block_ptr, b, k=2, t=2, x0=None, tol=1e-10, maxit=1000, policy=POL
     low = np.zeros(maxit + 1, dtype=np.uint8)
     st = Stats()
     lib().orc_pcg_kt(A.n, _p(A.rowptr), _p(A.colidx), _p(A.val), len(bp) - 1, _p(bp), k, t, policy, adp_tol,
-                     _p(b), _p(x), tol, maxit, _p(hist), _p(low), C.byref(st))
+                     int(bool(flexible)), _p(b), _p(x), tol, maxit, _p(hist), _p(low), C.byref(st))
     it = st.iters
     return dict(x=x, iters=it, converged=bool(st.converged), status=st.status, relres=st.relres,
                 true_relres=st.true_relres, restarts=st.restarts, hist=hist[:it + 1], low_used=low[:it + 1],

@@ -20,7 +20,8 @@
  *                          binary32 / binary16 and bfloat16 bit layouts
  *   packing / apply     -- M^-1_bjac(p_l) applied to r-hat (Algorithm 3.1)
  *   PCG + policies      -- fMP (Algorithm 3.1), aMP(hl) (Algorithm 3.2), aMP(lh)
- *                          (Algorithm 3.3), convergence test of Section 4.2
+ *                          (Algorithm 3.3), convergence test of Section 4.2; optionally the
+ *                          flexible-CG (Polak-Ribiere) direction coefficient
  *   multiscale / features / selection rule / MLP -- per-block quantities (Eq. 4-5,
  *                          Section 4.5.2) and the block-format selectors
  *   BJAC(k, t)          -- the inexact block Jacobi of Eq. 3-2 / 3-3 (inner Jacobi sweeps
@@ -351,6 +352,19 @@ void orc_apply_fp64(int32_t nb, const int32_t *block_ptr, const double *G, const
 /*   policy 3  aMP(lh) (Algorithm 3.3): the low set while relres >= adp_tol, else G        */
 /* After the recurrence meets tol, the true residual b - A x is formed; if it does not     */
 /* meet tol, PCG restarts from it (r = b - A x, p = M^-1 r) while iterations remain.       */
+/* Flexible (Polak-Ribiere) direction coefficient of flexible CG (G. H. Golub and Q. Ye, SIAM
+ * J. Sci. Comput. 21, 1999; Y. Notay, SIAM J. Sci. Comput. 22, 2000):
+ *     beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k),
+ * in place of rho_{k+1} / rho_k. It keeps consecutive search directions A-conjugate when the
+ * preconditioner changes between iterations (aMP's switch of Algorithms 3.2 / 3.3) or is not
+ * exactly linear (a low-precision apply), and equals rho_{k+1} / rho_k for a fixed symmetric
+ * preconditioner in exact arithmetic (z_{k+1}^T r_k = 0 there). */
+static double flexible_beta(int32_t n, const double *z, const double *r, const double *r_prev, double rho) {
+    double s = 0.0;
+    for (int32_t i = 0; i < n; ++i) s += z[i] * (r[i] - r_prev[i]);
+    return s / rho;
+}
+
 /* ====================================================================================== */
 typedef struct {
     int32_t iters, converged, status, restarts, low_applies, high_applies;
@@ -394,7 +408,7 @@ static void precondition(const precond *P, double relres, const double *r, doubl
 int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                 int32_t nb, const int32_t *block_ptr, const double *G, const int64_t *goff,
                 const uint8_t *fmt, const uint8_t *pool, const int64_t *qoff, const float *scale,
-                int32_t policy, double adp_tol, int32_t mode,
+                int32_t policy, double adp_tol, int32_t mode, int32_t flexible,
                 const double *b, double *x, double tol, int32_t maxit,
                 double *hist, uint8_t *low_used, orc_stats *st) {
     precond P = {nb, block_ptr, G, goff, fmt, pool, qoff, scale, policy, adp_tol, mode};
@@ -403,6 +417,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
     double *z = malloc(sizeof(double) * (size_t)n);
     double *p = malloc(sizeof(double) * (size_t)n);
     double *q = malloc(sizeof(double) * (size_t)n);
+    double *rp = malloc(sizeof(double) * (size_t)n);     /* r_k, kept for the flexible beta */
     double bnorm = sqrt(orc_dot(n, b, b));
     int32_t k = 0, status = ORC_OK;
     if (bnorm == 0.0) {
@@ -426,6 +441,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
             if (!(sigma > 0.0) || !isfinite(sigma)) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / sigma;
             for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            for (int32_t i = 0; i < n; ++i) rp[i] = r[i];
             for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
             ++k;
             relres = sqrt(orc_dot(n, r, r)) / bnorm;
@@ -436,7 +452,8 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
             precondition(&P, relres, r, z, st, low_used ? &low_used[k] : NULL);
             double rho_new = orc_dot(n, r, z);
             if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = ORC_BREAKDOWN; break; }
-            double beta = rho_new / rho;
+            double beta = flexible ? flexible_beta(n, z, r, rp, rho) : rho_new / rho;
+            if (!isfinite(beta)) { status = ORC_BREAKDOWN; break; }
             for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
             rho = rho_new;
         }
@@ -455,7 +472,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
 done:
     st->iters = k;
     st->status = status;
-    free(r); free(z); free(p); free(q);
+    free(r); free(z); free(p); free(q); free(rp);
     return status;
 }
 
@@ -828,8 +845,8 @@ int32_t orc_kt_apply(int32_t n, const int32_t *rowptr, const int32_t *colidx, co
 /* PCG as orc_pcg with M-hat^-1 of BJAC(k, t): policy 0 binary64, 1 fMP (binary32), 2 hl, 3 lh */
 int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
                    const int32_t *block_ptr, int32_t kk, int32_t tt, int32_t policy, double adp_tol,
-                   const double *b, double *x, double tol, int32_t maxit, double *hist, uint8_t *low_used,
-                   orc_stats *st) {
+                   int32_t flexible, const double *b, double *x, double tol, int32_t maxit, double *hist,
+                   uint8_t *low_used, orc_stats *st) {
     memset(st, 0, sizeof(*st));
     kt_state K;
     if (kt_init(&K, n, rowptr, colidx, val, nb, block_ptr, kk, tt)) {
@@ -842,6 +859,7 @@ int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
     double *z = malloc(sizeof(double) * (size_t)n);
     double *p = malloc(sizeof(double) * (size_t)n);
     double *q = malloc(sizeof(double) * (size_t)n);
+    double *rp = malloc(sizeof(double) * (size_t)n);
     double bnorm = sqrt(orc_dot(n, b, b));
     int32_t k = 0, status = ORC_OK;
 #define KT_PRECONDITION(rel, flag)                                  \
@@ -872,6 +890,7 @@ int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
             if (!(sigma > 0.0) || !isfinite(sigma)) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / sigma;
             for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            for (int32_t i = 0; i < n; ++i) rp[i] = r[i];
             for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
             ++k;
             relres = sqrt(orc_dot(n, r, r)) / bnorm;
@@ -882,7 +901,8 @@ int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
             KT_PRECONDITION(relres, low_used ? &low_used[k] : NULL);
             double rho_new = orc_dot(n, r, z);
             if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = ORC_BREAKDOWN; break; }
-            double beta = rho_new / rho;
+            double beta = flexible ? flexible_beta(n, z, r, rp, rho) : rho_new / rho;
+            if (!isfinite(beta)) { status = ORC_BREAKDOWN; break; }
             for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
             rho = rho_new;
         }
@@ -901,7 +921,7 @@ int32_t orc_pcg_kt(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
 done:
     st->iters = k;
     st->status = status;
-    free(r); free(z); free(p); free(q);
+    free(r); free(z); free(p); free(q); free(rp);
     kt_free(&K);
     return status;
 }

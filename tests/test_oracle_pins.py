@@ -661,3 +661,69 @@ def test_diag_boost_input_matches_oracle_definition(oracle):
         got = PB.diag_boost(pr.A, pd)
         ref = oracle.diag_boost(pr.A, pd)
         assert np.allclose(got.val, ref.val, rtol=1e-15, atol=0)
+
+
+def _step_conjugacy(oracle, pr, solve, steps=12):
+    """|d_{k+1}^T A d_k| / (||d_{k+1}||_A ||d_k||_A) for the steps d_k = x_{k+1} - x_k (= alpha_k p_k)
+    of the first iterations, each x_k from a separate run stopped after k iterations."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((pr.A.val, pr.A.colidx, pr.A.rowptr), shape=(pr.A.n, pr.A.n))
+    xs = [np.zeros(pr.A.n)] + [solve(k)["x"] for k in range(1, steps + 1)]
+    d = [xs[k + 1] - xs[k] for k in range(steps)]
+    return np.array([abs(d[k + 1] @ (A @ d[k])) / np.sqrt((d[k + 1] @ (A @ d[k + 1])) * (d[k] @ (A @ d[k])))
+                     for k in range(steps - 1)])
+
+
+@pytest.mark.parametrize("fmt", [2, 3])
+@pytest.mark.parametrize("policy,adp", [(2, 1e-2), (3, 1e-2), (1, 1.0)])
+def test_flexible_pcg_keeps_consecutive_directions_conjugate(oracle, fmt, policy, adp):
+    # Flexible CG (Golub-Ye 1999, Notay 2000): the Polak-Ribiere beta makes p_{k+1} A-conjugate
+    # to p_k whatever the preconditioner does between iterations; the Fletcher-Reeves beta of
+    # standard PCG loses that at aMP's precision switch and under a low-precision apply.
+    pr = PB.make_problem("voronoi3d", seed=4, m=12)
+    P = oracle.Preconditioner(pr.A, pr.block_ptr, fmt=fmt)
+    b = oracle.spmv(pr.A, pr.x_star)
+
+    def run(flexible):
+        return lambda k: oracle.pcg(pr.A, P, b, tol=1e-14, maxit=k, policy=policy, adp_tol=adp,
+                                    flexible=flexible)
+    flex = _step_conjugacy(oracle, pr, run(True))
+    std = _step_conjugacy(oracle, pr, run(False))
+    low = oracle.pcg(pr.A, P, b, tol=1e-14, maxit=12, policy=policy, adp_tol=adp)["low_used"]
+    if policy != 1:
+        assert 0 < low[:12].sum() < 12          # the switch happens inside the window
+    assert flex.max() < 1e-12, flex
+    assert std.max() > 1e3 * flex.max(), (std, flex)
+
+
+@pytest.mark.parametrize("name,kw", [("voronoi3d", dict(seed=4, m=12)), ("poisson2d", dict(bs=8))])
+def test_flexible_pcg_equals_standard_for_a_fixed_preconditioner(oracle, name, kw):
+    # binary64 blocks: a fixed SPD preconditioner, so z_{k+1}^T r_k = 0 and both betas agree
+    pr = PB.make_problem(name, **kw)
+    P = oracle.Preconditioner(pr.A, pr.block_ptr)
+    b = oracle.spmv(pr.A, pr.x_star)
+    std = oracle.pcg(pr.A, P, b, maxit=3000)
+    flex = oracle.pcg(pr.A, P, b, maxit=3000, flexible=True)
+    assert std["converged"] and flex["converged"]
+    assert abs(std["iters"] - flex["iters"]) <= 1
+    k = min(std["iters"], flex["iters"], 30)
+    assert np.allclose(std["hist"][:k], flex["hist"][:k], rtol=1e-8)
+    assert np.linalg.norm(std["x"] - flex["x"]) <= 1e-9 * np.linalg.norm(pr.x_star)
+    # and for BJAC(k, t), whose M-hat^-1 is fixed and symmetric in binary64
+    bp = np.linspace(0, pr.A.n, 5).astype(np.int32)
+    s2 = oracle.pcg_kt(pr.A, bp, b, maxit=3000)
+    f2 = oracle.pcg_kt(pr.A, bp, b, maxit=3000, flexible=True)
+    if s2["converged"]:
+        assert f2["converged"] and abs(s2["iters"] - f2["iters"]) <= 1
+
+
+def test_flexible_pcg_kt_keeps_consecutive_directions_conjugate(oracle):
+    # the same property with BJAC(2, 2) applied in binary32 (Algorithm 3.1 with Eq. 3-2 / 3-3)
+    pr = PB.make_problem("voronoi3d", seed=4, m=12)
+    bp = np.linspace(0, pr.A.n, 9).astype(np.int32)
+    b = oracle.spmv(pr.A, pr.x_star)
+    flex = _step_conjugacy(oracle, pr, lambda k: oracle.pcg_kt(pr.A, bp, b, tol=1e-14, maxit=k,
+                                                               policy=oracle.POLICY_HL, adp_tol=1e-2, flexible=True))
+    std = _step_conjugacy(oracle, pr, lambda k: oracle.pcg_kt(pr.A, bp, b, tol=1e-14, maxit=k,
+                                                              policy=oracle.POLICY_HL, adp_tol=1e-2))
+    assert flex.max() < 1e-12 and std.max() > 1e3 * flex.max(), (std, flex)
