@@ -256,6 +256,9 @@ def run_ours(args, rank, world, dist):
                                       adp_tol=10.0)
         table["amp-lh1e-5-bf16"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"], temporal=B.TEMPORAL_LH,
                                         adp_tol=1e-5)
+        table["fmp-bf16-flexible"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"], flexible=True)
+        table["amp-hl10-bf16-flexible"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"],
+                                               temporal=B.TEMPORAL_HL, adp_tol=10.0, flexible=True)
         table["rule"] = dict(select=B.SELECT_RULE)
         from paper_2407_15973_gb300 import selector as SEL
         if os.path.exists(SEL.DEFAULT_WEIGHTS):

@@ -105,6 +105,13 @@ typedef struct bjac_policy {
                                Every layout sums each row in CSR order: same result bits.  */
     int32_t kt_outer;       /* BJAC_SELECT_KT: outer sweeps k (0: 2)                        */
     int32_t kt_inner;       /* BJAC_SELECT_KT: inner Jacobi sweeps t (0: 2)                 */
+    int32_t flexible;       /* 0: beta = rho_{k+1} / rho_k (standard PCG, as in the paper);
+                               1: flexible CG (Golub-Ye 1999, Notay 2000), the Polak-Ribiere
+                               beta = z_{k+1}^T (r_{k+1} - r_k) / rho_k, which keeps p_{k+1}
+                               A-conjugate to p_k when the preconditioner changes between
+                               iterations (aMP's switch) or is not exactly linear (a low-
+                               precision apply); one more kernel per iteration. Not used by
+                               the batched solver.                                          */
     void *stream;           /* cudaStream_t for setup and solves (NULL = default stream)   */
 } bjac_policy;
 

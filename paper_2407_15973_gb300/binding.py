@@ -42,7 +42,7 @@ class bjac_policy(C.Structure):
                 ("safety_theta", C.c_double), ("mlp_params", C.c_void_p), ("block_fmt", C.c_void_p),
                 ("apply_variant", C.c_int32),
                 ("graph_mode", C.c_int32), ("spmv_format", C.c_int32), ("kt_outer", C.c_int32),
-                ("kt_inner", C.c_int32), ("stream", C.c_void_p)]
+                ("kt_inner", C.c_int32), ("flexible", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pcg_stats(C.Structure):
@@ -178,7 +178,7 @@ def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
 
 def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp_tol=10.0, theta=0.1,
                 safety_theta=0.5, fp64_fallback=False, mlp_params=None, block_fmt=None, apply_variant=0,
-                graph_mode=0, spmv_format=0, kt_outer=2, kt_inner=2, stream=None):
+                graph_mode=0, spmv_format=0, kt_outer=2, kt_inner=2, flexible=False, stream=None):
     p = bjac_policy()
     p.select, p.fixed_fmt, p.temporal = select, fixed_fmt, temporal
     p.fp64_fallback = int(bool(fp64_fallback))
@@ -187,6 +187,7 @@ def make_policy(select=SELECT_FIXED, fixed_fmt=FP32, temporal=TEMPORAL_NONE, adp
     p.graph_mode = graph_mode
     p.spmv_format = spmv_format
     p.kt_outer, p.kt_inner = kt_outer, kt_inner
+    p.flexible = int(bool(flexible))
     p._mlp_keep = None
     if mlp_params is not None:
         arr = np.ascontiguousarray(mlp_params, dtype=np.float32)

@@ -425,6 +425,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     if (P.temporal != BJAC_TEMPORAL_NONE && P.select == BJAC_SELECT_UNIFORM)
         return fail(MPBJAC_ERR_INVALID_ARG, "aMP switching needs a low-precision set");
     if (P.spmv_format < 0 || P.spmv_format > 3) return fail(MPBJAC_ERR_INVALID_ARG, "spmv_format must be 0..3");
+    if (P.flexible != 0 && P.flexible != 1) return fail(MPBJAC_ERR_INVALID_ARG, "flexible must be 0 or 1");
 
     bjac_handle *h = new bjac_handle();
     h->A = *A;
@@ -766,6 +767,10 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         else rc = launch_apply_generic(kApplyFused, use_low ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                        h->d_S, cs);
         if (rc) return rc;
+        *launches += 1;
+    }
+    if (h->pol.flexible) {
+        MPB_TRY_RC(launch_flex_beta(h->n, h->d_q, h->d_z, h->d_part, h->d_S, cs));
         *launches += 1;
     }
     if (ev) MPB_CUDA(cudaEventRecord(ev[3], cs));

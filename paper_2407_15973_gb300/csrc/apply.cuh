@@ -53,9 +53,11 @@ __device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyI
         if (rel <= S->tol) { S->state = kConverged; return; }
         if (S->iter >= S->maxit) { S->state = kMaxit; return; }
     }
-    // kApplyTemporal and kApplyFused (still running): beta = rho_new / rho_old
+    // kApplyTemporal and kApplyFused (still running): beta = rho_new / rho_old (the flexible
+    // variant replaces beta in a kernel of its own and reads rho_old from rho_prev)
     if (!finite_pos(rho)) { S->state = kBreakdown; return; }
     S->beta = rho / S->rho;
+    S->rho_prev = S->rho;
     S->rho = rho;
 }
 

@@ -128,13 +128,14 @@ struct SolverState {
     // dynamic state
     double bnorm;
     double rho, sigma, alpha, beta, rr, relres, true_relres;
+    double rho_prev;       // rho of the previous application (the flexible beta's denominator)
     int32_t iter, state, use_low, x_pending;
     int32_t low_applies, high_applies, restarts, pad1;
     unsigned int tickets[8];
 };
 
 enum Ticket { kTicketSpmv = 0, kTicketUpdR = 1, kTicketApply = 2, kTicketUpdXP = 3, kTicketRes = 4,
-              kTicketInit = 5 };
+              kTicketInit = 5, kTicketFlex = 6 };
 
 __device__ __forceinline__ int choose_low(const SolverState *S, double relres) {
     if (S->temporal == BJAC_TEMPORAL_HL) return !(relres >= S->adp_tol);   // Algorithm 3.2

@@ -105,6 +105,43 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, run ? 1u : 0u);
 }
 
+// Flexible (Polak-Ribiere) direction coefficient of flexible CG (Golub and Ye 1999, Notay 2000):
+// beta_k = z_{k+1}^T (r_{k+1} - r_k) / rho_k. The loop has overwritten r_k, so the numerator is
+// taken as -alpha_k (q_k . z_{k+1}), the same quantity by r_{k+1} = r_k - alpha_k q_k. Runs after
+// the preconditioner application of a still-running iteration and replaces its beta.
+__global__ void __launch_bounds__(kNT) k_flex_beta(int n, const double *__restrict__ q,
+                                                   const double *__restrict__ z, double *part, SolverState *S) {
+    pdl_enter();
+    __shared__ double red[kWarps];
+    if (S->state != kRunning) return;
+    const uint64_t pol = vec_policy(S->l2_keep);
+    double s = 0.0;
+    const int n2 = n >> 1;
+    const double2 *q2 = reinterpret_cast<const double2 *>(q);
+    const double2 *z2 = reinterpret_cast<const double2 *>(z);
+#pragma unroll 2
+    for (int i = blockIdx.x * kNT + threadIdx.x; i < n2; i += gridDim.x * kNT) {
+        const double2 qv = ld_vec2(q2 + i, pol);
+        const double2 zv = ld_vec2(z2 + i, pol);
+        s = fma(qv.x, zv.x, s);
+        s = fma(qv.y, zv.y, s);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s = fma(q[n - 1], z[n - 1], s);
+    const double bsum = block_sum<kNT>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+    if (!last_cta(&S->tickets[kTicketFlex])) return;
+    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
+    if (threadIdx.x != 0) return;
+    const double beta = -S->alpha * t / S->rho_prev;
+    if (!(fabs(beta) < 1.0e308)) S->state = kBreakdown;
+    else S->beta = beta;
+}
+
+int launch_flex_beta(int n, const double *q, const double *z, double *part, SolverState *S, cudaStream_t st) {
+    MPB_CUDA(launch_kernel(k_flex_beta, vec_grid2(n), kNT, 0, st, n, q, z, part, S));
+    return MPBJAC_OK;
+}
+
 int launch_update_r(int n, const double *q, double *r, double *part, SolverState *S, cudaStream_t st) {
     MPB_CUDA(launch_kernel(k_update_r, vec_grid2(n), kNT, 0, st, n, q, r, part, S));
     return MPBJAC_OK;

@@ -13,4 +13,8 @@ int launch_update_r(int n, const double *q, double *r, double *part, SolverState
 int launch_update_xp(int n, const double *z, double *p, SolverState *S, cudaGraphConditionalHandle cond,
                      int use_cond, cudaStream_t st);
 
+// Flexible CG: beta = z_{k+1}^T (r_{k+1} - r_k) / rho_k, evaluated as -alpha_k q_k^T z_{k+1} / rho_k
+// (the residual recurrence r_{k+1} = r_k - alpha_k q_k), replacing the beta the apply set.
+int launch_flex_beta(int n, const double *q, const double *z, double *part, SolverState *S, cudaStream_t st);
+
 }  // namespace mpbjac

@@ -94,3 +94,7 @@ def test_invalid_spmv_format_rejected_on_host(libpath):
     rc = L.bjac_setup(ctypes.byref(csr), bp.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(pol), ctypes.byref(out))
     assert rc == B.ERR_INVALID_ARG
     assert b"spmv_format" in L.bjac_last_error()
+    pol.spmv_format, pol.flexible = 0, 2
+    rc = L.bjac_setup(ctypes.byref(csr), bp.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(pol), ctypes.byref(out))
+    assert rc == B.ERR_INVALID_ARG
+    assert b"flexible" in L.bjac_last_error()
