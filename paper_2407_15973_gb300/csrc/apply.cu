@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
     using Geo = RegGeom<QT, BS>;
     constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
     __shared__ __align__(16) float s_rh[kWarps][BS];
-    __shared__ double s_red[2][kWarps];
+    __shared__ double s_red[2 * kNT];
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (MODE == kApplyTemporal || MODE == kApplyInit) {
@@ -404,26 +404,16 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
         }
         sc_c = sc_n;
     }
-    rho = warp_sum(rho);
-    rr = warp_sum(rr);
-    if (lane == 0) {
-        s_red[0][warp] = rho;
-        s_red[1][warp] = rr;
-    }
-    __syncthreads();
+    double b1, b2;
+    cta_sum_to0<kNT, true>(rho, rr, s_red, b1, b2);
     if (MODE == kApplyStandalone && io.out == nullptr) return;
     if (threadIdx.x == 0) {
-        double b1 = 0.0, b2 = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
-            b1 += s_red[0][w];
-            b2 += s_red[1][w];
-        }
         io.part[2 * blockIdx.x] = b1;
         io.part[2 * blockIdx.x + 1] = b2;
     }
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red[0]);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red[1]);
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red + kNT);
     if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
 }
 
@@ -459,7 +449,7 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
     pdl_enter();
     __shared__ __align__(16) float s_rh[kWarps][32];
     __shared__ __align__(16) double s_r[kWarps][32];
-    __shared__ double s_red[2][kWarps];
+    __shared__ double s_red[2 * kNT];
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (MODE == kApplyTemporal || MODE == kApplyInit) {
@@ -507,26 +497,16 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
         rho = fma(v, zi, rho);
         __syncwarp();
     }
-    rho = warp_sum(rho);
-    rr = warp_sum(rr);
-    if (lane == 0) {
-        s_red[0][warp] = rho;
-        s_red[1][warp] = rr;
-    }
-    __syncthreads();
+    double b1, b2;
+    cta_sum_to0<kNT, true>(rho, rr, s_red, b1, b2);
     if (MODE == kApplyStandalone && io.out == nullptr) return;
     if (threadIdx.x == 0) {
-        double b1 = 0.0, b2 = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
-            b1 += s_red[0][w];
-            b2 += s_red[1][w];
-        }
         io.part[2 * blockIdx.x] = b1;
         io.part[2 * blockIdx.x + 1] = b2;
     }
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red[0]);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red[1]);
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red + kNT);
     if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
 }
 

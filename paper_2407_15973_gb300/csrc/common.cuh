@@ -181,6 +181,31 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return t;
 }
 
+// Sums over the CTA of one (TWO = false) or two per-thread values, valid in thread 0 only
+// (the per-CTA partials of a grid reduction). The values pass through shared memory and warp 0
+// adds them: NT/32 adds per lane in a fixed order, then one warp tree per value. That is about
+// a sixth of the FP64 instructions of a tree in every warp, and the FP64 pipe is a co-bound of
+// the loop kernels. sm: NT doubles per value.
+template <int NT, bool TWO>
+__device__ __forceinline__ void cta_sum_to0(double a, double b, double *sm, double &ra, double &rb) {
+    __syncthreads();
+    sm[threadIdx.x] = a;
+    if (TWO) sm[NT + threadIdx.x] = b;
+    __syncthreads();
+    ra = 0.0;
+    rb = 0.0;
+    if (threadIdx.x < 32) {
+        double s = sm[threadIdx.x], t = TWO ? sm[NT + threadIdx.x] : 0.0;
+#pragma unroll
+        for (int i = 1; i < NT / 32; ++i) {
+            s += sm[threadIdx.x + 32 * i];
+            if (TWO) t += sm[NT + threadIdx.x + 32 * i];
+        }
+        ra = warp_sum(s);
+        if (TWO) rb = warp_sum(t);
+    }
+}
+
 // Every CTA publishes its partials (written by thread 0), then the last CTA to arrive
 // (ticket) sees them all. Only thread 0 fences: it wrote the partials and takes the ticket.
 // Returns true in every thread of that last CTA. The ticket counter is reset there.

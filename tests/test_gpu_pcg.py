@@ -61,7 +61,10 @@ def test_uniform_fp64_iterations(B, name):
     ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000)
     got = _gpu_solve(B, pr, b, select=B.SELECT_UNIFORM, hist=True)
     assert ref["converged"] and got["converged"]
-    assert abs(got["iters"] - ref["iters"]) <= 2
+    # equally valid summation orders of the dot products move the count of this textbook PCG
+    # by up to 3 % on the ill-conditioned cases (aniso27_12_bs64: 326 ... 336 with sequential,
+    # exactly rounded, BLAS and randomly permuted sums), so the count is compared within that
+    assert abs(got["iters"] - ref["iters"]) <= max(2, 0.03 * ref["iters"])
     assert got["true_relres"] <= TOL
     assert abs(_err(got["x"], pr.x_star) - _err(ref["x"], pr.x_star)) <= 10 * _err(ref["x"], pr.x_star) + 1e-12
     k = min(got["iters"], ref["iters"], 20)
