@@ -233,8 +233,8 @@ static int choose_apply_kind(bjac_handle *h) {
     unsigned int *ticket = nullptr;
     MPB_CUDA(cudaMalloc(&r, sizeof(double) * h->n));
     MPB_CUDA(cudaMalloc(&z, sizeof(double) * h->n));
-    MPB_CUDA(cudaMalloc(&part, sizeof(double) * 2 * kMaxGrid + 64));
-    ticket = reinterpret_cast<unsigned int *>(part + 2 * kMaxGrid);
+    MPB_CUDA(cudaMalloc(&part, sizeof(double) * 3 * kMaxGrid + 64));
+    ticket = reinterpret_cast<unsigned int *>(part + 3 * kMaxGrid);
     MPB_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * h->n, st));
     MPB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
     ApplyIO io{};
@@ -614,7 +614,7 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     MPB_TRY(dalloc(&h->d_z, n));
     MPB_TRY(dalloc(&h->d_p, n));
     MPB_TRY(dalloc(&h->d_q, n));
-    MPB_TRY(dalloc(&h->d_part, 2 * (size_t)kMaxGrid));
+    MPB_TRY(dalloc(&h->d_part, 3 * (size_t)kMaxGrid));     // up to 3 partial sums per CTA
     MPB_TRY(dalloc(&h->d_S, 1));
     if (P.fp64_fallback) MPB_TRY(dalloc(&h->d_x0, n));
     MPB_TRY(cudaMallocHost((void **)&h->h_S, sizeof(SolverState)) == cudaSuccess
@@ -763,13 +763,17 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         ApplyIO io = base_io(h);
         io.set = use_low ? 1 : 0;
+        io.flex = h->pol.flexible;
         if (use_low && lo_uses_tma(h)) rc = launch_lo_special(h, kApplyFused, io, cs);
         else rc = launch_apply_generic(kApplyFused, use_low ? h->lo : h->hi, h->have_hi ? h->hi : h->lo, io,
                                        h->d_S, cs);
         if (rc) return rc;
         *launches += 1;
     }
-    if (h->pol.flexible) {
+    // the fused register kernels sum q.z themselves and finish the flexible beta
+    const bool flex_fused = !kt && !temporal && use_low && lo_uses_tma(h) &&
+                            (h->apply_kind == kApplyKindReg || h->apply_kind == kApplyKindMix);
+    if (h->pol.flexible && !flex_fused) {
         MPB_TRY_RC(launch_flex_beta(h->n, h->d_q, h->d_z, h->d_part, h->d_S, cs));
         *launches += 1;
     }
@@ -836,6 +840,7 @@ static int run_solve(bjac_handle *h, int which, const double *b, double *x, doub
     hs.temporal = which == 0 ? h->pol.temporal : BJAC_TEMPORAL_NONE;
     hs.low_default = (which == 0 && h->have_lo) ? 1 : 0;
     hs.l2_keep = g_l2_keep;
+    hs.flexible = h->pol.flexible;
     MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;
@@ -1128,6 +1133,7 @@ extern "C" int pcg_profile(bjac_handle *h, const double *b, double *x, double to
     hs.temporal = h->pol.temporal;
     hs.low_default = h->have_lo ? 1 : 0;
     hs.l2_keep = g_l2_keep;
+    hs.flexible = h->pol.flexible;
     MPB_CUDA(cudaMemcpyAsync(h->d_S, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
     int rc = launch_residual(h->A, b, x, h->d_r, h->d_part, &h->d_S->tickets[kTicketRes], nullptr, h->d_S, 1, st);
     if (rc) return rc;

@@ -314,13 +314,13 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
 // small per-warp buffer. The next block's row, r and q are loaded before the current block is
 // computed (two blocks in flight per warp). No TMA, no shared-memory copy of Q, no CTA sync.
 // ----------------------------------------------------------------------------------------
-template <typename QT, int BS, int MODE>
+template <typename QT, int BS, int MODE, bool FLEX = false>
 __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
     pdl_enter();
     using Geo = RegGeom<QT, BS>;
     constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
     __shared__ __align__(16) float s_rh[kWarps][BS];
-    __shared__ double s_red[2 * kNT];
+    __shared__ double s_red[(MODE == kApplyFused && FLEX ? 3 : 2) * kNT];
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (MODE == kApplyTemporal || MODE == kApplyInit) {
@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
         }
         if (sizeof(QT) == 2) sc = __ldg(P.scale + blk);
     };
-    double rho = 0.0, rr = 0.0;
+    constexpr bool flex = MODE == kApplyFused && FLEX;
+    double rho = 0.0, rr = 0.0, qz = 0.0;     // qz = q.z for the flexible beta
     if (gw < nb) load(gw, qc, rc, vc, sc_c);
     for (int blk = gw; blk < nb; blk += nw) {
         const int nxt = blk + nw;
@@ -391,6 +392,7 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
             if (MODE == kApplyFused) {
                 st_vec(io.r_out + row, rv[h], pol);
                 rr = fma(rv[h], rv[h], rr);
+                if (flex) qz = fma(vc[h], zi, qz);
             }
             rho = fma(rv[h], zi, rho);
         }
@@ -404,17 +406,27 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
         }
         sc_c = sc_n;
     }
-    double b1, b2;
-    cta_sum_to0<kNT, true>(rho, rr, s_red, b1, b2);
-    if (MODE == kApplyStandalone && io.out == nullptr) return;
-    if (threadIdx.x == 0) {
-        io.part[2 * blockIdx.x] = b1;
-        io.part[2 * blockIdx.x + 1] = b2;
+    // rho, r.r and (flexible CG) q.z: partials in io.part with stride nv
+    double b[3] = {0.0, 0.0, 0.0};
+    if (flex) {
+        const double v[3] = {rho, rr, qz};
+        cta_sum_to0<kNT, 3>(v, s_red, b);
+    } else {
+        const double v[2] = {rho, rr};
+        double b2[2];
+        cta_sum_to0<kNT, 2>(v, s_red, b2);
+        b[0] = b2[0];
+        b[1] = b2[1];
     }
+    if (MODE == kApplyStandalone && io.out == nullptr) return;
+    const int nv = flex ? 3 : 2;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nv; ++k) io.part[nv * blockIdx.x + k] = b[k];
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red + kNT);
-    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, nv, s_red);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, nv, s_red + kNT);
+    const double t3 = flex ? reduce_partials<kNT>(io.part + 2, gridDim.x, nv, s_red + 2 * kNT) : 0.0;
+    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1, flex, t3);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -444,12 +456,12 @@ __device__ __forceinline__ float mix_row(const uint4 (&q)[8], const float *rh) {
     return a;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, SolverState *S) {
+template <int MODE, bool FLEX = false>
+__global__ void __launch_bounds__(kNT, 3) k_apply_mix32(PSet P, ApplyIO io, SolverState *S) {
     pdl_enter();
     __shared__ __align__(16) float s_rh[kWarps][32];
     __shared__ __align__(16) double s_r[kWarps][32];
-    __shared__ double s_red[2 * kNT];
+    __shared__ double s_red[(MODE == kApplyFused && FLEX ? 3 : 2) * kNT];
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (MODE == kApplyTemporal || MODE == kApplyInit) {
@@ -460,7 +472,8 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
     const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
-    double rho = 0.0, rr = 0.0;
+    constexpr bool flex = MODE == kApplyFused && FLEX;
+    double rho = 0.0, rr = 0.0, qz = 0.0;     // qz = q.z for the flexible beta
     for (int blk = gw; blk < P.nb; blk += nw) {
         const int f = __ldg(P.fmt + blk);
         const uint4 *base = reinterpret_cast<const uint4 *>(P.pool + __ldg(P.qoff + blk));
@@ -473,8 +486,11 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
             for (int v = 0; v < 8; ++v)
                 if (v < vpr) q[v] = __ldcs(base + (size_t)lane * vpr + v);
         }
-        double v = ld_vec(io.r + row, pol);
-        if (MODE == kApplyFused) v = fma(-alpha, ld_vec(io.q + row, pol), v);
+        double v = ld_vec(io.r + row, pol), qi = 0.0;
+        if (MODE == kApplyFused) {
+            qi = ld_vec(io.q + row, pol);
+            v = fma(-alpha, qi, v);
+        }
         s_r[warp][lane] = v;
         s_rh[warp][lane] = f64_to_f32_rn(v);
         __syncwarp();
@@ -493,21 +509,32 @@ __global__ void __launch_bounds__(kNT, 4) k_apply_mix32(PSet P, ApplyIO io, Solv
         if (MODE == kApplyFused) {
             st_vec(io.r_out + row, v, pol);
             rr = fma(v, v, rr);
+            if (flex) qz = fma(qi, zi, qz);
         }
         rho = fma(v, zi, rho);
         __syncwarp();
     }
-    double b1, b2;
-    cta_sum_to0<kNT, true>(rho, rr, s_red, b1, b2);
-    if (MODE == kApplyStandalone && io.out == nullptr) return;
-    if (threadIdx.x == 0) {
-        io.part[2 * blockIdx.x] = b1;
-        io.part[2 * blockIdx.x + 1] = b2;
+    // rho, r.r and (flexible CG) q.z: partials in io.part with stride nv
+    double b[3] = {0.0, 0.0, 0.0};
+    if (flex) {
+        const double v[3] = {rho, rr, qz};
+        cta_sum_to0<kNT, 3>(v, s_red, b);
+    } else {
+        const double v[2] = {rho, rr};
+        double b2[2];
+        cta_sum_to0<kNT, 2>(v, s_red, b2);
+        b[0] = b2[0];
+        b[1] = b2[1];
     }
+    if (MODE == kApplyStandalone && io.out == nullptr) return;
+    const int nv = flex ? 3 : 2;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nv; ++k) io.part[nv * blockIdx.x + k] = b[k];
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red + kNT);
-    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1);
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, nv, s_red);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, nv, s_red + kNT);
+    const double t3 = flex ? reduce_partials<kNT>(io.part + 2, gridDim.x, nv, s_red + 2 * kNT) : 0.0;
+    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1, flex, t3);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -569,12 +596,12 @@ static int launch_tma_mode(const PSet &P, const ApplyIO &io, SolverState *S, int
     }
 }
 
-template <typename QT, int BS, int MODE>
+template <typename QT, int BS, int MODE, bool FLEX = false>
 static int launch_reg_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
     static int per_sm = 0;
     if (per_sm == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_reg<QT, BS, MODE>, kNT, 0) != cudaSuccess || v < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_reg<QT, BS, MODE, FLEX>, kNT, 0) != cudaSuccess || v < 1)
             v = 1;
         per_sm = v;
     }
@@ -583,26 +610,26 @@ static int launch_reg_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaSt
     if (g > need) g = need;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g < 1) g = 1;
-    MPB_CUDA(launch_kernel(k_apply_reg<QT, BS, MODE>, g, kNT, 0, st, P, io, S));
+    MPB_CUDA(launch_kernel(k_apply_reg<QT, BS, MODE, FLEX>, g, kNT, 0, st, P, io, S));
     return MPBJAC_OK;
 }
 
-template <int MODE>
+template <int MODE, bool FLEX = false>
 static int launch_reg_mode(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
     switch (P.ufmt * 1000 + P.ubs) {
-        case BJAC_FP32 * 1000 + 32: return launch_reg_t<float, 32, MODE>(P, io, S, st);
-        case BJAC_BF16 * 1000 + 32: return launch_reg_t<__nv_bfloat16, 32, MODE>(P, io, S, st);
-        case BJAC_FP16S * 1000 + 32: return launch_reg_t<__half, 32, MODE>(P, io, S, st);
+        case BJAC_FP32 * 1000 + 32: return launch_reg_t<float, 32, MODE, FLEX>(P, io, S, st);
+        case BJAC_BF16 * 1000 + 32: return launch_reg_t<__nv_bfloat16, 32, MODE, FLEX>(P, io, S, st);
+        case BJAC_FP16S * 1000 + 32: return launch_reg_t<__half, 32, MODE, FLEX>(P, io, S, st);
         default: return fail(MPBJAC_ERR_UNSUPPORTED, "no register apply kernel for this format / block size");
     }
 }
 
-template <int MODE>
+template <int MODE, bool FLEX = false>
 static int launch_mix_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
     static int per_sm = 0;
     if (per_sm == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_mix32<MODE>, kNT, 0) != cudaSuccess || v < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_mix32<MODE, FLEX>, kNT, 0) != cudaSuccess || v < 1)
             v = 1;
         per_sm = v;
     }
@@ -611,7 +638,7 @@ static int launch_mix_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaSt
     if (g > need) g = need;
     if (g > kMaxGrid) g = kMaxGrid;
     if (g < 1) g = 1;
-    MPB_CUDA(launch_kernel(k_apply_mix32<MODE>, g, kNT, 0, st, P, io, S));
+    MPB_CUDA(launch_kernel(k_apply_mix32<MODE, FLEX>, g, kNT, 0, st, P, io, S));
     return MPBJAC_OK;
 }
 
@@ -622,7 +649,8 @@ int launch_apply_mix(int mode, const PSet &P, const ApplyIO &io, SolverState *S,
         case kApplyStandalone: return launch_mix_t<kApplyStandalone>(P, io, S, st);
         case kApplyInit: return launch_mix_t<kApplyInit>(P, io, S, st);
         case kApplyTemporal: return launch_mix_t<kApplyTemporal>(P, io, S, st);
-        default: return launch_mix_t<kApplyFused>(P, io, S, st);
+        default:
+            return io.flex ? launch_mix_t<kApplyFused, true>(P, io, S, st) : launch_mix_t<kApplyFused>(P, io, S, st);
     }
 }
 
@@ -635,7 +663,8 @@ int launch_apply_reg(int mode, const PSet &P, const ApplyIO &io, SolverState *S,
         case kApplyStandalone: return launch_reg_mode<kApplyStandalone>(P, io, S, st);
         case kApplyInit: return launch_reg_mode<kApplyInit>(P, io, S, st);
         case kApplyTemporal: return launch_reg_mode<kApplyTemporal>(P, io, S, st);
-        default: return launch_reg_mode<kApplyFused>(P, io, S, st);
+        default:
+            return io.flex ? launch_reg_mode<kApplyFused, true>(P, io, S, st) : launch_reg_mode<kApplyFused>(P, io, S, st);
     }
 }
 

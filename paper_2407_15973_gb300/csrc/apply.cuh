@@ -23,6 +23,7 @@ struct ApplyIO {
     int *err;              // device error word (nullable)
     int set;               // 1 low-precision set, 0 binary64 set (standalone / fused)
     int only_set;          // -1: this launch serves both sets; else it serves only that set
+    int flex;              // fused mode, register kernels: also sum q.z for the flexible-CG beta
 };
 
 // ----------------------------------------------------------------------------------------
@@ -30,7 +31,7 @@ struct ApplyIO {
 // ----------------------------------------------------------------------------------------
 template <int MODE>
 __device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyIO &io, SolverState *S,
-                                             int used_low) {
+                                             int used_low, bool has_qz = false, double qz = 0.0) {
     if (MODE == kApplyStandalone) {
         if (io.out) *io.out = rho;
         return;
@@ -53,10 +54,14 @@ __device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyI
         if (rel <= S->tol) { S->state = kConverged; return; }
         if (S->iter >= S->maxit) { S->state = kMaxit; return; }
     }
-    // kApplyTemporal and kApplyFused (still running): beta = rho_new / rho_old (the flexible
-    // variant replaces beta in a kernel of its own and reads rho_old from rho_prev)
+    // kApplyTemporal and kApplyFused (still running): beta = rho_new / rho_old. Flexible CG
+    // takes beta = z_{k+1}^T (r_{k+1} - r_k) / rho_old = -alpha q.z_{k+1} / rho_old: here when the
+    // kernel summed q.z (has_qz), else in a kernel of its own that reads rho_old from rho_prev.
     if (!finite_pos(rho)) { S->state = kBreakdown; return; }
-    S->beta = rho / S->rho;
+    double beta = rho / S->rho;
+    if (has_qz && S->flexible) beta = -S->alpha * qz / S->rho;
+    if (!(fabs(beta) < 1.0e308)) { S->state = kBreakdown; return; }
+    S->beta = beta;
     S->rho_prev = S->rho;
     S->rho = rho;
 }

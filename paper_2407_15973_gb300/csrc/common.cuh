@@ -130,7 +130,8 @@ struct SolverState {
     double rho, sigma, alpha, beta, rr, relres, true_relres;
     double rho_prev;       // rho of the previous application (the flexible beta's denominator)
     int32_t iter, state, use_low, x_pending;
-    int32_t low_applies, high_applies, restarts, pad1;
+    int32_t low_applies, high_applies, restarts;
+    int32_t flexible;      // flexible-CG beta (set by the host for the solve)
     unsigned int tickets[8];
 };
 
@@ -181,28 +182,27 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return t;
 }
 
-// Sums over the CTA of one (TWO = false) or two per-thread values, valid in thread 0 only
-// (the per-CTA partials of a grid reduction). The values pass through shared memory and warp 0
-// adds them: NT/32 adds per lane in a fixed order, then one warp tree per value. That is about
-// a sixth of the FP64 instructions of a tree in every warp, and the FP64 pipe is a co-bound of
-// the loop kernels. sm: NT doubles per value.
-template <int NT, bool TWO>
-__device__ __forceinline__ void cta_sum_to0(double a, double b, double *sm, double &ra, double &rb) {
+// Sums over the CTA of NV per-thread values, valid in thread 0 only (the per-CTA partials of
+// a grid reduction). The values pass through shared memory and warp 0 adds them: NT/32 adds
+// per lane in a fixed order, then one warp tree per value. That is about a sixth of the FP64
+// instructions of a tree in every warp, and the FP64 pipe is a co-bound of the loop kernels.
+// sm: NV * NT doubles.
+template <int NT, int NV>
+__device__ __forceinline__ void cta_sum_to0(const double (&v)[NV], double *sm, double (&out)[NV]) {
     __syncthreads();
-    sm[threadIdx.x] = a;
-    if (TWO) sm[NT + threadIdx.x] = b;
-    __syncthreads();
-    ra = 0.0;
-    rb = 0.0;
-    if (threadIdx.x < 32) {
-        double s = sm[threadIdx.x], t = TWO ? sm[NT + threadIdx.x] : 0.0;
 #pragma unroll
-        for (int i = 1; i < NT / 32; ++i) {
-            s += sm[threadIdx.x + 32 * i];
-            if (TWO) t += sm[NT + threadIdx.x + 32 * i];
+    for (int k = 0; k < NV; ++k) sm[k * NT + threadIdx.x] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = 0.0;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = sm[k * NT + threadIdx.x];
+#pragma unroll
+            for (int i = 1; i < NT / 32; ++i) s += sm[k * NT + threadIdx.x + 32 * i];
+            out[k] = warp_sum(s);
         }
-        ra = warp_sum(s);
-        if (TWO) rb = warp_sum(t);
     }
 }
 
