@@ -182,6 +182,13 @@ int pcg_solve_batched(bjac_batch *h, const double *const *b, double *const *x, d
  * 64-row tiles likewise) of a batch. All outputs HOST and nullable. */
 int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid, float *tune_ms);
 
+/* Failure-path test hook: with on = 1, the grid barriers of the batch's next solves wait for
+ * one CTA more than the grid holds, so every CTA's bounded wait (2 s of %globaltimer) expires,
+ * the kernel leaves at that barrier and pcg_solve_batched returns TIMEOUT with the context
+ * still usable; on = 0 restores normal solves. Nothing faults, traps or hangs. Returns
+ * INVALID_ARG for a NULL batch or on outside {0, 1}. */
+int bjac_batch_force_timeout(bjac_batch *h, int32_t on);
+
 void bjac_batch_destroy(bjac_batch *h);
 
 /* Release everything the handle owns (synchronises its stream first). NULL is ignored. */

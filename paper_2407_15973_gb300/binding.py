@@ -88,6 +88,7 @@ def lib():
                 "bjac_batch_setup": (C.c_int, [i32, P, P, P, C.POINTER(bjac_policy), C.POINTER(P)]),
                 "pcg_solve_batched": (C.c_int, [P, P, P, f64, i32, P]),
                 "bjac_batch_info": (C.c_int, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), P]),
+                "bjac_batch_force_timeout": (C.c_int, [P, i32]),
                 "bjac_batch_destroy": (None, [P]),
                 "bjac_mlp_grad": (C.c_int, [P, i32, P, P, i32, P, P, P]),
                 "bjac_mlp_train": (C.c_int, [P, P, P, i32, i32, C.c_float, P, P]),
@@ -353,6 +354,10 @@ class Batch:
         ms = (C.c_float * 6)()
         _check(lib().bjac_batch_info(self.h, C.byref(nt), C.byref(tr), C.byref(g), ms))
         return dict(ntiles=nt.value, tile_rows=tr.value, grid=g.value, tune_ms=list(ms))
+
+    def force_timeout(self, on: bool):
+        """Test hook: the next solves' grid barriers time out (TIMEOUT, context usable)."""
+        _check(lib().bjac_batch_force_timeout(self.h, int(bool(on))))
 
     def solve(self, bs, xs, tol=1e-10, maxit=5000):
         _require_cuda(*bs, *xs)

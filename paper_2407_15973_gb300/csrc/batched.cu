@@ -68,16 +68,18 @@ struct BatchDev {
     // barrier and control
     unsigned int *bar_count, *bar_gen;
     int32_t *err, *active;
+    int32_t bar_extra;           // arrivals a barrier waits for beyond the grid (0; 1 = forced timeout)
 };
 
 __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
+    __shared__ int s_ok;     // thread 0's verdict, so that the whole CTA leaves or stays together
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int *gen = d.bar_gen;
         const unsigned int g = *gen;
         __threadfence();
         const unsigned int arrived = atomicAdd(d.bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == gridDim.x - 1 + (unsigned int)d.bar_extra) {
             *d.bar_count = 0u;
             __threadfence();
             atomicAdd(d.bar_gen, 1u);
@@ -93,9 +95,10 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
             }
         }
         __threadfence();
+        s_ok = *((volatile int32_t *)d.err) == 0;
     }
     __syncthreads();
-    return *((volatile int32_t *)d.err) == 0;
+    return s_ok != 0;
 }
 
 // a tile's description, read with two 16-byte loads
@@ -503,6 +506,8 @@ struct bjac_batch {
     cudaGraphExec_t exec = nullptr;
     double tol_cached = -1.0;
     int maxit_cached = -1;
+    int force_timeout = 0;                   // test hook: barriers wait for one CTA too many
+    int force_cached = 0;
     int32_t blocks_per_fmt[4] = {0, 0, 0, 0};
     float setup_ms = 0.0f;
 };
@@ -572,6 +577,7 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     d.bar_gen = h->ctl + 1;
     d.err = reinterpret_cast<int32_t *>(h->ctl + 2);
     d.active = reinterpret_cast<int32_t *>(h->ctl + 3);
+    d.bar_extra = h->force_timeout ? 1 : 0;
     d.nlist = reinterpret_cast<int32_t *>(h->ctl + 4);
     d.soff = h->soff;
     d.tinfo = h->tinfo;
@@ -783,7 +789,7 @@ static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bo
     BatchDev d = batch_dev(h, tol, maxit);
     MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned int), st));
     if (!use_graph) return launch_batched(h->variant, h->fp32_only, d, st, h->grid);
-    if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit) {
+    if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit || h->force_cached != h->force_timeout) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
         if (h->graph) cudaGraphDestroy(h->graph);
         h->exec = nullptr;
@@ -802,6 +808,7 @@ static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bo
         h->graph = g;
         h->tol_cached = tol;
         h->maxit_cached = maxit;
+        h->force_cached = h->force_timeout;
     }
     MPB_CUDA(cudaGraphLaunch(h->exec, st));
     return MPBJAC_OK;
@@ -1073,6 +1080,13 @@ extern "C" int pcg_solve_batched(bjac_batch *h, const double *const *b, double *
 }
 
 extern "C" void bjac_batch_destroy(bjac_batch *h) { free_batch(h); }
+
+extern "C" int bjac_batch_force_timeout(bjac_batch *h, int32_t on) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "batch is NULL");
+    if (on != 0 && on != 1) return fail(MPBJAC_ERR_INVALID_ARG, "on must be 0 or 1");
+    h->force_timeout = on;
+    return MPBJAC_OK;
+}
 
 extern "C" int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid,
                                float *tune_ms) {

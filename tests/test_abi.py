@@ -55,6 +55,7 @@ def test_host_side_validation_without_gpu(libpath):
     assert L.pcg_solve(None, None, None, 1e-10, 10, None, None) == B.ERR_INVALID_ARG
     assert L.bjac_mlp_param_count() == 5187 + 24
     assert L.bjac_l2_residency(2) == B.ERR_INVALID_ARG
+    assert L.bjac_batch_force_timeout(None, 1) == B.ERR_INVALID_ARG
     assert L.bjac_l2_residency(0) == 1 and L.bjac_l2_residency(1) == 0     # default on; restored
 
 

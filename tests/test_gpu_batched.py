@@ -82,3 +82,29 @@ def test_batched_repeatable(B, systems):
     assert runs[0][0] == runs[1][0]
     for x1, x2 in zip(runs[0][1], runs[1][1]):
         assert np.array_equal(x1, x2)
+
+
+def test_batched_barrier_timeout_reports_and_recovers(B, systems):
+    # the failure path of the persistent kernel: its grid barriers are bounded waits. With the
+    # test hook each barrier waits for one CTA more than the grid holds, so every wait expires
+    # (2 s), the kernel leaves and the call reports TIMEOUT; nothing faults or hangs, and the
+    # next normal solve on the same batch (same context) converges
+    import time
+    sub = systems[:3]
+    rhs = [cuda(O.spmv(p.A, p.x_star)) for p in sub]
+    bt = B.Batch([B.DeviceCSR(p.A) for p in sub], [p.block_ptr for p in sub], select=B.SELECT_FIXED,
+                 fixed_fmt=B.FP32)
+    try:
+        bt.force_timeout(True)
+        xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in sub]
+        t0 = time.time()
+        with pytest.raises(B.MpbjacError) as e:
+            bt.solve(rhs, xs, tol=TOL, maxit=5000)
+        assert e.value.code == B.ERR_TIMEOUT
+        assert 1.5 < time.time() - t0 < 60
+        bt.force_timeout(False)
+        xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in sub]
+        rc, st = bt.solve(rhs, xs, tol=TOL, maxit=5000)
+        assert rc == 0 and all(s["converged"] and s["true_relres"] <= TOL for s in st)
+    finally:
+        bt.close()
