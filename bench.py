@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--m", type=int, default=128, help="grid side (128 = the named workload)")
     ap.add_argument("--bs", type=int, default=32)
     ap.add_argument("--fmt", default="bf16", choices=list(FMT))
+    ap.add_argument("--temporal", default="none", choices=["none", "hl", "lh"],
+                    help="aMP switching for the headline policy (adp_tol 10 for hl, 1e-5 for lh)")
+    ap.add_argument("--flexible", action="store_true", help="flexible-CG beta for the headline policy")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode table")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
     ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
@@ -73,7 +76,7 @@ def workload_config(args):
     return {"workload": f"diffusion3d-7pt-{args.m}^3-subcube8-logU[1e-3,1e3]-dt1e-2",
             "n": args.m ** 3, "block_size": args.bs, "mixed_format": args.fmt, "tol": TOL,
             "step": "bjac_setup + pcg_solve + bjac_destroy", "l2": "inputs larger than L2 (no flush)",
-            "l2_residency": args.l2_residency}
+            "l2_residency": args.l2_residency, "temporal": args.temporal, "flexible": args.flexible}
 
 
 # ------------------------------------------------------------------------------------------
@@ -220,7 +223,9 @@ def run_ours(args, rank, world, dist):
     apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3, "mix": 4}[args.apply_kernel]
     layout_pin = {"auto": 0, "csr": 1, "sell": 2, "sell-pf": 3}[args.spmv_layout]
     head = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[args.fmt], apply_variant=apply_pin,
-                graph_mode=1 if args.eager else 0, spmv_format=layout_pin)
+                graph_mode=1 if args.eager else 0, spmv_format=layout_pin, flexible=args.flexible,
+                temporal={"none": B.TEMPORAL_NONE, "hl": B.TEMPORAL_HL, "lh": B.TEMPORAL_LH}[args.temporal],
+                adp_tol={"none": 10.0, "hl": 10.0, "lh": 1e-5}[args.temporal])
     if args.profile_iters:
         if args.profile_kt:
             pk = PB.make_problem("diff3d-const", seed=0, m=args.m)

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     __shared__ StageMeta meta[kStages];
-    __shared__ double red[2][kSpNT / 32];
+    __shared__ double red[2 * kSpNT];
     __shared__ int s_bad;
 
     if (KIND == kSpPcg) {
@@ -170,15 +170,23 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         return;
     }
     if (KIND == kSpY) return;
-    const double b1 = block_sum<kSpNT>(acc1, red[0]);
-    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    double cs[2] = {0.0, 0.0};     // this CTA's partial sums (valid in thread 0)
+    if (RES) {
+        const double v[2] = {acc1, acc2};
+        cta_sum_to0<kSpNT, 2>(v, red, cs);
+    } else {
+        const double v[1] = {acc1};
+        double c1[1];
+        cta_sum_to0<kSpNT, 1>(v, red, c1);
+        cs[0] = c1[0];
+    }
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = b1;
-        part[2 * blockIdx.x + 1] = b2;
+        part[2 * blockIdx.x] = cs[0];
+        part[2 * blockIdx.x + 1] = cs[1];
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
     if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
 }
 
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     constexpr bool RES = KIND >= 10;
     __shared__ double s_v[NW][CH];
     __shared__ int32_t s_c[NW][CH];
-    __shared__ double red[2][NW];
+    __shared__ double red[2 * kSpNT];
     if (KIND == kSpPcg) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
@@ -299,15 +307,23 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
         nx_lo = nn_lo; nx_hi = nn_hi;
     }
     if (KIND == kSpY) return;
-    const double b1 = block_sum<kSpNT>(acc1, red[0]);
-    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    double cs[2] = {0.0, 0.0};     // this CTA's partial sums (valid in thread 0)
+    if (RES) {
+        const double v[2] = {acc1, acc2};
+        cta_sum_to0<kSpNT, 2>(v, red, cs);
+    } else {
+        const double v[1] = {acc1};
+        double c1[1];
+        cta_sum_to0<kSpNT, 1>(v, red, c1);
+        cs[0] = c1[0];
+    }
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = b1;
-        part[2 * blockIdx.x + 1] = b2;
+        part[2 * blockIdx.x] = cs[0];
+        part[2 * blockIdx.x + 1] = cs[1];
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
     if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
 }
 
@@ -331,7 +347,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
     constexpr bool RES = KIND >= 10;
     __shared__ double s_v[NW][2][CH];
     __shared__ double s_x[NW][2][CH];
-    __shared__ double red[2][NW];
+    __shared__ double red[2 * kSpNT];
     if (KIND == kSpPcg) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
@@ -449,15 +465,23 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32
         p_hi = q_hi;
     }
     if (KIND == kSpY) return;
-    const double b1 = block_sum<kSpNT>(acc1, red[0]);
-    const double b2 = RES ? block_sum<kSpNT>(acc2, red[1]) : 0.0;
+    double cs[2] = {0.0, 0.0};     // this CTA's partial sums (valid in thread 0)
+    if (RES) {
+        const double v[2] = {acc1, acc2};
+        cta_sum_to0<kSpNT, 2>(v, red, cs);
+    } else {
+        const double v[1] = {acc1};
+        double c1[1];
+        cta_sum_to0<kSpNT, 1>(v, red, c1);
+        cs[0] = c1[0];
+    }
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = b1;
-        part[2 * blockIdx.x + 1] = b2;
+        part[2 * blockIdx.x] = cs[0];
+        part[2 * blockIdx.x + 1] = cs[1];
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red[0]);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red[1]) : 0.0;
+    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
+    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
     if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
 }
 
