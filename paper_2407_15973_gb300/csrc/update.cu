@@ -5,6 +5,18 @@
 
 namespace mpbjac {
 
+// The flexible-beta dot product: half the CTAs of the plain vector kernels, so there are fewer
+// per-CTA partial sums to add on the narrow FP64 pipe (each thread streams more pairs instead;
+// measured in the PCG graph: 278 -> 252 ms for the 128^3 aMP(hl) flexible solve). The residual
+// update of the aMP loop keeps the full grid, which measured faster there.
+static int vec_grid_red(int n) {
+    int g = sm_count() * 4;
+    const int need = (n / 2 + kNT - 1) / kNT;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return g < 1 ? 1 : g;
+}
+
 static int vec_grid2(int n) {
     int g = sm_count() * 8;
     const int need = (n / 2 + kNT - 1) / kNT;
@@ -18,7 +30,7 @@ static int vec_grid2(int n) {
 __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
                                                   double *part, SolverState *S) {
     pdl_enter();
-    __shared__ double red[kWarps];
+    __shared__ double red[kNT];
     if (S->state != kRunning) return;
     const double alpha = S->alpha;
     const uint64_t pol = vec_policy(S->l2_keep);
@@ -41,8 +53,10 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
         r[n - 1] = v;
         rr = fma(v, v, rr);
     }
-    const double bsum = block_sum<kNT>(rr, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+    const double v[1] = {rr};
+    double bsum[1];
+    cta_sum_to0<kNT, 1>(v, red, bsum);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum[0];
     if (!last_cta(&S->tickets[kTicketUpdR])) return;
     const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
     if (threadIdx.x != 0) return;
@@ -112,7 +126,7 @@ __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restri
 __global__ void __launch_bounds__(kNT) k_flex_beta(int n, const double *__restrict__ q,
                                                    const double *__restrict__ z, double *part, SolverState *S) {
     pdl_enter();
-    __shared__ double red[kWarps];
+    __shared__ double red[kNT];
     if (S->state != kRunning) return;
     const uint64_t pol = vec_policy(S->l2_keep);
     double s = 0.0;
@@ -127,8 +141,10 @@ __global__ void __launch_bounds__(kNT) k_flex_beta(int n, const double *__restri
         s = fma(qv.y, zv.y, s);
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s = fma(q[n - 1], z[n - 1], s);
-    const double bsum = block_sum<kNT>(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+    const double v[1] = {s};
+    double bsum[1];
+    cta_sum_to0<kNT, 1>(v, red, bsum);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum[0];
     if (!last_cta(&S->tickets[kTicketFlex])) return;
     const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
     if (threadIdx.x != 0) return;
@@ -138,7 +154,7 @@ __global__ void __launch_bounds__(kNT) k_flex_beta(int n, const double *__restri
 }
 
 int launch_flex_beta(int n, const double *q, const double *z, double *part, SolverState *S, cudaStream_t st) {
-    MPB_CUDA(launch_kernel(k_flex_beta, vec_grid2(n), kNT, 0, st, n, q, z, part, S));
+    MPB_CUDA(launch_kernel(k_flex_beta, vec_grid_red(n), kNT, 0, st, n, q, z, part, S));
     return MPBJAC_OK;
 }
 
