@@ -167,6 +167,16 @@ def committed_traffic(kernel, workload_key):
 
 
 # ------------------------------------------------------------------------------------------
+def max_over_ranks(value, dist, device):
+    """The slowest rank's value (the job's time); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2407_15973_gb300 import binding as B
@@ -210,10 +220,7 @@ def run_ours(args, rank, world, dist):
         barrier()
         ms = ev[0].elapsed_time(ev[k]) / k
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k)]
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         timed.last_steps = per
         return ms, stats
 
