@@ -592,7 +592,7 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
 // that format alone, which need fewer registers
 constexpr int kBatchVariants = 6;
 constexpr int kVarTR[kBatchVariants] = {32, 32, 32, 64, 64, 64};
-constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6};
+[[maybe_unused]] constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6};   // as instantiated below
 
 template <int TR, int MINB, int FMT>
 static int launch_batched_t(const BatchDev &d, cudaStream_t st, int grid) {
@@ -910,7 +910,6 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     }
     BTRY(cudaMalloc(&h->pool, std::max<int64_t>(16, qoff[nb_tot])));
     BTRY(cudaMemcpy(h->qoff, qoff.data(), sizeof(int64_t) * (nb_tot + 1), cudaMemcpyHostToDevice));
-    bjac_csr big{h->n_tot, h->nnz_tot, h->rowptr, h->colidx, h->val};
     SetupArgs a{};
     a.n = h->n_tot;
     a.rowptr = h->rowptr;
