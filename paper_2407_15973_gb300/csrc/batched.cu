@@ -939,7 +939,6 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     if (hstat[0] != 0) return bail(fail(MPBJAC_ERR_NOT_SPD, "a diagonal block of the batch is not positive definite"));
     for (uint8_t f : hf) h->blocks_per_fmt[f & 3] += 1;
     h->fp32_only = h->blocks_per_fmt[BJAC_FP32] == nb_tot;
-    (void)big;
     // vectors and per-system state
     BTRY(cudaMalloc(&h->b, sizeof(double) * n_tot));
     BTRY(cudaMalloc(&h->x, sizeof(double) * n_tot));
