@@ -18,9 +18,12 @@
  *   PCG             Section 3.2 (Hestenes-Stiefel CG), stopping rule of Section 4.2:
  *                   ||r_k||_2 / ||b||_2 <= tol with the recurrence residual, followed by a
  *                   true-residual check b - A x (Section 4.5.1).
+ *   BJAC(k, t)      Eq. 3-2 / 3-3 with inner Jacobi sweeps (BJAC_SELECT_KT), the paper's
+ *                   experimental configuration.
  * Beyond the paper (its exact blocks are the special case it names): per-block storage
  * formats FP32, BF16 and power-of-two-scaled FP16, chosen per block by a condition-number
- * rule or a learned selector.
+ * rule or a learned selector; the flexible-CG direction coefficient (policy.flexible);
+ * many independent systems in one persistent launch (bjac_batch_*).
  */
 #ifndef MPBJAC_H
 #define MPBJAC_H
