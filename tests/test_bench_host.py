@@ -69,3 +69,17 @@ def test_reference_arm_rank0_prints_one_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("diffusion3d-7pt-128^3")
+
+
+def test_algorithmic_bytes_of_the_128_cube_workload():
+    # per-launch bytes the roofline divides by (values read or written once): the SpMV moves
+    # A (12 B per nonzero), row pointers, p and q; the fused BF16 apply the inverses, the block
+    # scales and r, q in / r, z out; the x/p update x, p, z in and x, p out
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nnz, nb, bs = 128 ** 3, 7 * 128 ** 3 - 6 * 128 ** 2, 128 ** 3 // 32, 32
+    assert nnz == 14581760                                  # Table 4.1
+    got = bench.algorithmic_bytes(n, nnz, nb, bs, 2)
+    assert got == {"spmv": 174981120 + 8388612 + 33554432, "apply": 134217728 + 262144 + 67108864,
+                   "update_xp": 83886080}
+    assert bench.algorithmic_bytes(n, nnz, nb, bs, 4)["apply"] == 268435456 + 67108864      # FP32: no scales
