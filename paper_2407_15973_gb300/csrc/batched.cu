@@ -72,7 +72,7 @@ struct BatchDev {
 };
 
 __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
-    __shared__ int s_ok;     // thread 0's verdict, so that the whole CTA leaves or stays together
+    __shared__ int s_ok;     // thread 0's decision, so that the whole CTA leaves or stays together
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int *gen = d.bar_gen;
