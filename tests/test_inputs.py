@@ -94,3 +94,17 @@ def test_batched_workload_recipe():
         expect = 9 * p.meta["side"] ** 2 - 12 * p.meta["side"] + 4 if p.meta["nine"] else 5 * p.meta["side"] ** 2 - 4 * p.meta["side"]
         assert p.A.nnz == expect
     assert sum(p.A.n for p in sys_) == 11037723 and sum(p.A.nnz for p in sys_) == 78749967
+
+
+def test_aniso27_workload_recipe():
+    # Q1 trilinear elements on (m+1)^3 elements: 27-point stencil on m^3 interior nodes,
+    # symmetric positive definite, but with positive off-diagonal entries (not an M-matrix)
+    m = 6
+    A = PB.make_problem("aniso27", seed=3, m=m).A
+    assert A.n == m ** 3 and A.nnz == (3 * m - 2) ** 3
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.colidx, A.rowptr), shape=(A.n, A.n)).toarray()
+    assert np.allclose(M, M.T, rtol=1e-14, atol=0)
+    assert np.linalg.eigvalsh(M).min() > 0
+    off = M - np.diag(np.diag(M))
+    assert (off > 0).any()
