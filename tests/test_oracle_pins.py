@@ -727,3 +727,15 @@ def test_flexible_pcg_kt_keeps_consecutive_directions_conjugate(oracle):
     std = _step_conjugacy(oracle, pr, lambda k: oracle.pcg_kt(pr.A, bp, b, tol=1e-14, maxit=k,
                                                               policy=oracle.POLICY_HL, adp_tol=1e-2))
     assert flex.max() < 1e-12 and std.max() > 1e3 * flex.max(), (std, flex)
+
+
+def test_oracle_rounds_every_product_and_sum(oracle):
+    # the oracle's sums are sequential with each product rounded before it is added (no fused
+    # multiply-add): (1 + 2^-30)(1 - 2^-30) = 1 - 2^-60 rounds to 1, so -1 + that product is 0;
+    # a fused evaluation would give -2^-60
+    c, d = 1.0 + 2.0 ** -30, 1.0 - 2.0 ** -30
+    assert oracle.dot(np.array([-1.0, c]), np.array([1.0, d])) == 0.0
+    A = PB.CSR(1, np.array([0, 2], np.int32), np.array([0, 0], np.int32), np.array([-1.0, c]))
+    assert oracle.spmv(A, np.array([1.0]))[0] == c - 1.0            # -1 * 1 + c * 1, each rounded
+    A2 = PB.CSR(2, np.array([0, 2, 2], np.int32), np.array([0, 1], np.int32), np.array([-1.0, c]))
+    assert oracle.spmv(A2, np.array([1.0, d]))[0] == 0.0
