@@ -51,6 +51,7 @@ def lib():
             sig = {
                 "orc_spmv": (None, [i32, P, P, P, P, P]),
                 "orc_dot": (f64, [i64, P, P]),
+                "orc_set_dot_order": (i32, [i32]),
                 "orc_residual": (None, [i32, P, P, P, P, P, P]),
                 "orc_block_inverse": (i32, [i32, P, P, P, i32, P, P, P, P]),
                 "orc_round_f32_bits": (C.c_uint32, [f64]),
@@ -103,6 +104,16 @@ def spmv(A, x):
 def dot(a, b):
     a, b = _c(a, np.float64), _c(b, np.float64)
     return lib().orc_dot(len(a), _p(a), _p(b))
+
+
+DOT_SEQUENTIAL, DOT_REVERSED, DOT_PAIRWISE, DOT_STRIDED, DOT_COMPENSATED = 0, 1, 2, 3, 4
+
+
+def set_dot_order(order: int) -> int:
+    """Summation order of every dot product and norm of the oracle's PCG (0 sequential, the
+    default; 1 reversed; 2 pairwise; 3 1024 strided partials; 4 compensated). Returns the
+    previous order. Process-wide: restore it after use."""
+    return int(lib().orc_set_dot_order(int(order)))
 
 
 def residual(A, b, x):

@@ -52,10 +52,71 @@ void orc_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const dou
     }
 }
 
-/* a . b, summed from index 0 upward. */
+/* Summation order of orc_dot (and so of every dot product and norm in orc_pcg). Every order
+ * rounds each product a_i * b_i once and adds the products in binary64; they differ only in
+ * which partial sums are formed, so each is an equally valid evaluation of the definition.
+ *   0  sequential from index 0 upward (the default; every pin and parity test uses it)
+ *   1  sequential from index n-1 downward
+ *   2  pairwise: the range is halved recursively, runs of <= 8 terms summed in order
+ *   3  strided partials: 1024 running sums, sum p over the indices i = p (mod 1024) in
+ *      increasing order, then the 1024 partials added pairwise (the shape of a grid-stride
+ *      GPU reduction)
+ *   4  compensated (Neumaier's variant of Kahan summation, Neumaier 1974): the running
+ *      rounding error is carried and added at the end, nearly the exactly rounded sum
+ * Only the spread test selects another order; the setting is process-wide. */
+static int32_t g_dot_order = 0;
+
+int32_t orc_set_dot_order(int32_t order) {
+    int32_t old = g_dot_order;
+    if (order >= 0 && order <= 4) g_dot_order = order;
+    return old;
+}
+
+static double dot_pairwise(int64_t n, const double *a, const double *b) {
+    if (n <= 8) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+        return s;
+    }
+    int64_t h = n / 2;
+    return dot_pairwise(h, a, b) + dot_pairwise(n - h, a + h, b + h);
+}
+
+static double sum_pairwise(int64_t n, const double *v) {
+    if (n <= 8) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += v[i];
+        return s;
+    }
+    int64_t h = n / 2;
+    return sum_pairwise(h, v) + sum_pairwise(n - h, v + h);
+}
+
+/* a . b in the order g_dot_order names (default: from index 0 upward). */
 double orc_dot(int64_t n, const double *a, const double *b) {
     double s = 0.0;
-    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    if (g_dot_order == 1) {
+        for (int64_t i = n - 1; i >= 0; --i) s += a[i] * b[i];
+    } else if (g_dot_order == 2) {
+        s = dot_pairwise(n, a, b);
+    } else if (g_dot_order == 3) {
+        double part[1024];
+        for (int p = 0; p < 1024; ++p) part[p] = 0.0;
+        for (int64_t i = 0; i < n; ++i) part[i % 1024] += a[i] * b[i];
+        s = sum_pairwise(1024, part);
+    } else if (g_dot_order == 4) {
+        double c = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = a[i] * b[i];
+            double u = s + t;
+            if (fabs(s) >= fabs(t)) c += (s - u) + t;
+            else c += (t - u) + s;
+            s = u;
+        }
+        s += c;
+    } else {
+        for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    }
     return s;
 }
 

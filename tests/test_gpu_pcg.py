@@ -6,6 +6,7 @@ import torch
 import oracle as O
 from paper_2407_15973_gb300 import problems as PB
 from gpu_util import cuda, host, need_gpu
+from pcg_cases import PROBLEMS, uniform_iteration_band
 
 pytestmark = pytest.mark.gpu
 
@@ -16,15 +17,6 @@ TOL = 1e-10
 def B():
     return need_gpu()
 
-
-PROBLEMS = {
-    "poisson2d_bs8": lambda: PB.make_problem("poisson2d", bs=8),
-    "subcube24_bs32": lambda: PB.make_problem("subcube3d", seed=1, m=24, bs=32),
-    "subcube24_bs64": lambda: PB.make_problem("subcube3d", seed=2, m=24, bs=64),
-    "aniso27_12_bs64": lambda: PB.make_problem("aniso27", seed=3, m=12, bs=64),
-    "voronoi24_uneven": lambda: PB.make_problem("voronoi3d", seed=4, m=24),
-    "ragged13_bs32": lambda: PB.make_problem("subcube3d", seed=5, m=13, bs=32),
-}
 
 _cache = {}
 
@@ -61,10 +53,11 @@ def test_uniform_fp64_iterations(B, name):
     ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000)
     got = _gpu_solve(B, pr, b, select=B.SELECT_UNIFORM, hist=True)
     assert ref["converged"] and got["converged"]
-    # equally valid summation orders of the dot products move the count of this textbook PCG
-    # by up to 3 % on the ill-conditioned cases (aniso27_12_bs64: 326 ... 336 with sequential,
-    # exactly rounded, BLAS and randomly permuted sums), so the count is compared within that
-    assert abs(got["iters"] - ref["iters"]) <= max(2, 0.03 * ref["iters"])
+    # +-2 around the band of counts the oracle itself gives under five valid summation orders
+    # of its dot products (test_oracle_pins.py::test_uniform_iteration_band_over_summation_orders:
+    # one count on every system here but the 27-point anisotropic one, 326 ... 334 there)
+    lo, hi = uniform_iteration_band(pr, b, P)
+    assert lo - 2 <= got["iters"] <= hi + 2, (got["iters"], lo, hi)
     assert got["true_relres"] <= TOL
     assert abs(_err(got["x"], pr.x_star) - _err(ref["x"], pr.x_star)) <= 10 * _err(ref["x"], pr.x_star) + 1e-12
     k = min(got["iters"], ref["iters"], 20)

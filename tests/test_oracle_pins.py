@@ -405,6 +405,58 @@ def test_zero_rhs_and_maxit(oracle):
 
 
 # ---------------------------------------------------------------------------------------
+# Summation order of the dot products: every order is a valid evaluation of PCG
+# ---------------------------------------------------------------------------------------
+def test_dot_orders_within_error_bound(oracle):
+    # every order rounds each product once and adds in binary64: the textbook bound
+    # |computed - exact| <= gamma_n sum |a_i b_i| holds for each; the compensated one is
+    # within 2u |exact| + gamma_n^2 sum |a_i b_i| (Neumaier 1974)
+    rng = np.random.default_rng(21)
+    u = 2.0 ** -53
+    for n in (1, 7, 100, 5000):
+        a = rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 3, n)
+        b = rng.standard_normal(n)
+        exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
+        absum = float(np.sum(np.abs(a * b)))
+        gamma = n * u / (1 - n * u)
+        got = {}
+        old = oracle.set_dot_order(0)
+        try:
+            for order in range(5):
+                oracle.set_dot_order(order)
+                got[order] = oracle.dot(a, b)
+        finally:
+            oracle.set_dot_order(old)
+        for order in range(4):
+            assert abs(Fraction(got[order]) - exact) <= Fraction(gamma * absum * 1.0000001)
+        assert abs(Fraction(got[4]) - exact) <= Fraction(2 * u * abs(float(exact)) + gamma ** 2 * absum * 2)
+        if n == 5000:
+            assert len(set(got.values())) > 1     # the orders really differ
+    # the default order is the plain loop from index 0
+    x = np.array([1e16, 1.0, -1e16, 1.0])
+    assert oracle.dot(x, np.ones(4)) == 1.0
+
+
+@pytest.mark.parametrize("name", ["poisson2d_bs8", "subcube24_bs32", "subcube24_bs64", "aniso27_12_bs64",
+                                  "voronoi24_uneven", "ragged13_bs32"])
+def test_uniform_iteration_band_over_summation_orders(oracle, name):
+    # How far the binary64 BJAC-PCG iteration count moves when only the summation order of the
+    # dot products changes. On the well-conditioned systems every order gives the same count;
+    # on the ill-conditioned 27-point anisotropic system (not an M-matrix, kappa(M^-1 A) large)
+    # the five orders give 326 ... 334. The GPU parity test accepts the band the orders span,
+    # widened by the stated +-2, so its tolerance stays +-2 where the band is one count.
+    import pcg_cases
+    pr = pcg_cases.PROBLEMS[name]()
+    b = oracle.spmv(pr.A, pr.x_star)
+    P = oracle.Preconditioner(pr.A, pr.block_ptr)
+    lo, hi = pcg_cases.uniform_iteration_band(pr, b, P)
+    if name == "aniso27_12_bs64":
+        assert (lo, hi) == (326, 334)
+    else:
+        assert hi - lo == 0
+
+
+# ---------------------------------------------------------------------------------------
 # Multiscale strength (Eq. 4-5) against Tables 4.3 and 4.4
 # ---------------------------------------------------------------------------------------
 def _percent(tau, bins):
@@ -525,6 +577,72 @@ def test_mlp_gradient_central_differences(oracle):
         wm[k] -= h
         num = (oracle.mlp_loss_grad(wp, x, y)[0] - oracle.mlp_loss_grad(wm, x, y)[0]) / (2 * h)
         assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(g[k])) + 1e-8
+
+
+def _mlp_params(W1, b1, W2, b2, W3, b3):
+    """Parameter vector in the oracle's layout W1[64][12] b1 W2[64][64] b2 W3[3][64] b3."""
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+
+
+def test_mlp_forward_hand_computed(oracle):
+    # Integer weights, few nonzeros; every value below is worked out by hand.
+    #   x = (1, -2, 0, ..., 0)
+    #   layer 1 (W1 x + b1, then ReLU):
+    #     unit 0: 1*1 + 1*(-2) + 0   = -1  -> 0   (cut by the ReLU)
+    #     unit 1: 2*1 + 1            =  3  -> 3
+    #     unit 2: -1*(-2) - 1        =  1  -> 1
+    #     unit 3: 0.5*(-2) + 3       =  2  -> 2   (bias before the ReLU: ReLU(-1) + 3 would be 3)
+    #     units 4..63: bias 0        =  0  -> 0
+    #   layer 2 (W2 h1 + b2, then ReLU), W2[out][in]:
+    #     unit 0: 5*h1_0 + 1*h1_1 - 4*h1_2 + 0 = 0 + 3 - 4   = -1 -> 0 (cut)
+    #     unit 1: 1*h1_0 + 2*h1_1 - 1          = 0 + 6 - 1   =  5 -> 5
+    #     unit 2: 3*h1_2 + 1*h1_3 + 0.5        = 3 + 2 + 0.5 = 5.5 -> 5.5
+    #     unit 3: -2*h1_0 + 1*h1_1 + 1*h1_2    = 0 + 3 + 1   =  4 -> 4
+    #     unit 4: 1*h1_3 - 3                   = 2 - 3       = -1 -> 0 (cut)
+    #   logits (W3 h2 + b3):
+    #     0: 7*h2_0 + 1*h2_1 + 2*h2_4 + 0.25 = 0 + 5 + 0 + 0.25 = 5.25
+    #     1: 2*h2_2 - 1*h2_3 - 1             = 11 - 4 - 1        = 6
+    #     2: 1*h2_0 - 1*h2_1 + 1*h2_2 + 1*h2_3 = 0 - 5 + 5.5 + 4  = 4.5
+    # A missing ReLU (layer 1: unit 0 = -1 reaches layer 2; layer 2: units 0, 4 = -1 reach the
+    # logits), a bias added after the ReLU, or W2 / W3 read transposed each change the logits.
+    W1 = np.zeros((64, 12)); b1 = np.zeros(64)
+    W1[0, 0], W1[0, 1] = 1, 1
+    W1[1, 0], b1[1] = 2, 1
+    W1[2, 1], b1[2] = -1, -1
+    W1[3, 1], b1[3] = 0.5, 3
+    W2 = np.zeros((64, 64)); b2 = np.zeros(64)
+    W2[0, 0], W2[0, 1], W2[0, 2] = 5, 1, -4
+    W2[1, 0], W2[1, 1], b2[1] = 1, 2, -1
+    W2[2, 2], W2[2, 3], b2[2] = 3, 1, 0.5
+    W2[3, 0], W2[3, 1], W2[3, 2] = -2, 1, 1
+    W2[4, 3], b2[4] = 1, -3
+    W3 = np.zeros((3, 64)); b3 = np.array([0.25, -1.0, 0.0])
+    W3[0, 0], W3[0, 1], W3[0, 4] = 7, 1, 2
+    W3[1, 2], W3[1, 3] = 2, -1
+    W3[2, 0], W3[2, 1], W3[2, 2], W3[2, 3] = 1, -1, 1, 1
+    w = _mlp_params(W1, b1, W2, b2, W3, b3)
+    x = np.zeros((2, 12))
+    x[0, 0], x[0, 1] = 1, -2
+    # second sample: every input 0, so only the biases act: h1 = ReLU(b1) = (0, 1, 0, 3, 0...),
+    # h2 = ReLU(W2 h1 + b2) = (1, 2 - 1, 3 + 0.5, 1, 3 - 3) = (1, 1, 3.5, 1, 0),
+    # logits = (7 + 1 + 0 + 0.25, 7 - 1 - 1, 1 - 1 + 3.5 + 1) = (8.25, 5, 4.5)
+    got = oracle.mlp_forward(w, x)
+    assert np.array_equal(got, np.array([[5.25, 6.0, 4.5], [8.25, 5.0, 4.5]]))
+
+
+def test_mlp_forward_random_weights_vs_matrix_products(oracle):
+    # the same network written as three matrix products with numpy (ReLU as np.maximum)
+    rng = np.random.default_rng(11)
+    W1, b1 = rng.standard_normal((64, 12)), rng.standard_normal(64)
+    W2, b2 = rng.standard_normal((64, 64)) * 0.2, rng.standard_normal(64)
+    W3, b3 = rng.standard_normal((3, 64)) * 0.2, rng.standard_normal(3)
+    x = rng.standard_normal((40, 12))
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    ref = h2 @ W3.T + b3
+    assert (h1 == 0).any() and (h2 == 0).any()          # the ReLUs act in both layers
+    got = oracle.mlp_forward(_mlp_params(W1, b1, W2, b2, W3, b3), x)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
 def test_mlp_softmax_ce_closed_form(oracle):
