@@ -49,7 +49,10 @@ def parse():
                     help="aMP switching for the headline policy (adp_tol 10 for hl, 1e-5 for lh)")
     ap.add_argument("--flexible", action="store_true", help="flexible-CG beta for the headline policy")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode table")
-    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=16,
+                    help="oracle PCG iterations in the all-core CPU sample (a quarter of them single-threaded)")
+    ap.add_argument("--ref-iters", type=int, default=12,
+                    help="oracle PCG iterations per step of the reference arm (after the full setup)")
     ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
                     help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
     ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell", "sell-pf"],
@@ -552,36 +555,127 @@ def other_configs():
 
 
 # ------------------------------------------------------------------------------------------
-def oracle_sample(args, gpu_iters=None):
-    """The CPU oracle, unchanged, on a bounded sample of the same workload: the full setup
-    (block LU inverses + rounding) and args.cpu_iters PCG iterations, scaled to a whole
-    solve of `gpu_iters` (or the oracle's own count at the reduced sample) iterations."""
+def host_cpu():
+    """(model name, logical cores) of this host: lscpu, else /proc/cpuinfo."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return model or platform.processor() or "unknown", os.cpu_count() or 1
+
+
+def oracle_problem(args):
     import oracle as O
     from paper_2407_15973_gb300 import problems as PB
     pr = PB.make_problem("subcube3d", seed=0, m=args.m, bs=args.bs)
-    b = O.spmv(pr.A, pr.x_star)
-    t0 = time.perf_counter()
-    P = O.Preconditioner(pr.A, pr.block_ptr, fmt=FMT[args.fmt])
-    t_setup = time.perf_counter() - t0
-    k = args.cpu_iters
-    t0 = time.perf_counter()
-    O.pcg(pr.A, P, b, tol=TOL, maxit=k, policy=O.POLICY_FMP, mode=1)
-    t_iter = (time.perf_counter() - t0) / k
-    if gpu_iters:
-        iters = gpu_iters
-    else:     # the oracle's own full-size count (oracle/reference_runs.py), else its sample's count
-        ref = os.path.join(ROOT, "oracle", "full_size_reference.json")
-        key = f"m{args.m}_bs{args.bs}_{args.fmt}"
-        iters = 0
-        if os.path.exists(ref):
-            with open(ref) as f:
-                iters = json.load(f).get(key, {}).get("iters", 0)
-        if not iters:
-            raise SystemExit(f"no oracle iteration count for {key}: run oracle/reference_runs.py")
-    ms = (t_setup + t_iter * iters) * 1e3
-    return {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"full setup ({t_setup:.1f} s) + {k} PCG iterations ({t_iter*1e3:.0f} ms each) of the same "
-                      f"{args.m}^3 system, scaled to {iters} iterations"}
+    return pr, O.spmv(pr.A, pr.x_star)
+
+
+def oracle_iters(args, fallback=None):
+    """The oracle's own iteration count for this system (a whole serial solve run once by
+    oracle/reference_runs.py), else `fallback` (the GPU's count), with the source named."""
+    ref = os.path.join(ROOT, "oracle", "full_size_reference.json")
+    key = f"m{args.m}_bs{args.bs}_{args.fmt}"
+    if os.path.exists(ref):
+        with open(ref) as f:
+            it = json.load(f).get(key, {}).get("iters", 0)
+        if it:
+            return it, "the oracle's own whole solve of this system (oracle/full_size_reference.json)"
+    if fallback:
+        return fallback, "the GPU solve's count (no whole oracle solve recorded for this system)"
+    raise SystemExit(f"no oracle iteration count for {key}: run oracle/reference_runs.py")
+
+
+def oracle_sample(pr, b, args, k, parallel):
+    """The CPU oracle, unchanged, on the bench's own system: its full setup (binary64 LU
+    inverse of every block, rounding to the format) and then k PCG iterations of fMP in the
+    binary32-emulation mode (the GPU's arithmetic), both timed with a wall clock. parallel:
+    the OpenMP build of the same source on every host core (same bits), else the
+    single-threaded checker. Returns (setup seconds, seconds per iteration, threads)."""
+    import oracle as O
+    old = O.use_parallel(parallel)
+    try:
+        threads = O.threads()
+        t0 = time.perf_counter()
+        P = O.Preconditioner(pr.A, pr.block_ptr, fmt=FMT[args.fmt])
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.pcg(pr.A, P, b, tol=TOL, maxit=k, policy=O.POLICY_FMP, mode=1)
+        t_iter = (time.perf_counter() - t0) / k
+    finally:
+        O.use_parallel(old)
+    return t_setup, t_iter, threads
+
+
+def cpu_baseline(args, gpu_iters):
+    """The oracle timed on this host: all cores (the baseline) and one thread, each on a
+    bounded sample (full setup + a few iterations), extrapolated to a whole solve."""
+    model, cores = host_cpu()
+    pr, b = oracle_problem(args)
+    iters, src = oracle_iters(args, gpu_iters)
+    s_all, it_all, thr = oracle_sample(pr, b, args, args.cpu_iters, True)
+    s_one, it_one, _ = oracle_sample(pr, b, args, max(2, args.cpu_iters // 4), False)
+    ms_all = (s_all + it_all * iters) * 1e3
+    ms_one = (s_one + it_one * iters) * 1e3
+    return {"value": round(ms_all, 1), "unit": "ms", "cores": thr, "threads": thr, "host_cores": cores,
+            "cpu_model": model, "kind": "oracle", "extrapolated": True, "timed_iters": args.cpu_iters,
+            "scaled_to_iters": iters, "iters_source": src,
+            "setup_s": round(s_all, 3), "ms_per_iter": round(it_all * 1e3, 2),
+            "sample": f"OpenMP build on {thr} threads: full setup ({s_all:.2f} s) + {args.cpu_iters} fMP PCG "
+                      f"iterations ({it_all * 1e3:.1f} ms each) of the same {args.m}^3 system, timed; "
+                      f"time to solution = setup + {iters} x per-iteration time",
+            "single_thread": {"value": round(ms_one, 1), "threads": 1, "timed_iters": max(2, args.cpu_iters // 4),
+                              "setup_s": round(s_one, 3), "ms_per_iter": round(it_one * 1e3, 2)}}
+
+
+def run_reference(args, world):
+    """The reference arm: the oracle (the paper has no code), OpenMP build on every host core.
+    Each step is a bounded sample, timed (full setup + --ref-iters PCG iterations); the
+    metric is that sample extrapolated to a whole solve (median over the timed steps)."""
+    model, cores = host_cpu()
+    pr, b = oracle_problem(args)
+    iters, src = oracle_iters(args)
+    k = args.ref_iters
+    walls, ttx, setups, per_it = [], [], [], []
+    thr = 1
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s, it, thr = oracle_sample(pr, b, args, k, True)
+        wall = time.perf_counter() - t0
+        if i >= args.warmup:
+            walls.append(wall)
+            setups.append(s)
+            per_it.append(it)
+            ttx.append((s + it * iters) * 1e3)
+    value = statistics.median(ttx)
+    cb = {"value": round(value, 1), "unit": "ms", "cores": thr, "threads": thr, "host_cores": cores,
+          "cpu_model": model, "kind": "oracle", "extrapolated": True, "timed_iters": k, "scaled_to_iters": iters,
+          "iters_source": src, "setup_s": round(statistics.median(setups), 3),
+          "ms_per_iter": round(statistics.median(per_it) * 1e3, 2),
+          "sample": f"each step: OpenMP build on {thr} threads, full setup + {k} fMP PCG iterations of the same "
+                    f"{args.m}^3 system, timed; value = median over steps of setup + {iters} x per-iteration time"}
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(walls) * 1e3, 1),
+            "extrapolated": True, "timed_iters": k, "scaled_to_iters": iters,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (oracle; f32-emulated block apply)", "data": "synthetic (seeded generator, b = A x*)",
+            "config": workload_config(args), "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
@@ -592,13 +686,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = oracle_sample(args)
-        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"], "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle; f32 emulated block apply)",
-                "data": "synthetic", "config": workload_config(args), "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(run_reference(args, world)))
         return
     if world > 1:
         import torch.distributed as tdist
@@ -608,7 +696,7 @@ def main():
     if rank == 0 and world == 1 and not args.profile_iters:
         if not args.no_configs:
             out["other_configs"] = other_configs()
-        out["cpu_baseline"] = oracle_sample(args, out["iters"])
+        out["cpu_baseline"] = cpu_baseline(args, out["iters"])
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

@@ -15,8 +15,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_parallel = False
 
 FP64, FP32, BF16, FP16S = 0, 1, 2, 3
 FMT_BYTES = {FP64: 8, FP32: 4, BF16: 2, FP16S: 2}
@@ -24,15 +26,29 @@ NFEAT = 12
 POLICY_UNIFORM, POLICY_FMP, POLICY_HL, POLICY_LH = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (no FMA contraction) into oracle/_build/liboracle.so."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile oracle.c with gcc (no FMA contraction) into oracle/_build/liboracle.so, the
+    single-threaded checker every test uses, or (parallel=True) liboracle_omp.so, the same
+    source with OpenMP, used only to time the CPU baseline on all host cores."""
+    out = _OUT_OMP if parallel else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        omp = ["-fopenmp"] if parallel else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", *omp,
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.replace(tmp, out)
+    return out
+
+
+def use_parallel(on: bool) -> bool:
+    """Route every following oracle call to the OpenMP build (on) or the single-threaded
+    checker (off, the default). Only the benchmark's CPU-baseline timing turns it on; both
+    builds give the same bits. Returns the previous setting."""
+    global _parallel
+    old = _parallel
+    _parallel = bool(on)
+    return old
 
 
 class Stats(C.Structure):
@@ -42,16 +58,18 @@ class Stats(C.Structure):
 
 
 def lib():
-    global _lib
     with _lock:
+        _lib = _libs.get(_parallel)
         if _lib is None:
-            _lib = C.CDLL(build())
+            _lib = C.CDLL(build(parallel=_parallel))
+            _libs[_parallel] = _lib
             P = C.c_void_p
             i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
             sig = {
                 "orc_spmv": (None, [i32, P, P, P, P, P]),
                 "orc_dot": (f64, [i64, P, P]),
                 "orc_set_dot_order": (i32, [i32]),
+                "orc_threads": (i32, []),
                 "orc_residual": (None, [i32, P, P, P, P, P, P]),
                 "orc_block_inverse": (i32, [i32, P, P, P, i32, P, P, P, P]),
                 "orc_round_f32_bits": (C.c_uint32, [f64]),
@@ -114,6 +132,11 @@ def set_dot_order(order: int) -> int:
     default; 1 reversed; 2 pairwise; 3 1024 strided partials; 4 compensated). Returns the
     previous order. Process-wide: restore it after use."""
     return int(lib().orc_set_dot_order(int(order)))
+
+
+def threads() -> int:
+    """Threads the active build runs its loops on (1 for the single-threaded checker)."""
+    return int(lib().orc_threads())
 
 
 def residual(A, b, x):

@@ -6,8 +6,15 @@
  *
  * Everything here is written for a reader checking it against the paper by eye: plain
  * loops, sequential sums in natural index order, binary64 arithmetic, no blocking, no
- * fusion, no threads. Build flags keep the compiler from contracting a*b+c into an FMA
+ * fusion. Build flags keep the compiler from contracting a*b+c into an FMA
  * (-ffp-contract=off), so every product and every sum is rounded once, in program order.
+ *
+ * Threads: the checker build (liboracle.so, used by every test) is single-threaded. A second
+ * build of this same file with -fopenmp (liboracle_omp.so) serves only as the timed CPU
+ * baseline: the `omp` pragmas below split loops whose iterations are independent (rows of
+ * the SpMV, blocks of the inverse and the apply, entries of the vector updates) across
+ * threads; every row, block and entry is computed exactly as in the serial loop and the dot
+ * products stay sequential, so both builds give the same bits.
  *
  * Paper: "Mixed Precision Block-Jacobi Preconditioner: Algorithms, Performance Evaluation
  * and Feature Analysis" (arXiv 2407.15973).
@@ -33,6 +40,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the loops below run on: 1 in the checker build, the OpenMP team size otherwise. */
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 #define ORC_FP64 0
 #define ORC_FP32 1
 #define ORC_BF16 2
@@ -45,6 +65,7 @@
 /* y = A x; row i sums val[k] * x[colidx[k]] for k = rowptr[i] .. rowptr[i+1]-1 in order. */
 void orc_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
               const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[colidx[k]];
@@ -123,6 +144,7 @@ double orc_dot(int64_t n, const double *a, const double *b) {
 /* r = b - A x (the "true" residual of Section 4.5.1: from the definition, not the recurrence). */
 void orc_residual(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                   const double *b, const double *x, double *r) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[colidx[k]];
@@ -203,11 +225,14 @@ int32_t orc_block_inverse(int32_t n, const int32_t *rowptr, const int32_t *colid
     for (int32_t b = 0; b < nb; ++b)
         if (block_ptr[b + 1] - block_ptr[b] > maxbs) maxbs = block_ptr[b + 1] - block_ptr[b];
     size_t m2 = (size_t)maxbs * maxbs;
+    int32_t bad = 0;
+#pragma omp parallel reduction(+ : bad)
+    {
     double *B = malloc(sizeof(double) * m2);
     double *X = malloc(sizeof(double) * m2);
     double *work = malloc(sizeof(double) * (m2 + maxbs));
     int32_t *perm = malloc(sizeof(int32_t) * (maxbs > 0 ? maxbs : 1));
-    int32_t bad = 0;
+#pragma omp for schedule(dynamic, 64)
     for (int32_t b = 0; b < nb; ++b) {
         int32_t s = block_ptr[b], e = block_ptr[b + 1], bs = e - s;
         double *Gb = G + goff[b];
@@ -231,6 +256,7 @@ int32_t orc_block_inverse(int32_t n, const int32_t *rowptr, const int32_t *colid
                 Gb[(size_t)i * bs + j] = 0.5 * (X[(size_t)i * bs + j] + X[(size_t)j * bs + i]);
     }
     free(B); free(X); free(work); free(perm);
+    }
     return bad;
 }
 
@@ -324,6 +350,7 @@ float orc_block_scale(int32_t fmt, int64_t count, const double *Gb) {
 
 void orc_pack(int32_t nb, const int32_t *block_ptr, const uint8_t *fmt, const double *G,
               const int64_t *goff, uint8_t *pool, const int64_t *qoff, float *scale) {
+#pragma omp parallel for schedule(static)
     for (int32_t b = 0; b < nb; ++b) {
         int32_t bs = block_ptr[b + 1] - block_ptr[b];
         int64_t cnt = (int64_t)bs * bs;
@@ -359,6 +386,11 @@ static double q_entry(const uint8_t *blk, int f, int64_t idx) {
  *           multiplied by s_b in binary32 (a power of two), then widened to binary64. */
 void orc_apply(int32_t nb, const int32_t *block_ptr, const uint8_t *fmt, const uint8_t *pool,
                const int64_t *qoff, const float *scale, const double *r, double *z, int32_t mode) {
+    /* r-hat = ConvertPrecision(r, binary32), each entry rounded once */
+    int32_t n = block_ptr[nb];
+    float *rh = malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; ++i) rh[i] = as_float(orc_round_f32_bits(r[i]));
+#pragma omp parallel for schedule(static)
     for (int32_t b = 0; b < nb; ++b) {
         int32_t s = block_ptr[b], bs = block_ptr[b + 1] - s;
         const uint8_t *blk = pool + qoff[b];
@@ -370,27 +402,25 @@ void orc_apply(int32_t nb, const int32_t *block_ptr, const uint8_t *fmt, const u
                 z[s + i] = acc;
             } else if (mode == 0) {
                 double acc = 0.0;
-                for (int32_t j = 0; j < bs; ++j) {
-                    double rh = (double)as_float(orc_round_f32_bits(r[s + j]));
-                    acc += q_entry(blk, f, (int64_t)i * bs + j) * rh;
-                }
+                for (int32_t j = 0; j < bs; ++j) acc += q_entry(blk, f, (int64_t)i * bs + j) * (double)rh[s + j];
                 z[s + i] = acc * (double)scale[b];
             } else {
                 float acc = 0.0f;
                 for (int32_t j = 0; j < bs; ++j) {
-                    float rh = as_float(orc_round_f32_bits(r[s + j]));
                     float q = (float)q_entry(blk, f, (int64_t)i * bs + j);
-                    acc = fmaf(q, rh, acc);
+                    acc = fmaf(q, rh[s + j], acc);
                 }
                 z[s + i] = (double)(acc * scale[b]);
             }
         }
     }
+    free(rh);
 }
 
 /* z = G r with the binary64 inverses (the uniform / high-precision preconditioner). */
 void orc_apply_fp64(int32_t nb, const int32_t *block_ptr, const double *G, const int64_t *goff,
                     const double *r, double *z) {
+#pragma omp parallel for schedule(static)
     for (int32_t b = 0; b < nb; ++b) {
         int32_t s = block_ptr[b], bs = block_ptr[b + 1] - s;
         const double *Gb = G + goff[b];
@@ -495,14 +525,18 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
         precondition(&P, relres, r, z, st, low_used ? &low_used[k] : NULL);
         double rho = orc_dot(n, r, z);
         if (!(rho > 0.0) || !isfinite(rho)) { status = ORC_BREAKDOWN; break; }
+        #pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; ++i) p[i] = z[i];
         while (k < maxit) {
             orc_spmv(n, rowptr, colidx, val, p, q);
             double sigma = orc_dot(n, p, q);
             if (!(sigma > 0.0) || !isfinite(sigma)) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / sigma;
+            #pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            #pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; ++i) rp[i] = r[i];
+            #pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
             ++k;
             relres = sqrt(orc_dot(n, r, r)) / bnorm;
@@ -515,6 +549,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const d
             if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = ORC_BREAKDOWN; break; }
             double beta = flexible ? flexible_beta(n, z, r, rp, rho) : rho_new / rho;
             if (!isfinite(beta)) { status = ORC_BREAKDOWN; break; }
+            #pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
             rho = rho_new;
         }

@@ -69,6 +69,45 @@ def test_reference_arm_rank0_prints_one_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("diffusion3d-7pt-128^3")
+    # what was timed is stated: a sample per step, extrapolated to a whole solve, on all cores
+    cb = d["cpu_baseline"]
+    assert d["extrapolated"] is True and cb["extrapolated"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["timed_iters"] == cb["timed_iters"] > 0
+    assert d["scaled_to_iters"] == cb["scaled_to_iters"] > 1000
+    assert cb["threads"] == cb["cores"] == os.cpu_count() and cb["cpu_model"]
+    # ms_per_step is the wall time of the sample that ran, far below the extrapolated value
+    assert 0 < d["ms_per_step"] < d["value"]
+    assert abs(d["value"] - (1e3 * cb["setup_s"] + cb["ms_per_iter"] * cb["scaled_to_iters"])) <= 1e-3 * d["value"]
+
+
+def test_openmp_oracle_build_gives_the_checker_bits():
+    # the timing build (OpenMP over rows, blocks and vector entries) against the checker
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle as O
+    from paper_2407_15973_gb300 import problems as PB
+    pr = PB.make_problem("voronoi3d", seed=4, m=14)
+    b = O.spmv(pr.A, pr.x_star)
+    out = {}
+    for par in (False, True):
+        old = O.use_parallel(par)
+        try:
+            assert O.threads() == (os.cpu_count() if par else 1)
+            P = O.Preconditioner(pr.A, pr.block_ptr, fmt=O.BF16)
+            r1 = O.pcg(pr.A, P, b, tol=1e-10, maxit=500, policy=O.POLICY_FMP, mode=1)
+            r0 = O.pcg(pr.A, P, b, tol=1e-10, maxit=500, policy=O.POLICY_UNIFORM)
+            out[par] = (P.G, P.pool, r1["x"], r1["hist"], r0["x"], r0["hist"])
+        finally:
+            O.use_parallel(old)
+    for a, c in zip(out[False], out[True]):
+        assert np.array_equal(a, c)
+
+
+def test_host_cpu_reports_model_and_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    model, cores = bench.host_cpu()
+    assert isinstance(model, str) and model and cores == os.cpu_count()
 
 
 def test_algorithmic_bytes_of_the_128_cube_workload():
