@@ -722,6 +722,15 @@ struct PdlOff {
     ~PdlOff() { pdl_set(false); }
 };
 
+// aMP runs as a speculative application plus a redo (k_apply_spec) when both sets are uniform
+// 32-row blocks (the low one of one format) and no other apply kernel is forced; otherwise the
+// residual update, the application and the flexible beta are separate kernels.
+static bool amp_spec(const bjac_handle *h) {
+    if (h->pol.select == BJAC_SELECT_KT || !h->have_lo || !h->have_hi) return false;
+    if (h->pol.apply_variant != 0 && h->pol.apply_variant != 3) return false;
+    return spec_supported(h->lo, h->hi, h->n);
+}
+
 // One PCG iteration: captured into the body of a device-side while loop, or launched
 // eagerly by the profiler with an event between kernels (ev != nullptr: ev[0..4]).
 // pdl_first: the SpMV may overlap its predecessor kernel (programmatic launch; the later
@@ -753,6 +762,15 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         } else {
             MPB_TRY_RC(launch_kt_apply(kApplyTemporal, use_low ? 1 : 0, false, h->kt, io, h->d_S, cs, launches));
         }
+    } else if (temporal && amp_spec(h)) {
+        // speculative application with the previous set, fused with r -= alpha q, then the
+        // redo that runs only when this residual's relres picked the other set
+        if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
+        ApplyIO io = base_io(h);
+        io.flex = h->pol.flexible;
+        MPB_TRY_RC(launch_apply_spec(kApplySpec, h->lo, h->hi, io, h->d_S, cs));
+        MPB_TRY_RC(launch_apply_spec(kApplyRedo, h->lo, h->hi, io, h->d_S, cs));
+        *launches += 2;
     } else if (temporal) {
         MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
@@ -771,8 +789,9 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         *launches += 1;
     }
     // the fused register kernels sum q.z themselves and finish the flexible beta
-    const bool flex_fused = !kt && !temporal && use_low && lo_uses_tma(h) &&
-                            (h->apply_kind == kApplyKindReg || h->apply_kind == kApplyKindMix);
+    const bool flex_fused = (!kt && !temporal && use_low && lo_uses_tma(h) &&
+                             (h->apply_kind == kApplyKindReg || h->apply_kind == kApplyKindMix)) ||
+                            (temporal && amp_spec(h));
     if (h->pol.flexible && !flex_fused) {
         MPB_TRY_RC(launch_flex_beta(h->n, h->d_q, h->d_z, h->d_part, h->d_S, cs));
         *launches += 1;

@@ -538,6 +538,160 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_mix32(PSet P, ApplyIO io, Solv
 }
 
 // ----------------------------------------------------------------------------------------
+// aMP (Algorithms 3.2 / 3.3) without a separate residual-update kernel. The set of an
+// application depends on the relres of the residual it preconditions, which is known only
+// after a grid-wide sum; so the application after iteration k is made speculatively with the
+// set of the previous application (the choice changes a few times per solve at most), fused
+// with r -= alpha q as in fMP, and the last CTA compares that set with the one the exact
+// relres picks. If they agree, rho and beta are committed; if not, S->redo is raised and the
+// kApplyRedo launch that follows applies the right set to the updated r (the speculative z
+// and rho are discarded). A committed application is the same arithmetic, in the same order,
+// as in the separate kernels. Blocks of 32 rows: the low set of one format (lane i keeps its
+// row of the next block in registers, as in k_apply_reg), the binary64 set by 16-byte pairs.
+// ----------------------------------------------------------------------------------------
+template <typename QT, int MODE, bool FLEX>
+__global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_spec(PSet lo, PSet hi, ApplyIO io,
+                                                                            SolverState *S) {
+    pdl_enter();
+    using Geo = RegGeom<QT, 32>;
+    constexpr int VPR = Geo::kVPR, EPV = Geo::kEPV;
+    constexpr int NV = FLEX ? 3 : 2;
+    constexpr bool SPEC = MODE == kApplySpec;
+    __shared__ __align__(16) float s_rh[kWarps][32];
+    __shared__ __align__(16) double s_r[kWarps][32];
+    __shared__ double s_red[3 * kNT];
+    if (S->state != kRunning) return;
+    if (!SPEC && !S->redo) return;
+    const int use_low = S->use_low;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = lo.nb;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const double alpha = SPEC ? S->alpha : 0.0;
+    const uint64_t pol = vec_policy(S->l2_keep);
+    const double *__restrict__ q = io.q;
+    double *__restrict__ r = io.r_out;
+    double *__restrict__ z = io.z;
+    double rho = 0.0, rr = 0.0, qz = 0.0;
+    if (use_low) {
+        const size_t blk_bytes = (size_t)32 * 32 * sizeof(QT);
+        uint4 qc[VPR], qn[VPR];
+        double rc = 0.0, rn = 0.0, vc = 0.0, vn = 0.0;
+        float sc_c = 1.0f, sc_n = 1.0f;
+        auto load = [&](int blk, uint4 (&qv)[VPR], double &rv, double &qq, float &sc) {
+            const uint4 *base = reinterpret_cast<const uint4 *>(lo.pool + (size_t)blk * blk_bytes);
+#pragma unroll
+            for (int v = 0; v < VPR; ++v) qv[v] = __ldcs(base + (size_t)lane * VPR + v);
+            const size_t row = (size_t)blk * 32 + lane;
+            rv = ld_vec(r + row, pol);
+            if (SPEC || FLEX) qq = ld_vec(q + row, pol);
+            if (sizeof(QT) == 2) sc = __ldg(lo.scale + blk);
+        };
+        if (gw < nb) load(gw, qc, rc, vc, sc_c);
+        for (int blk = gw; blk < nb; blk += nw) {
+            const int nxt = blk + nw;
+            if (nxt < nb) load(nxt, qn, rn, vn, sc_n);
+            const double v = SPEC ? fma(-alpha, vc, rc) : rc;
+            s_rh[warp][lane] = f64_to_f32_rn(v);
+            __syncwarp();
+            const float4 *rh4 = reinterpret_cast<const float4 *>(s_rh[warp]);
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < VPR; ++k) {
+#pragma unroll
+                for (int e4 = 0; e4 < EPV; e4 += 4) {
+                    const float4 r4 = rh4[(k * EPV + e4) >> 2];
+                    acc = fmaf(vec_entry<QT>(qc[k], e4 + 0), r4.x, acc);
+                    acc = fmaf(vec_entry<QT>(qc[k], e4 + 1), r4.y, acc);
+                    acc = fmaf(vec_entry<QT>(qc[k], e4 + 2), r4.z, acc);
+                    acc = fmaf(vec_entry<QT>(qc[k], e4 + 3), r4.w, acc);
+                }
+            }
+            __syncwarp();
+            const size_t row = (size_t)blk * 32 + lane;
+            const double zi = f32_to_f64(acc * sc_c);
+            st_vec(z + row, zi, pol);
+            if (SPEC) {
+                st_vec(r + row, v, pol);
+                rr = fma(v, v, rr);
+            }
+            if (FLEX) qz = fma(vc, zi, qz);
+            rho = fma(v, zi, rho);
+#pragma unroll
+            for (int k = 0; k < VPR; ++k) qc[k] = qn[k];
+            rc = rn;
+            vc = vn;
+            sc_c = sc_n;
+        }
+    } else {
+        for (int blk = gw; blk < nb; blk += nw) {
+            const size_t row = (size_t)blk * 32 + lane;
+            double v = ld_vec(r + row, pol), qi = 0.0;
+            if (SPEC || FLEX) qi = ld_vec(q + row, pol);
+            if (SPEC) v = fma(-alpha, qi, v);
+            s_r[warp][lane] = v;
+            __syncwarp();
+            const uint4 *base = reinterpret_cast<const uint4 *>(hi.pool + __ldg(hi.qoff + blk));
+            const double zi = vec_row_f64(base + (size_t)lane * 16, 16, s_r[warp]);
+            __syncwarp();
+            st_vec(z + row, zi, pol);
+            if (SPEC) {
+                st_vec(r + row, v, pol);
+                rr = fma(v, v, rr);
+            }
+            if (FLEX) qz = fma(qi, zi, qz);
+            rho = fma(v, zi, rho);
+        }
+    }
+    double b[3] = {0.0, 0.0, 0.0};
+    if (FLEX) {
+        const double v3[3] = {rho, rr, qz};
+        cta_sum_to0<kNT, 3>(v3, s_red, b);
+    } else {
+        const double v2[2] = {rho, rr};
+        double b2[2];
+        cta_sum_to0<kNT, 2>(v2, s_red, b2);
+        b[0] = b2[0];
+        b[1] = b2[1];
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) io.part[NV * blockIdx.x + k] = b[k];
+    if (!last_cta(io.ticket)) return;
+    const double t_rho = reduce_partials<kNT>(io.part, gridDim.x, NV, s_red);
+    const double t_rr = SPEC ? reduce_partials<kNT>(io.part + 1, gridDim.x, NV, s_red + kNT) : 0.0;
+    const double t_qz = FLEX ? reduce_partials<kNT>(io.part + 2, gridDim.x, NV, s_red + 2 * kNT) : 0.0;
+    if (threadIdx.x != 0) return;
+    if (SPEC) {
+        // the recurrence residual of this iteration: relres, convergence, the set it picks
+        S->iter += 1;
+        S->x_pending = 1;
+        const double rel = sqrt(t_rr) / S->bnorm;
+        S->relres = rel;
+        S->rr = t_rr;
+        if (S->hist) S->hist[S->iter] = rel;
+        if (!(rel < 1.0e308)) { S->state = kBreakdown; return; }
+        if (rel <= S->tol) { S->state = kConverged; return; }
+        if (S->iter >= S->maxit) { S->state = kMaxit; return; }
+        const int want = choose_low(S, rel);
+        if (want != use_low) {
+            S->use_low = want;
+            S->redo = 1;
+            return;
+        }
+    } else {
+        S->redo = 0;
+    }
+    if (use_low) S->low_applies += 1;
+    else S->high_applies += 1;
+    if (!finite_pos(t_rho)) { S->state = kBreakdown; return; }
+    double beta = t_rho / S->rho;
+    if (FLEX && S->flexible) beta = -S->alpha * t_qz / S->rho;
+    if (!(fabs(beta) < 1.0e308)) { S->state = kBreakdown; return; }
+    S->beta = beta;
+    S->rho_prev = S->rho;
+    S->rho = t_rho;
+}
+
+// ----------------------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------------------
 // resident CTAs of the generic kernel (one wave), at most the blocks' warps
@@ -643,6 +797,49 @@ static int launch_mix_t(const PSet &P, const ApplyIO &io, SolverState *S, cudaSt
 }
 
 bool mix_supported(const PSet &P, int n) { return P.ubs == 32 && (long long)P.nb * 32 == n; }
+
+template <typename QT, int MODE, bool FLEX>
+static int launch_spec_t(const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply_spec<QT, MODE, FLEX>, kNT, 0) != cudaSuccess ||
+            v < 1)
+            v = 1;
+        per_sm = v;
+    }
+    int g = sm_count() * per_sm;
+    const int need = (lo.nb + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    if (g > kMaxGrid) g = kMaxGrid;
+    if (g < 1) g = 1;
+    MPB_CUDA(launch_kernel(k_apply_spec<QT, MODE, FLEX>, g, kNT, 0, st, lo, hi, io, S));
+    return MPBJAC_OK;
+}
+
+template <int MODE, bool FLEX>
+static int launch_spec_mode(const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    switch (lo.ufmt) {
+        case BJAC_FP32: return launch_spec_t<float, MODE, FLEX>(lo, hi, io, S, st);
+        case BJAC_BF16: return launch_spec_t<__nv_bfloat16, MODE, FLEX>(lo, hi, io, S, st);
+        case BJAC_FP16S: return launch_spec_t<__half, MODE, FLEX>(lo, hi, io, S, st);
+        default: return fail(MPBJAC_ERR_UNSUPPORTED, "no speculative aMP apply kernel for this format");
+    }
+}
+
+bool spec_supported(const PSet &lo, const PSet &hi, int n) {
+    return reg_supported(lo, n) && hi.ufmt == BJAC_FP64 && hi.ubs == 32 && (long long)hi.nb * 32 == n;
+}
+
+int launch_apply_spec(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S, cudaStream_t st) {
+    if (mode == kApplySpec)
+        return io.flex ? launch_spec_mode<kApplySpec, true>(lo, hi, io, S, st)
+                       : launch_spec_mode<kApplySpec, false>(lo, hi, io, S, st);
+    if (mode == kApplyRedo)
+        return io.flex ? launch_spec_mode<kApplyRedo, true>(lo, hi, io, S, st)
+                       : launch_spec_mode<kApplyRedo, false>(lo, hi, io, S, st);
+    return fail(MPBJAC_ERR_INVALID_ARG, "launch_apply_spec takes kApplySpec or kApplyRedo");
+}
 
 int launch_apply_mix(int mode, const PSet &P, const ApplyIO &io, SolverState *S, cudaStream_t st) {
     switch (mode) {

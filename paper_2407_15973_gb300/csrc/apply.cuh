@@ -9,6 +9,10 @@ enum ApplyMode {
     kApplyInit = 1,        // PCG start: z = M^-1 r, p = z, rho = r.z (set from S->use_low)
     kApplyTemporal = 2,    // PCG loop, aMP: set from S->use_low; beta = rho_new / rho
     kApplyFused = 3,       // PCG loop: r -= alpha q; z = M^-1 r; r.r, r.z; convergence; beta
+    kApplySpec = 4,        // aMP loop: as kApplyFused with the set of the previous application;
+                           // if this residual's relres picks the other set, S->redo is raised
+                           // and rho / beta are left for the redo
+    kApplyRedo = 5,        // aMP loop: only when S->redo: z = M^-1 r with S->use_low, rho, beta
 };
 
 struct ApplyIO {
@@ -65,6 +69,11 @@ __device__ __forceinline__ void apply_finish(double rho, double rr, const ApplyI
     S->rho_prev = S->rho;
     S->rho = rho;
 }
+
+// aMP's speculative application and its redo (kApplySpec / kApplyRedo) for a low set of
+// uniform 32-row blocks of one format and the binary64 set of the same blocks
+bool spec_supported(const PSet &lo, const PSet &hi, int n);
+int launch_apply_spec(int mode, const PSet &lo, const PSet &hi, const ApplyIO &io, SolverState *S, cudaStream_t st);
 
 bool tma_supported(const PSet &P, int n);
 int prepare_apply_tma(const PSet &P);   // set kernel attributes (call before any capture)

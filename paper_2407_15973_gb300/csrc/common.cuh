@@ -132,6 +132,8 @@ struct SolverState {
     int32_t iter, state, use_low, x_pending;
     int32_t low_applies, high_applies, restarts;
     int32_t flexible;      // flexible-CG beta (set by the host for the solve)
+    int32_t redo;          // aMP: the speculative application used the other set; apply again
+    int32_t pad_;
     unsigned int tickets[8];
 };
 

@@ -96,9 +96,12 @@ def test_amp_limits(B, temporal, adp, limit):
         assert got["high_applies"] == 0
 
 
+# blocks of 64: separate residual-update and apply kernels; blocks of 32: the speculative
+# application with its redo (k_apply_spec)
+@pytest.mark.parametrize("name", ["subcube24_bs64", "subcube24_bs32"])
 @pytest.mark.parametrize("temporal,adp", [(1, 10.0), (1, 1e-4), (2, 1e-5), (2, 1e-2)])
-def test_amp_against_oracle(B, temporal, adp):
-    pr, b, P = _problem("subcube24_bs64")
+def test_amp_against_oracle(B, temporal, adp, name):
+    pr, b, P = _problem(name)
     P.set_formats(O.BF16)
     pol = O.POLICY_HL if temporal == 1 else O.POLICY_LH
     ref = O.pcg(pr.A, P, b, tol=TOL, maxit=3000, policy=pol, adp_tol=adp, mode=1)
@@ -188,3 +191,37 @@ def test_eager_loop_matches_graph(B, temporal):
     assert outs[0]["iters"] == outs[1]["iters"] and outs[0]["converged"] and outs[1]["converged"]
     assert np.array_equal(outs[0]["x"], outs[1]["x"])
     assert outs[1]["graph_launches"] == 0
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+@pytest.mark.parametrize("temporal,adp", [(1, 1e-4), (2, 1e-4), (1, 10.0), (2, 1e-5)])
+def test_amp_speculative_matches_separate_kernels(B, temporal, adp, flexible):
+    # the speculative application (default for 32-row blocks) against the separate residual
+    # update + generic apply (apply_variant 1): the same choice of set at every application and
+    # counts within the +-2 that regrouped partial sums allow
+    pr = PB.make_problem("subcube3d", seed=3, m=64, bs=32)      # 8,192 blocks
+    b = O.spmv(pr.A, pr.x_star)
+    pol = dict(select=B.SELECT_FIXED, fixed_fmt=B.BF16, temporal=temporal, adp_tol=adp, flexible=flexible)
+    spec = _gpu_solve(B, pr, b, hist=True, **pol)
+    sep = _gpu_solve(B, pr, b, hist=True, apply_variant=1, **pol)
+    for got in (spec, sep):
+        assert got["converged"] and got["true_relres"] <= TOL
+        if got["restarts"] == 0:
+            h = got["hist"][:got["iters"]]
+            expect_low = int(np.sum(h < adp)) if temporal == 1 else int(np.sum(h >= adp))
+            assert got["low_applies"] == expect_low
+            assert got["low_applies"] + got["high_applies"] == got["iters"]
+    assert abs(spec["iters"] - sep["iters"]) <= 2
+    k = min(spec["iters"], sep["iters"], 15)
+    assert np.allclose(spec["hist"][:k], sep["hist"][:k], rtol=1e-8)
+
+
+@pytest.mark.parametrize("temporal,adp", [(1, 1e-4), (2, 1e-4)])
+def test_amp_speculative_graph_equals_eager(B, temporal, adp):
+    # the redo launch runs inside the graph's loop as it does from the host: same bits
+    pr, b, P = _problem("subcube24_bs32")
+    pol = dict(select=B.SELECT_FIXED, fixed_fmt=B.BF16, temporal=temporal, adp_tol=adp)
+    g = _gpu_solve(B, pr, b, hist=True, **pol)
+    e = _gpu_solve(B, pr, b, hist=True, graph_mode=1, **pol)
+    assert g["iters"] == e["iters"] and g["low_applies"] == e["low_applies"]
+    assert np.array_equal(g["x"], e["x"]) and np.array_equal(g["hist"], e["hist"])
