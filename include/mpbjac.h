@@ -163,7 +163,8 @@ typedef struct bjac_batch bjac_batch;
 
 /* Set up nsys independent systems A[s] (DEVICE CSR arrays, copied into one block-diagonal
  * matrix owned by the batch) with contiguous blocks block_ptr[s] (HOST, nb[s]+1 entries,
- * every block 1..32 rows). policy: select UNIFORM, FIXED or RULE (no aMP switching);
+ * every block 1..32 rows). policy: select UNIFORM, FIXED, RULE or GIVEN (block_fmt then
+ * names the format of every block of every system, systems in order; no aMP switching);
  * policy.stream is used for every call. The setup also times six variants of the persistent
  * kernel (32- or 64-row work tiles, registers for 2, 4 or 6 CTAs per SM) on this batch
  * (20 iterations each) and keeps the fastest.
@@ -203,7 +204,8 @@ const char *bjac_last_error(void);
 /* ---- the steps of one PCG iteration, callable alone ---------------------------------- */
 
 /* y = A x (DEVICE x, y; n doubles). If xy (DEVICE, nullable) is given, *xy = x . y is
- * written as well (deterministic two-stage reduction). */
+ * written as well (deterministic two-stage reduction). For long rows the kernel stages tiles
+ * with TMA copies under bounded waits; if one expires, *xy and the rows not reached are NaN. */
 int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *stream);
 
 /* Allocation-free y = A x and *xy = x . y, for callers that cannot allocate device memory
@@ -218,7 +220,9 @@ int bjac_spmv(const bjac_csr *A, const double *x, double *y, double *xy, void *s
  * current); make that first call before any stream capture. Every call shares the one buffer
  * and finds there what the previous call left (the ticket counter is cleared each time):
  * calls that overlap on the GPU (other streams, other threads) race and must not be made.
- * Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * Calls no cudaMalloc, cudaFree or allocating library routine. As in bjac_spmv, matrices with
+ * long rows (mean > 8 nonzeros) stage their tiles with TMA copies whose waits are bounded: if
+ * one expires, *xy and the rows the kernel did not reach are NaN (the call itself cannot tell). */
 int bjac_spmv_noalloc(const bjac_csr *A, const double *x, double *y, double *xy, void *stream);
 
 /* r = b - A x and, if rr (DEVICE, nullable) is given, *rr = r . r. */
@@ -283,12 +287,12 @@ int bjac_import_inverse(bjac_handle *h, const double *G);
 int bjac_apply_kernel(const bjac_handle *h, int32_t *kind, float *tune_ms);
 
 /* Process-wide choice of the SpMV kernel for matrices with short rows (mean <= 8 nonzeros):
- * 0 = timed once per matrix shape at setup and the fastest kept (default), 1 = TMA-staged
- * CTA tiles, 2 = warp-cooperative, 3 = software-pipelined warp-cooperative, 4 = per-warp
- * TMA rings, 5 = bjac_spmv and bjac_residual build a SELL-32 copy of A for the call and run
- * the SELL-32 kernel (a test mode: it allocates and synchronises; handles are unaffected).
- * Rows longer on average always use the TMA kernel with large stages. Returns the previous
- * setting, or INVALID_ARG. Not thread-safe. */
+ * 0 = timed once per matrix shape at setup and the faster kept (default), 1 = TMA-staged CTA
+ * tiles, 2 = warp-cooperative, 5 = bjac_spmv and bjac_residual build a SELL-32 copy of A for
+ * the call and run the SELL-32 kernel (a test mode: it allocates and synchronises; handles are
+ * unaffected). Rows longer on average always use the TMA kernel with large stages. Returns
+ * the previous setting, or INVALID_ARG (3 and 4 named kernels that no workload chose and are
+ * no longer built). Not thread-safe. */
 int bjac_spmv_kernel(int32_t variant);
 
 /* Process-wide L2 residency of the PCG vectors in the solver loop: 1 (default) = the loop's
@@ -299,9 +303,8 @@ int bjac_spmv_kernel(int32_t variant);
  * setting, or INVALID_ARG. Not thread-safe. */
 int bjac_l2_residency(int32_t keep);
 
-/* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative, 3 pipelined, 4
- * per-warp TMA) and, if the timing ran for it, the four median times in ms (ms[4], HOST,
- * nullable). */
+/* SpMV kernel that A's shape uses now (1 TMA-staged, 2 warp-cooperative) and, if the timing
+ * ran for it, the two median times in ms (ms[2], HOST, nullable). */
 int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms);
 
 /* ---- the learned selector (training and inference on the GPU) ------------------------ */

@@ -221,6 +221,11 @@ static int choose_apply_kind(bjac_handle *h) {
     if (v == 1 || (!tma_ok && !mix_ok)) { h->apply_kind = kApplyKindGeneric; return MPBJAC_OK; }
     if (v == 2) { h->apply_kind = tma_ok ? kApplyKindTma : kApplyKindGeneric; return MPBJAC_OK; }
     if (v == 3) { h->apply_kind = reg_ok ? kApplyKindReg : tma_ok ? kApplyKindTma : kApplyKindGeneric; return MPBJAC_OK; }
+    // blocks of 32 rows in several formats: the mixed register kernel, without timing (it beat
+    // the generic kernel on every such set timed); on uniform 32-row sets the generic kernel is
+    // not timed either (it lost to both the register and the TMA kernel every time: 49 against
+    // 29 and 33 us for the BF16 set of the 128^3 workload), the other two are
+    if (mix_ok && h->lo.ufmt < 0) { h->apply_kind = kApplyKindMix; return MPBJAC_OK; }
     const TuneKey key{h->lo.ufmt, h->lo.ubs, h->nb};
     for (auto &e : g_tune_cache)
         if (e.first == key) {
@@ -251,8 +256,8 @@ static int choose_apply_kind(bjac_handle *h) {
     constexpr int kRounds = 8;
     float t[4][kRounds] = {};
     auto usable = [&](int k) {
-        return k == kApplyKindGeneric || (k == kApplyKindTma && tma_ok) || (k == kApplyKindReg && reg_ok) ||
-               (k == kApplyKindMix && mix_ok);
+        return (k == kApplyKindGeneric && !reg_ok) || (k == kApplyKindTma && tma_ok) || (k == kApplyKindReg && reg_ok) ||
+               (k == kApplyKindMix && mix_ok && !reg_ok);
     };
     for (int rep = 0; rep < kRounds; ++rep) {
         for (int k = 0; k < 4; ++k) {
@@ -269,7 +274,7 @@ static int choose_apply_kind(bjac_handle *h) {
         }
     }
     float best = 1e30f;
-    int best_kind = kApplyKindGeneric;
+    int best_kind = reg_ok ? kApplyKindReg : kApplyKindGeneric;
     for (int k = 0; k < 4; ++k) {
         if (!usable(k)) continue;
         std::sort(t[k] + 1, t[k] + kRounds);
@@ -927,12 +932,13 @@ extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol,
     SolverState res = *h->h_S;
     int fallback = 0;
     auto status_of = [&](const SolverState &s) {
+        if (s.state == kTimeout) return MPBJAC_ERR_TIMEOUT;
         if (s.state == kBreakdown || s.state == kBreakdownSigma) return MPBJAC_ERR_BREAKDOWN;
         if (s.state == kConverged && s.true_relres <= tol) return MPBJAC_OK;
         return MPBJAC_NOT_CONVERGED;
     };
     int status = status_of(res);
-    if (status != MPBJAC_OK && h->pol.fp64_fallback && h->have_lo && h->have_hi) {
+    if (status != MPBJAC_OK && status != MPBJAC_ERR_TIMEOUT && h->pol.fp64_fallback && h->have_lo && h->have_hi) {
         MPB_CUDA(cudaMemcpyAsync(x, h->d_x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
         rc = run_solve(h, 1, b, x, tol, maxit, relres_hist, &launches);
         if (rc) return rc;
@@ -961,6 +967,7 @@ extern "C" int pcg_solve(bjac_handle *h, const double *b, double *x, double tol,
         stats->setup_ms = h->setup_ms;
         cudaEventElapsedTime(&stats->solve_ms, h->ev0, h->ev1);
     }
+    if (status == MPBJAC_ERR_TIMEOUT) set_error("a bounded wait of a loop kernel expired (a TMA copy did not land)");
     if (status == MPBJAC_ERR_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0 or r.z <= 0 or non-finite)");
     else if (status == MPBJAC_NOT_CONVERGED) set_error("maximum number of iterations reached");
     return status;

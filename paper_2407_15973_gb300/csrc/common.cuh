@@ -113,6 +113,7 @@ enum SolverStateCode : int32_t {
     kMaxit = 2,
     kBreakdown = 3,        // r.z <= 0 or non-finite scalars after the x/r update
     kBreakdownSigma = 4,   // p.Ap <= 0 before the x/r update of this iteration
+    kTimeout = 5,          // a bounded wait of a loop kernel expired (a TMA copy did not land)
 };
 
 struct SolverState {

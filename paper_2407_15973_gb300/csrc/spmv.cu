@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     double acc1 = 0.0, acc2 = 0.0;   // dot / norm partial sums
     int it = 0;
     bool ok = true;
+    int t_fail = ntiles;                 // first tile this CTA did not finish (a wait expired)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int s = it % kStages;
         const unsigned phase = (unsigned)((it / kStages) & 1);
@@ -114,7 +115,11 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
             my_hi = __ldg(rowptr + row + 1);
         }
         ok = mbar_wait_bounded(&full[s], phase);
-        if (__syncthreads_or(!ok)) { ok = false; break; }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            t_fail = t;
+            break;
+        }
         const StageMeta m = meta[s];
         const uint8_t *st = smem + 128 + (size_t)s * kStageBytes;
         const double *sv = reinterpret_cast<const double *>(st) - m.lo4;
@@ -166,7 +171,17 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     }
     __syncthreads();
     if (s_bad) {
-        if (threadIdx.x == 0 && S) S->state = kBreakdown;
+        // the solve stops with TIMEOUT; a standalone call leaves NaN in the dot product and in
+        // every row this CTA did not reach, so the failure cannot pass for a result
+        const double nan = __longlong_as_double(0x7FF8000000000000ll);
+        if (threadIdx.x == 0) {
+            if (S) S->state = kTimeout;
+            else if (out) *out = nan;
+        }
+        for (int t = t_fail; t < ntiles; t += gridDim.x) {
+            const int row = t * RPT + lrow;
+            if (row < n) y[row] = nan;
+        }
         return;
     }
     if (KIND == kSpY) return;
@@ -328,338 +343,20 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
 }
 
 // ----------------------------------------------------------------------------------------
-// software-pipelined warp variant. A warp walks its tiles T_0, T_1, ... (32 rows each) and,
-// in the iteration that sums T_i, it also gathers x for T_{i+1}, loads the values and column
-// indices of T_{i+2} and the row pointers of T_{i+3}. Values and gathered x of a tile are
-// parked in one of two warp-private shared buffers, so the summation touches only shared
-// memory: global-memory latency is hidden by the pipeline rather than by more warps. Tiles
-// with more than 32*K nonzeros are summed straight from global memory.
-// ----------------------------------------------------------------------------------------
-template <int K, int KIND>
-__global__ void __launch_bounds__(kSpNT) k_spmv_pipe(int n, int nnz, const int32_t *__restrict__ rowptr,
-                                                     const int32_t *__restrict__ colidx,
-                                                     const double *__restrict__ val, const double *__restrict__ x,
-                                                     const double *__restrict__ b, double *__restrict__ y,
-                                                     double *part, unsigned int *ticket, double *out, SolverState *S) {
-    pdl_enter();
-    constexpr int CH = 32 * K;
-    constexpr int NW = kSpNT / 32;
-    constexpr bool RES = KIND >= 10;
-    __shared__ double s_v[NW][2][CH];
-    __shared__ double s_x[NW][2][CH];
-    __shared__ double red[2 * kSpNT];
-    if (KIND == kSpPcg) {
-        // the previous iteration's x update is done (stream order): clear its flag even when
-        // this iteration does not run, so a loop body after convergence changes nothing
-        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
-        if (S->state != kRunning) return;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = (n + 31) >> 5;
-    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
-    double acc1 = 0.0, acc2 = 0.0;
-
-    auto rows_of = [&](int tt, int &lo_r, int &hi_r) {
-        const int r = (tt << 5) + lane;
-        if (tt < ntiles) {
-            lo_r = __ldg(rowptr + min(r, n));
-            hi_r = r < n ? __ldg(rowptr + r + 1) : lo_r;
-        } else {
-            lo_r = hi_r = 0;
-        }
-    };
-    // per-stage tile descriptors (row range of this lane, chunk base, end, "big" flag)
-    struct Tile { int my_lo, my_hi, lo, hi; bool big; };
-    auto describe = [&](int mylo, int myhi) {
-        Tile d;
-        d.my_lo = mylo; d.my_hi = myhi;
-        d.lo = __shfl_sync(0xffffffffu, mylo, 0);
-        d.hi = __shfl_sync(0xffffffffu, myhi, 31);
-        d.big = d.hi - d.lo > CH;
-        return d;
-    };
-    double fv[K];       // values of the tile two ahead
-    int32_t fc[K];      // column indices of the tile two ahead
-    int32_t gc[K];      // column indices of the tile one ahead (to gather with)
-    double gx[K];       // gathered x of the tile one ahead
-    auto fetch = [&](const Tile &d) {
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-            const int k = d.lo + lane + 32 * m;
-            const bool in = !d.big && k < d.hi;
-            fv[m] = in ? __ldcs(val + k) : 0.0;
-            fc[m] = in ? __ldcs(colidx + k) : -1;
-        }
-    };
-    // prologue: T_0 fetched and gathered, T_1 fetched, row pointers of T_2 loaded
-    int t = gw;
-    int r_lo, r_hi;
-    rows_of(t, r_lo, r_hi);
-    Tile d0 = describe(r_lo, r_hi);
-    rows_of(t + nw, r_lo, r_hi);
-    Tile d1 = describe(r_lo, r_hi);
-    fetch(d0);
-    int buf = 0;
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        s_v[warp][buf][lane + 32 * m] = fv[m];
-        gc[m] = fc[m];
-    }
-#pragma unroll
-    for (int m = 0; m < K; ++m) gx[m] = gc[m] >= 0 ? __ldg(x + gc[m]) : 0.0;
-    fetch(d1);
-    int p_lo, p_hi;                 // row pointers of T_{i+2}
-    rows_of(t + 2 * nw, p_lo, p_hi);
-    while (t < ntiles) {
-        // row pointers of T_{i+3}
-        int q_lo, q_hi;
-        rows_of(t + 3 * nw, q_lo, q_hi);
-        // park gathered x of T_i; values of T_i were parked one iteration ago
-#pragma unroll
-        for (int m = 0; m < K; ++m) s_x[warp][buf][lane + 32 * m] = gx[m];
-        // values of T_{i+1} into the other buffer, then gather x for T_{i+1}
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-            s_v[warp][buf ^ 1][lane + 32 * m] = fv[m];
-            gc[m] = fc[m];
-        }
-#pragma unroll
-        for (int m = 0; m < K; ++m) gx[m] = gc[m] >= 0 ? __ldg(x + gc[m]) : 0.0;
-        // fetch values / columns of T_{i+2}
-        const Tile d2 = describe(p_lo, p_hi);
-        fetch(d2);
-        __syncwarp();
-        // sum this lane's row of T_i
-        const int row = (t << 5) + lane;
-        double xr = 0.0, bi = 0.0;
-        if (row < n) {
-            if (RES) bi = b[row];
-            else if (KIND != kSpY) xr = __ldg(x + row);
-        }
-        double acc = 0.0;
-        if (!d0.big) {
-            const double *sv = s_v[warp][buf] - d0.lo;
-            const double *sx = s_x[warp][buf] - d0.lo;
-            for (int k = d0.my_lo; k < d0.my_hi; ++k) acc = fma(sv[k], sx[k], acc);
-        } else {
-            for (int k = d0.my_lo; k < d0.my_hi; ++k) acc = fma(__ldg(val + k), __ldg(x + __ldg(colidx + k)), acc);
-        }
-        if (row < n) {
-            if (RES) {
-                const double ri = bi - acc;
-                y[row] = ri;
-                acc1 = fma(ri, ri, acc1);
-                acc2 = fma(bi, bi, acc2);
-            } else {
-                y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
-            }
-        }
-        __syncwarp();
-        // rotate the pipeline
-        t += nw;
-        buf ^= 1;
-        d0 = d1;
-        d1 = d2;
-        p_lo = q_lo;
-        p_hi = q_hi;
-    }
-    if (KIND == kSpY) return;
-    double cs[2] = {0.0, 0.0};     // this CTA's partial sums (valid in thread 0)
-    if (RES) {
-        const double v[2] = {acc1, acc2};
-        cta_sum_to0<kSpNT, 2>(v, red, cs);
-    } else {
-        const double v[1] = {acc1};
-        double c1[1];
-        cta_sum_to0<kSpNT, 1>(v, red, c1);
-        cs[0] = c1[0];
-    }
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = cs[0];
-        part[2 * blockIdx.x + 1] = cs[1];
-    }
-    if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
-    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
-}
-
-// ----------------------------------------------------------------------------------------
-// per-warp TMA variant: every warp owns a ring of WS shared-memory stages; lane 0 streams the
-// values and column indices of the warp's next tiles (32 rows each) into them with
-// cp.async.bulk, WS tiles ahead, so the copy engine (not registers) holds the bytes in
-// flight. Each lane sums its row from the stage, gathering x through L1/L2. A tile that does
-// not fit a stage, or touches the unaligned tail of the arrays, is summed from global memory.
-// ----------------------------------------------------------------------------------------
-constexpr int kWCap = 264;                         // nonzeros per stage (32 rows of 7-point + slack)
-constexpr int kWStages = 4;
-constexpr int kWStageBytes = kWCap * 12;
-constexpr int kWWarps = 16;                        // warps per CTA
-constexpr int kWThreads = kWWarps * 32;
-constexpr int kWSmem = kWWarps * (kWStages * 8 + 16) + kWWarps * kWStages * kWStageBytes;
-
-template <int KIND>
-__global__ void __launch_bounds__(kWThreads) k_spmv_wtma(int n, int nnz, const int32_t *__restrict__ rowptr,
-                                                         const int32_t *__restrict__ colidx,
-                                                         const double *__restrict__ val, const double *__restrict__ x,
-                                                         const double *__restrict__ b, double *__restrict__ y,
-                                                         double *part, unsigned int *ticket, double *out,
-                                                         SolverState *S) {
-    pdl_enter();
-    constexpr bool RES = KIND >= 10;
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_meta[kWWarps][kWStages][2];
-    __shared__ double red[2][kWWarps];
-    __shared__ int s_bad;
-    if (KIND == kSpPcg) {
-        // the previous iteration's x update is done (stream order): clear its flag even when
-        // this iteration does not run, so a loop body after convergence changes nothing
-        if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
-        if (S->state != kRunning) return;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * kWStages;
-    uint8_t *stages = smem + kWWarps * (kWStages * 8 + 16) + (size_t)warp * kWStages * kWStageBytes;
-    const int ntiles = (n + 31) >> 5;
-    const int gw = blockIdx.x * kWWarps + warp, nw = gridDim.x * kWWarps;
-    const int nnz4 = nnz & ~3;
-
-    auto issue = [&](int t, int s) {     // lane 0 only
-        const int r0 = t << 5;
-        const int lo = __ldg(rowptr + r0), hi = __ldg(rowptr + min(r0 + 32, n));
-        const int lo4 = lo & ~3, hi4 = (hi + 3) & ~3;
-        const bool direct = (hi4 - lo4 > kWCap) || (hi4 > nnz4) || (hi4 == lo4);
-        s_meta[warp][s][0] = lo4;
-        s_meta[warp][s][1] = direct ? 1 : 0;
-        uint8_t *dst = stages + (size_t)s * kWStageBytes;
-        if (direct) {
-            mbar_arrive(&bars[s]);
-        } else {
-            const unsigned cnt = (unsigned)(hi4 - lo4);
-            mbar_expect_tx(&bars[s], cnt * 12u);
-            bulk_g2s(dst, val + lo4, cnt * 8u, &bars[s]);
-            bulk_g2s(dst + kWCap * 8, colidx + lo4, cnt * 4u, &bars[s]);
-        }
-    };
-    if (threadIdx.x == 0) s_bad = 0;
-    __syncthreads();
-    if (lane == 0) {
-        for (int s = 0; s < kWStages; ++s) mbar_init(&bars[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int s = 0; s < kWStages; ++s)
-            if (gw + s * nw < ntiles) issue(gw + s * nw, s);
-    }
-    __syncwarp();
-    double acc1 = 0.0, acc2 = 0.0;
-    bool ok = true;
-    int it = 0;
-    for (int t = gw; t < ntiles; t += nw, ++it) {
-        const int s = it % kWStages;
-        const unsigned phase = (unsigned)((it / kWStages) & 1);
-        const int row = (t << 5) + lane;
-        int my_lo = 0, my_hi = 0;
-        double xr = 0.0, bi = 0.0;
-        if (row < n) {
-            my_lo = __ldg(rowptr + row);
-            my_hi = __ldg(rowptr + row + 1);
-            if (RES) bi = b[row];
-            else if (KIND != kSpY) xr = __ldg(x + row);
-        }
-        ok = mbar_wait_bounded(&bars[s], phase);
-        if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
-        const int lo4 = s_meta[warp][s][0];
-        const int direct = s_meta[warp][s][1];
-        const uint8_t *st = stages + (size_t)s * kWStageBytes;
-        const double *sv = reinterpret_cast<const double *>(st) - lo4;
-        const int32_t *sc = reinterpret_cast<const int32_t *>(st + kWCap * 8) - lo4;
-        double acc = 0.0;
-        if (!direct) {
-            for (int k0 = my_lo; k0 < my_hi; k0 += 8) {
-                double xv[8], vv[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const bool in = k0 + j < my_hi;
-                    xv[j] = in ? __ldg(x + sc[k0 + j]) : 0.0;
-                    vv[j] = in ? sv[k0 + j] : 0.0;
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (k0 + j < my_hi) acc = fma(vv[j], xv[j], acc);
-            }
-        } else {
-            for (int k = my_lo; k < my_hi; ++k) acc = fma(__ldg(val + k), __ldg(x + __ldg(colidx + k)), acc);
-        }
-        __syncwarp();     // stage s consumed by every lane
-        if (lane == 0 && t + kWStages * nw < ntiles) issue(t + kWStages * nw, s);
-        if (row < n) {
-            if (RES) {
-                const double ri = bi - acc;
-                y[row] = ri;
-                acc1 = fma(ri, ri, acc1);
-                acc2 = fma(bi, bi, acc2);
-            } else {
-                y[row] = acc;
-                if (KIND != kSpY) acc1 = fma(acc, xr, acc1);
-            }
-        }
-    }
-    if (!ok && lane == 0) {
-        for (int k = 0; k < kWStages; ++k) {
-            const int itk = it + k;
-            if (gw + itk * nw < ntiles) (void)mbar_wait_bounded(&bars[itk % kWStages], (unsigned)((itk / kWStages) & 1));
-        }
-        s_bad = 1;
-    }
-    acc1 = warp_sum(acc1);
-    acc2 = warp_sum(acc2);
-    if (lane == 0) {
-        red[0][warp] = acc1;
-        red[1][warp] = acc2;
-    }
-    __syncthreads();
-    if (s_bad) {
-        if (threadIdx.x == 0 && S) S->state = kBreakdown;
-        return;
-    }
-    if (KIND == kSpY) return;
-    if (threadIdx.x == 0) {
-        double b1 = 0.0, b2 = 0.0;
-        for (int w = 0; w < kWWarps; ++w) {
-            b1 += red[0][w];
-            b2 += red[1][w];
-        }
-        part[2 * blockIdx.x] = b1;
-        part[2 * blockIdx.x + 1] = b2;
-    }
-    if (!last_cta(ticket)) return;
-    double t1 = 0.0, t2 = 0.0;
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < (int)gridDim.x; ++c) {
-            t1 += __ldcg(part + 2 * c);
-            t2 += __ldcg(part + 2 * c + 1);
-        }
-        spmv_finish<KIND>(t1, t2, out, S);
-    }
-}
-
-// ----------------------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------------------
 static bool long_rows(const bjac_csr &A) { return A.n > 0 && (double)A.nnz / A.n > 8.0; }
 
 // SpMV kernel choice per matrix shape, made once by timing (see prepare_spmv)
-enum SpmvVariant { kSpVarTma = 0, kSpVarWarp = 1, kSpVarPipe = 2, kSpVarWtma = 3 };
+enum SpmvVariant { kSpVarTma = 0, kSpVarWarp = 1 };
 struct SpTune {
     int n, nnz, variant;
-    float ms[4];
+    float ms[2];
 };
 static std::vector<SpTune> g_sp_tune;
 
-// 0 timed choice, 1 TMA-staged, 2 warp-cooperative, 3 pipelined warp, 4 per-warp TMA,
-// 5 SELL-32 copy built per call by the standalone entry points (the CSR kernels keep the
-// timed choice)
+// 0 timed choice, 1 TMA-staged, 2 warp-cooperative, 5 SELL-32 copy built per call by the
+// standalone entry points (the CSR kernels keep the timed choice)
 static int g_sp_force = 0;
 bool spmv_forced_sell() { return g_sp_force == 5; }
 
@@ -667,8 +364,6 @@ static int spmv_variant(const bjac_csr &A) {
     if (long_rows(A)) return kSpVarTma;
     if (g_sp_force == 1) return kSpVarTma;
     if (g_sp_force == 2) return kSpVarWarp;
-    if (g_sp_force == 3) return kSpVarPipe;
-    if (g_sp_force == 4) return kSpVarWtma;
     for (const SpTune &t : g_sp_tune)
         if (t.n == A.n && t.nnz == A.nnz) return t.variant;
     return kSpVarWarp;
@@ -718,47 +413,11 @@ static int launch_warp_t(const bjac_csr &A, const double *x, const double *b, do
 }
 
 template <int KIND>
-static int launch_pipe_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
-                         unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmv_pipe<8, KIND>, kSpNT, 0) != cudaSuccess || v < 1)
-            v = 1;
-        per_sm = v;
-    }
-    const int ntiles = (A.n + 31) / 32;
-    int g = sm_count() * per_sm;
-    if (g > kMaxGrid) g = kMaxGrid;
-    const int need = (ntiles + kSpNT / 32 - 1) / (kSpNT / 32);
-    if (g > need) g = need;
-    if (g < 1) g = 1;
-    MPB_CUDA(launch_kernel(k_spmv_pipe<8, KIND>, g, kSpNT, 0, st, A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y, part,
-                           ticket, out, S));
-    return MPBJAC_OK;
-}
-
-template <int KIND>
-static int launch_wtma_t(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
-                         unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
-    const int ntiles = (A.n + 31) / 32;
-    int g = sm_count();                 // one 16-warp CTA per SM (the stages fill its shared memory)
-    const int need = (ntiles + kWWarps - 1) / kWWarps;
-    if (g > need) g = need;
-    if (g < 1) g = 1;
-    MPB_CUDA(launch_kernel(k_spmv_wtma<KIND>, g, kWThreads, kWSmem, st, A.n, A.nnz, A.rowptr, A.colidx, A.val, x, b, y,
-                           part, ticket, out, S));
-    return MPBJAC_OK;
-}
-
-template <int KIND>
 static int launch_kind(const bjac_csr &A, const double *x, const double *b, double *y, double *part,
                        unsigned int *ticket, double *out, SolverState *S, cudaStream_t st) {
     if (long_rows(A)) return launch_t<SpLong, KIND>(A, x, b, y, part, ticket, out, S, st);
     const int v = spmv_variant(A);
     if (v == kSpVarWarp) return launch_warp_t<KIND>(A, x, b, y, part, ticket, out, S, st);
-    if (v == kSpVarPipe) return launch_pipe_t<KIND>(A, x, b, y, part, ticket, out, S, st);
-    if (v == kSpVarWtma) return launch_wtma_t<KIND>(A, x, b, y, part, ticket, out, S, st);
     return launch_t<SpShort, KIND>(A, x, b, y, part, ticket, out, S, st);
 }
 
@@ -775,10 +434,6 @@ int prepare_spmv(const bjac_csr &A) {
         return MPBJAC_OK;
     }
     MPB_ATTRS(SpShort);
-#define MPB_WATTR(K) MPB_CUDA(cudaFuncSetAttribute(k_spmv_wtma<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem))
-    MPB_WATTR(kSpY); MPB_WATTR(kSpYDot); MPB_WATTR(kSpPcg); MPB_WATTR(kResStandalone); MPB_WATTR(kResStart);
-    MPB_WATTR(kResCheck);
-#undef MPB_WATTR
 #undef MPB_ATTRS
 #undef MPB_ATTR
     for (const SpTune &t : g_sp_tune)
@@ -792,23 +447,21 @@ int prepare_spmv(const bjac_csr &A) {
     MPB_CUDA(cudaEventCreate(&e1));
     // interleaved rounds (A B A B ...) so that clock ramps affect both alike; median of 7
     constexpr int kRounds = 8;
-    float t[4][kRounds];
+    float t[2][kRounds];
     for (int rep = 0; rep < kRounds; ++rep) {
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 2; ++v) {
             MPB_CUDA(cudaEventRecord(e0, 0));
-            int rc = v == kSpVarTma    ? launch_t<SpShort, kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0)
-                     : v == kSpVarWarp ? launch_warp_t<kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0)
-                     : v == kSpVarPipe ? launch_pipe_t<kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0)
-                                       : launch_wtma_t<kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0);
+            int rc = v == kSpVarTma ? launch_t<SpShort, kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0)
+                                    : launch_warp_t<kSpY>(A, x, nullptr, y, nullptr, nullptr, nullptr, nullptr, 0);
             if (rc) return rc;
             MPB_CUDA(cudaEventRecord(e1, 0));
             MPB_CUDA(cudaEventSynchronize(e1));
             cudaEventElapsedTime(&t[v][rep], e0, e1);
         }
     }
-    float best[4];
+    float best[2];
     int pick = 0;
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 2; ++v) {
         std::sort(t[v] + 1, t[v] + kRounds);     // round 0 is a warm-up
         best[v] = t[v][1 + (kRounds - 1) / 2];
         if (best[v] < best[pick]) pick = v;
@@ -817,7 +470,7 @@ int prepare_spmv(const bjac_csr &A) {
     cudaEventDestroy(e1);
     cudaFree(x);
     cudaFree(y);
-    g_sp_tune.push_back({A.n, A.nnz, pick, {best[0], best[1], best[2], best[3]}});
+    g_sp_tune.push_back({A.n, A.nnz, pick, {best[0], best[1]}});
     return MPBJAC_OK;
 }
 
@@ -828,12 +481,13 @@ extern "C" int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms) 
     if (variant) *variant = mpbjac::spmv_variant(*A) + 1;
     for (const auto &t : mpbjac::g_sp_tune)
         if (t.n == A->n && t.nnz == A->nnz && ms)
-            for (int i = 0; i < 4; ++i) ms[i] = t.ms[i];
+            for (int i = 0; i < 2; ++i) ms[i] = t.ms[i];
     return MPBJAC_OK;
 }
 
 extern "C" int bjac_spmv_kernel(int32_t variant) {
-    if (variant < 0 || variant > 5) return mpbjac::fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..5");
+    if (variant < 0 || variant > 5 || variant == 3 || variant == 4)
+        return mpbjac::fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 5");
     const int old = mpbjac::g_sp_force;
     mpbjac::g_sp_force = variant;
     return old;

@@ -57,7 +57,7 @@ def test_spmv_integer_exact(B):
     assert host(xy)[0] == float(np.dot(x, ref))    # integers below 2^53: exact in any order
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 5])
 @pytest.mark.parametrize("case", list(SPMV_CASES))
 def test_spmv_parity(B, case, variant):
     A = SPMV_CASES[case]()
@@ -82,13 +82,13 @@ def test_spmv_parity(B, case, variant):
 
 @pytest.mark.parametrize("case", list(SPMV_CASES))
 def test_spmv_layouts_bitwise_equal(B, case):
-    """Every SpMV kernel (four CSR kernels, the SELL-32 copy) sums each row as the same FMA
+    """Every SpMV kernel (two CSR kernels, the SELL-32 copy) sums each row as the same FMA
     chain in CSR order, so all give the same bits."""
     A = SPMV_CASES[case]()
     x = cuda(PB.solution(A.n, 23))
     dA = B.DeviceCSR(A)
     outs = []
-    for variant in (1, 2, 3, 4, 5):
+    for variant in (1, 2, 5):
         y = torch.empty(A.n, dtype=torch.float64, device="cuda")
         old = B.bjac_spmv_kernel(variant)
         try:
@@ -353,7 +353,7 @@ def test_mixed_format_register_apply_bitwise(B, m):
             outs.append(zd)
         finally:
             h.close()
-    assert kinds[:2] == ["mixed", "generic"], kinds
+    assert kinds == ["mixed", "generic", "mixed"], kinds
     for o in outs[1:]:
         assert np.array_equal(outs[0], o, equal_nan=True)
 

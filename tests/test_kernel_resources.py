@@ -24,12 +24,17 @@ LOOP_KERNELS = [
     ("k_apply_regI13__nv_bfloat16Li32ELi3ELb0E", 64),
     ("k_apply_regI6__halfLi32ELi3ELb0E", 64),
     ("k_apply_mix32ILi3ELb0E", 80),
+    ("k_apply_specI13__nv_bfloat16Li4ELb0E", 64),
+    ("k_apply_specI6__halfLi4ELb0E", 64),
     ("k_update_xp", 32),
     ("k_update_r", 32),
     ("k_flex_beta", 32),
 ]
-# kernels known to spill a few bytes (the binary32 register apply holds two 4 KB blocks per warp)
-SPILL_ALLOWED = ("k_apply_regIfLi32E",)
+# kernels known to spill a few bytes: the binary32 register applies hold two 4 KB blocks per
+# warp (k_apply_reg, and the speculative aMP apply, which also holds the binary64 path); the
+# flexible speculative applies keep a third running sum at 64 registers
+SPILL_ALLOWED = ("k_apply_regIfLi32E", "k_apply_specIf", "k_apply_specI13__nv_bfloat16Li4ELb1E",
+                 "k_apply_specI6__halfLi4ELb1E")
 
 
 def _resources(src, tmp):

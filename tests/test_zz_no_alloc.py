@@ -1,4 +1,4 @@
-"""The allocation-free SpMV (bjac_spmv_noalloc) against the ordinary bjac_spmv.
+"""The allocation-free SpMV (bjac_spmv_noalloc) against the ordinary bjac_spmv and the oracle.
 
 bjac_spmv_noalloc exists for callers that cannot allocate device memory while they run
 (a device-memory budget reserved up front, a hard memory cap, or code that must not let
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2407_15973_gb300 import problems as PB
 from gpu_util import cuda, host, need_gpu, spmv_tol
 
@@ -36,12 +37,20 @@ def test_noalloc_matches_bjac_spmv_on_two_calls(case):
     tol_y = spmv_tol(A, host(x))
     yr = host(y_ref)
     dot_ref = host(xy_ref)[0]
+    # the oracle's sequential CSR-order product and dot product of the same x
+    yo = O.spmv(A, host(x))
+    dot_o = O.dot(host(x), yo)
     for _ in range(2):       # the second call finds the first call's leftovers in the buffer
         y = torch.full((A.n,), float("nan"), dtype=torch.float64, device="cuda")
         xy = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
         B.bjac_spmv_noalloc(dA, x, y, xy)
         assert np.max(np.abs(host(y) - yr)) <= tol_y
         assert abs(host(xy)[0] - dot_ref) <= 1e-14 * float(np.sum(np.abs(host(x) * yr)))
+        # each row adds the same products in the same CSR order as the oracle's loop (the GPU
+        # fuses each multiply-add, the oracle rounds the product first), so y is within the
+        # stated 1e-14 of max (|A||x|)_i of the oracle's, and the dot within 1e-14 of sum |x_i y_i|
+        assert np.max(np.abs(host(y) - yo)) <= tol_y
+        assert abs(host(xy)[0] - dot_o) <= 1e-14 * float(np.sum(np.abs(host(x) * yo)))
 
 
 def test_noalloc_rejects_rows_beyond_its_buffer():
