@@ -53,7 +53,7 @@ def parse():
                     help="oracle PCG iterations in the all-core CPU sample (a quarter of them single-threaded)")
     ap.add_argument("--ref-iters", type=int, default=12,
                     help="oracle PCG iterations per step of the reference arm (after the full setup)")
-    ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp", "pipe", "wtma"],
+    ap.add_argument("--spmv-kernel", default="auto", choices=["auto", "tma", "warp"],
                     help="pin the SpMV kernel instead of the timed choice (for profiler runs)")
     ap.add_argument("--spmv-layout", default="auto", choices=["auto", "csr", "sell", "sell-pf"],
                     help="pin the loop SpMV's matrix layout instead of the timed choice")
@@ -203,7 +203,9 @@ def run_ours(args, rank, world, dist):
 
     def step(pol, want_stats=False):
         x.zero_()
-        h = B.bjac_setup(dA, pr.block_ptr, **pol)
+        pol = dict(pol)
+        bp = pol.pop("block_ptr", pr.block_ptr)
+        h = B.bjac_setup(dA, bp, **pol)
         st = h.solve(b, x, tol=TOL, maxit=MAXIT)
         h.close()
         return st
@@ -227,7 +229,7 @@ def run_ours(args, rank, world, dist):
         timed.last_steps = per
         return ms, stats
 
-    spmv_pin = {"auto": 0, "tma": 1, "warp": 2, "pipe": 3, "wtma": 4}[args.spmv_kernel]
+    spmv_pin = {"auto": 0, "tma": 1, "warp": 2}[args.spmv_kernel]
     B.bjac_spmv_kernel(spmv_pin)
     B.bjac_l2_residency(1 if args.l2_residency == "on" else 0)
     apply_pin = {"auto": 0, "generic": 1, "tma": 2, "reg": 3, "mix": 4}[args.apply_kernel]
@@ -277,13 +279,21 @@ def run_ours(args, rank, world, dist):
         table["rule"] = dict(select=B.SELECT_RULE)
         from paper_2407_15973_gb300 import selector as SEL
         if os.path.exists(SEL.DEFAULT_WEIGHTS):
-            table["mlp"] = dict(select=B.SELECT_MLP, mlp_params=SEL.load())
+            table["mlp"] = dict(select=B.SELECT_MLP, mlp_params=SEL.load(), safety_theta=SEL.load_safety_theta())
+        # BASELINE's 128^3 configuration names blocks of 32 and of 64
+        bp64 = PB.uniform_blocks(n, 64)
+        table["uniform-fp64-bs64"] = dict(select=B.SELECT_UNIFORM, block_ptr=bp64)
+        for f in ("fp32", "bf16"):
+            table[f"fmp-{f}-bs64"] = dict(select=B.SELECT_FIXED, fixed_fmt=FMT[f], block_ptr=bp64)
         for name, pol in table.items():
             ms, sts = timed(pol, 2, 1)
             s = sts[-1]
+            bsz = 64 if "block_ptr" in pol else args.bs
+            pbytes = sum(cnt * bsz * bsz * {0: 8, 1: 4, 2: 2, 3: 2}[f] for f, cnt in enumerate(s["blocks_per_fmt"]))
             modes[name] = {"ms": round(ms, 3), "solve_ms": round(s["solve_ms"], 3), "setup_ms": round(s["setup_ms"], 3),
                            "iters": s["iters"], "true_relres": s["true_relres"], "converged": s["converged"],
-                           "blocks_per_fmt": s["blocks_per_fmt"]}
+                           "blocks_per_fmt": s["blocks_per_fmt"], "block_size": bsz,
+                           "precond_bytes": int(pbytes)}
 
     # per-kernel device times of one iteration (eager launches, CUDA events on the stream)
     h = B.bjac_setup(dA, pr.block_ptr, **head)
@@ -309,7 +319,7 @@ def run_ours(args, rank, world, dist):
     spmv_var = {}
     xy = torch.zeros(1, dtype=torch.float64, device="cuda")
     yv = torch.empty(n, dtype=torch.float64, device="cuda")
-    for v, name in ((1, "tma"), (2, "warp"), (3, "pipe"), (4, "wtma")):
+    for v, name in ((1, "tma"), (2, "warp")):
         old = B.bjac_spmv_kernel(v)
         for _ in range(3):
             B.bjac_spmv(dA, xs, yv, xy)
@@ -337,8 +347,7 @@ def run_ours(args, rank, world, dist):
         layout_ms[name] = round(ev0.elapsed_time(ev1) / 20, 5)
     apply_name = {"generic": "k_apply_generic", "tma": "k_apply_tma", "register": "k_apply_reg",
                   "mixed": "k_apply_mix32"}[apply_kernel]
-    csr_name = {"tma": "k_spmv", "warp": "k_spmv_warp", "pipe": "k_spmv_pipe", "wtma": "k_spmv_wtma"}[
-        B.bjac_spmv_tuning(dA)[0]]
+    csr_name = {"tma": "k_spmv", "warp": "k_spmv_warp"}[B.bjac_spmv_tuning(dA)[0]]
     spmv_name = {"sell32": "k_spmv_sell", "sell32-prefetch": "k_spmv_sell_pf"}.get(layout["format"], csr_name)
     kernel_name = {"spmv": spmv_name, "apply": apply_name, "update_xp": "k_update_xp"}[dom]
     roofline = {"kernel": kernel_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -355,7 +364,7 @@ def run_ours(args, rank, world, dist):
                                 "standalone_ms": layout_ms},
                 "spmv_variant_ms": spmv_var,
                 "spmv_kernel": B.bjac_spmv_tuning(dA)[0],
-                "spmv_autotune_ms": dict(zip(("tma", "warp", "pipe", "wtma"),
+                "spmv_autotune_ms": dict(zip(("tma", "warp"),
                                              [round(t, 4) for t in B.bjac_spmv_tuning(dA)[1]])),
                 "apply_autotune_ms": dict(zip(("generic", "tma", "register"), [round(t, 4) for t in tune_ms]))}
 
@@ -428,6 +437,7 @@ def other_configs():
     from paper_2407_15973_gb300 import selector as SEL
     stream = torch.cuda.current_stream()
     params = SEL.load() if os.path.exists(SEL.DEFAULT_WEIGHTS) else None
+    theta_s = SEL.load_safety_theta() if params is not None else 0.5
 
     def timed_step(dA, bp, b, pol):
         x = torch.zeros(dA.n, dtype=torch.float64, device="cuda")
@@ -449,9 +459,11 @@ def other_configs():
             ("aniso27-q1-160^3-lognormal2-z1e4-bs64", "aniso27",
              ("uniform-fp64", "fmp-fp32", "fmp-bf16", "rule", "mlp")),
             ("voronoi7pt-256^3-5mat-1e6-uneven16..128", "voronoi3d",
-             ("uniform-fp64", "fmp-fp32", "rule", "mlp+fp64-fallback"))):
+             ("uniform-fp64", "fmp-fp32", "fmp-bf16", "fmp-fp16s", "rule", "mlp+fp64-fallback")),
+            ("mscore7pt-96^3-rand1e10core-rand1e2-bs32", "mscore3d",
+             ("uniform-fp64", "fmp-fp32", "fmp-bf16", "rule", "mlp", "mlp+fp64-fallback"))):
         t0 = time.time()
-        pr = PB.make_problem(name, seed=0)
+        pr = PB.make_problem(name, seed=0, m=96 if name == "mscore3d" else None)
         gen = time.time() - t0
         dA = B.DeviceCSR(pr.A)
         xs = torch.as_tensor(pr.x_star).cuda()
@@ -460,16 +472,24 @@ def other_configs():
         pols = {"uniform-fp64": dict(select=B.SELECT_UNIFORM),
                 "fmp-fp32": dict(select=B.SELECT_FIXED, fixed_fmt=FMT["fp32"]),
                 "fmp-bf16": dict(select=B.SELECT_FIXED, fixed_fmt=FMT["bf16"]),
+                "fmp-fp16s": dict(select=B.SELECT_FIXED, fixed_fmt=FMT["fp16s"]),
                 "rule": dict(select=B.SELECT_RULE)}
         if params is not None:
-            pols["mlp"] = dict(select=B.SELECT_MLP, mlp_params=params)
-            pols["mlp+fp64-fallback"] = dict(select=B.SELECT_MLP, mlp_params=params, fp64_fallback=True)
+            pols["mlp"] = dict(select=B.SELECT_MLP, mlp_params=params, safety_theta=theta_s)
+            pols["mlp+fp64-fallback"] = dict(select=B.SELECT_MLP, mlp_params=params, safety_theta=theta_s,
+                                             fp64_fallback=True)
         timed_step(dA, pr.block_ptr, b, pols["fmp-fp32"])          # warm-up: autotuners for this shape
         res = {}
+        bsz = np.diff(pr.block_ptr).astype(np.int64)
         for m in modes:
             if m in pols:
                 res[m], x = timed_step(dA, pr.block_ptr, b, pols[m])
                 res[m]["x_rel_err"] = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+                # preconditioner bytes from the formats the setup chose
+                h = B.bjac_setup(dA, pr.block_ptr, **pols[m])
+                fm = h.formats()
+                h.close()
+                res[m]["precond_bytes"] = int(np.sum(bsz * bsz * np.array([8, 4, 2, 2])[fm]))
         base = res.get("uniform-fp64", {}).get("ms")
         out[key] = {"n": pr.A.n, "nnz": pr.A.nnz, "blocks": pr.nb, "generate_s": round(gen, 1),
                     "modes": res,

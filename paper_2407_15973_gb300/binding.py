@@ -159,17 +159,17 @@ def bjac_l2_residency(keep: int) -> int:
 
 
 def bjac_spmv_kernel(variant: int) -> int:
-    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 3: pipelined warp,
-    4: per-warp TMA rings. Returns the old value."""
+    """0: timed choice (default), 1: TMA-staged tiles, 2: warp-cooperative, 5: a SELL-32 copy
+    per standalone call (test mode). Returns the old value."""
     return _check(lib().bjac_spmv_kernel(int(variant)), allow_positive=True)
 
 
 def bjac_spmv_tuning(A: DeviceCSR):
-    """(kernel name in use for A, timed medians in ms for tma / warp / pipe / wtma)."""
+    """(kernel name in use for A, timed medians in ms for tma / warp)."""
     v = C.c_int32()
-    ms = (C.c_float * 4)()
+    ms = (C.c_float * 2)()
     _check(lib().bjac_spmv_tuning(C.byref(A.c), C.byref(v), ms))
-    return {1: "tma", 2: "warp", 3: "pipe", 4: "wtma"}.get(v.value, "tma"), list(ms)
+    return {1: "tma", 2: "warp"}.get(v.value, "tma"), list(ms)
 
 
 def bjac_residual(A: DeviceCSR, b, x, r, rr=None, stream=None):
@@ -294,6 +294,13 @@ class Handle:
                                  G.ctypes.data, feat.ctypes.data))
         return dict(fmt=fmt, scale=scale, qoff=qoff, pool=pool[:pb], G=G[:ge], feat=feat)
 
+    def formats(self):
+        """Format of every block (uint8[nb]) and nothing else."""
+        nb, _, _ = self.info()
+        fmt = np.zeros(nb, np.uint8)
+        _check(lib().bjac_export(self.h, fmt.ctypes.data, None, None, None, None, None))
+        return fmt
+
     def import_inverse(self, G):
         G = np.ascontiguousarray(G, dtype=np.float64)
         _check(lib().bjac_import_inverse(self.h, G.ctypes.data))
@@ -370,7 +377,8 @@ class Batch:
         if rc < 0 and rc != ERR_BREAKDOWN:
             _check(rc)
         return rc, [dict(iters=s.iters, converged=bool(s.converged), status=s.status, restarts=s.restarts,
-                         relres=s.relres, true_relres=s.true_relres, solve_ms=s.solve_ms, setup_ms=s.setup_ms)
+                         relres=s.relres, true_relres=s.true_relres, solve_ms=s.solve_ms, setup_ms=s.setup_ms,
+                         blocks_per_fmt=list(s.blocks_per_fmt))
                     for s in st]
 
 

@@ -820,8 +820,11 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     *out = nullptr;
     if (nsys < 1 || !A || !block_ptr || !nb || !policy) return fail(MPBJAC_ERR_INVALID_ARG, "NULL argument or nsys < 1");
     const bjac_policy &P = *policy;
-    if (P.select != BJAC_SELECT_UNIFORM && P.select != BJAC_SELECT_FIXED && P.select != BJAC_SELECT_RULE)
-        return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes uniform, fixed or rule selection");
+    if (P.select != BJAC_SELECT_UNIFORM && P.select != BJAC_SELECT_FIXED && P.select != BJAC_SELECT_RULE &&
+        P.select != BJAC_SELECT_GIVEN)
+        return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes uniform, fixed, rule or given selection");
+    if (P.select == BJAC_SELECT_GIVEN && !P.block_fmt)
+        return fail(MPBJAC_ERR_INVALID_ARG, "SELECT_GIVEN needs block_fmt (every block of every system)");
     if (P.temporal != BJAC_TEMPORAL_NONE) return fail(MPBJAC_ERR_UNSUPPORTED, "no aMP switching in the batched solver");
     long long n_tot = 0, nnz_tot = 0, nb_tot = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -837,6 +840,9 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         nb_tot += nb[s];
     }
     if (n_tot >= (1ll << 31) || nnz_tot >= (1ll << 31)) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
+    if (P.select == BJAC_SELECT_GIVEN)
+        for (long long k = 0; k < nb_tot; ++k)
+            if (P.block_fmt[k] > BJAC_FP16S) return fail(MPBJAC_ERR_INVALID_ARG, "block_fmt entries must be 0..3");
     bjac_batch *h = new bjac_batch();
     auto bail = [&](int rc) { free_batch(h); return rc; };
     h->nsys = nsys;
@@ -905,7 +911,8 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     std::vector<int64_t> qoff(nb_tot + 1, 0);
     for (long long k = 0; k < nb_tot; ++k) {
         const int64_t bs = bp[k + 1] - bp[k];
-        const int by = P.select == BJAC_SELECT_RULE ? 8 : (ffmt == BJAC_FP64 ? 8 : ffmt == BJAC_FP32 ? 4 : 2);
+        const int by = (P.select == BJAC_SELECT_RULE || P.select == BJAC_SELECT_GIVEN)
+                           ? 8 : (ffmt == BJAC_FP64 ? 8 : ffmt == BJAC_FP32 ? 4 : 2);
         qoff[k + 1] = qoff[k] + ((bs * bs * by + 15) & ~int64_t(15));
     }
     BTRY(cudaMalloc(&h->pool, std::max<int64_t>(16, qoff[nb_tot])));
@@ -925,7 +932,11 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     a.fmt = h->fmt;
     a.scale = h->scale;
     a.qoff = h->qoff;
-    a.pool = h->pool;       // the rule path writes each block in its chosen format at its slot
+    a.pool = h->pool;       // the rule / given paths write each block in its format at its slot
+    if (P.select == BJAC_SELECT_GIVEN) {
+        BTRY(cudaMemcpy(h->fmt, P.block_fmt, nb_tot, cudaMemcpyHostToDevice));
+        a.given = h->fmt;
+    }
     a.feat = h->feat;
     a.kap = h->kap;
     a.status = h->status;

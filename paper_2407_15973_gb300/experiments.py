@@ -10,7 +10,16 @@ binary64 (uniform) against binary32 (fMP, aMP), on one GPU through the C ABI.
   * diagonal-dominance study (Section 4.5.2, Figure 4.8): a_ii += P_diag sum_{j!=i} |a_ij| on
     Diff3D-Dis(1000) (the RHD3D matrices are not available), iter_o = iter_fMP / iter_uniform.
 
-    python -m paper_2407_15973_gb300.experiments [--m 128] [--out experiments.json]
+The same two relationships with the library's own configuration, exact inverses of blocks of
+32 rows stored in binary32, bfloat16 or scaled binary16 (fMP), where they can be seen: with
+BJAC(2, 2) the binary32 set causes no delay on these laws.
+
+  * multiscale study (Section 4.5.1, Eq. 4-5): Diff3D-Rand(s), s = 1e2 ... 1e12, where the
+    largest multiscale strength tau_i grows with s: iter_o per storage format, or the failure
+    (breakdown or no convergence) of the solve.
+  * diagonal-dominance study on Diff3D-Rand(1e10) with P_diag = 0 ... 2.
+
+    python -m paper_2407_15973_gb300.experiments [--m 128] [--m-exact 64] [--out experiments.json]
 """
 from __future__ import annotations
 
@@ -89,17 +98,73 @@ def dominance_study(m):
     return res
 
 
+FORMATS = {"fp32": 1, "bf16": 2, "fp16s": 3}
+
+
+def _solve_exact(A, bs=32, maxit=50000, **pol):
+    dA = B.DeviceCSR(A)
+    xs = torch.as_tensor(PB.solution(A.n, 0)).cuda()
+    b = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    B.bjac_spmv(dA, xs, b)
+    h = B.bjac_setup(dA, PB.uniform_blocks(A.n, bs), **pol)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    st = h.solve(b, x, tol=TOL, maxit=maxit)
+    h.close()
+    return {"iters": st["iters"], "converged": st["converged"], "status": st["status"],
+            "true_relres": st["true_relres"], "solve_ms": round(st["solve_ms"], 2)}
+
+
+def _format_row(A):
+    u = _solve_exact(A, select=B.SELECT_UNIFORM)
+    row = {"uniform": u["iters"], "uniform_converged": u["converged"]}
+    for name, f in FORMATS.items():
+        r = _solve_exact(A, select=B.SELECT_FIXED, fixed_fmt=f, maxit=max(4 * u["iters"], 100))
+        row[name] = {"iters": r["iters"], "converged": r["converged"], "status": r["status"],
+                     "iter_o": round(r["iters"] / u["iters"], 4) if r["converged"] and u["iters"] else None}
+    return row
+
+
+def _tau(A, bs=32):
+    """(max, mean) of log10 tau_i (Eq. 4-5) over the rows, from the library's block features
+    (per block: max and mean of log10 tau_i over its rows; blocks of equal size)."""
+    h = B.bjac_setup(B.DeviceCSR(A), PB.uniform_blocks(A.n, bs), select=B.SELECT_UNIFORM)
+    feat = h.export()["feat"]
+    h.close()
+    return float(feat[:, 6].max()), float(feat[:, 7].mean())
+
+
+def multiscale_study(m, svals=(1e2, 1e4, 1e6, 1e8, 1e10, 1e12)):
+    res = {}
+    for s in svals:
+        A = PB.diff3d(m, "rand", s, 0)
+        row = _format_row(A)
+        mx, mean = _tau(A)
+        row["max_log10_tau"] = round(mx, 2)
+        row["mean_log10_tau"] = round(mean, 2)
+        res[f"rand{s:g}"] = row
+    return res
+
+
+def dominance_study_exact(m, pdvals=(0.0, 0.01, 0.1, 0.5, 1.0, 2.0)):
+    base = PB.diff3d(m, "rand", 1e10, 0)
+    return {f"pdiag{pd:g}": _format_row(PB.diag_boost(base, pd)) for pd in pdvals}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--m", type=int, default=128)
+    ap.add_argument("--m-exact", type=int, default=64)
     ap.add_argument("--out", default="experiments.json")
     a = ap.parse_args()
     B.lib()
     t0 = time.time()
-    out = {"config": {"m": a.m, "blocks": 32, "k": 2, "t": 2, "tol": TOL, "x_star_seed": 0},
+    out = {"config": {"m": a.m, "blocks": 32, "k": 2, "t": 2, "tol": TOL, "x_star_seed": 0,
+                      "m_exact": a.m_exact, "exact_block_rows": 32},
            "adp_tol_table_4_2": adp_tol_study(a.m),
            "anisotropy_figure_4_6": anisotropy_study(a.m),
-           "diagonal_dominance_figure_4_8": dominance_study(a.m)}
+           "diagonal_dominance_figure_4_8": dominance_study(a.m),
+           "multiscale_exact_blocks": multiscale_study(a.m_exact),
+           "diagonal_dominance_exact_blocks": dominance_study_exact(a.m_exact)}
     out["seconds"] = round(time.time() - t0, 1)
     with open(a.out, "w") as f:
         json.dump(out, f, indent=1)

@@ -192,6 +192,19 @@ def diff3d(m: int, kind: str, s: float = 1000.0, seed: int = 0) -> CSR:
     raise ValueError(kind)
 
 
+def multiscale_core(m: int, s_in: float = 1e10, s_out: float = 1e2, seed: int = 0) -> CSR:
+    """7-point diffusion whose coefficient is s^delta with delta iid U[0, 1] per node (the
+    Diff3D-Rand law of Section 4.1.1), s = s_in on the central cube [0.25, 0.75]^3 (the region
+    of the Diff3D-Dis law) and s = s_out elsewhere: a strongly multiscale core (multiscale
+    strength, Eq. 4-5, up to s_in) inside a mildly multiscale rest."""
+    x = (np.arange(m) + 1.0) / (m + 1.0)
+    inside = (x >= 0.25) & (x <= 0.75)
+    cube = inside[:, None, None] & inside[None, :, None] & inside[None, None, :]
+    delta = uniform(seed, 61, m ** 3).reshape(m, m, m)
+    k = np.power(np.where(cube, float(s_in), float(s_out)), delta)
+    return fdm3d_7pt(k, k, k)
+
+
 def diffusion_subcube(m: int = 128, sub: int = 8, lo: float = 1e-3, hi: float = 1e3,
                       dt: float = 1e-2, seed: int = 0) -> CSR:
     """7-point diffusion, coefficient log-uniform in [lo, hi], constant on sub^3 subcubes,
@@ -389,6 +402,8 @@ def make_problem(name: str, seed: int = 0, bs: int | None = None, m: int | None 
     voronoi3d      3D 7-point, 5 materials 10^{0,1.5,3,4.5,6} on 64 Voronoi cells,
                    256^3, uneven material-aligned blocks of 16..128
     diff3d-const / -ani / -dis / -rand   Section 4.1.1 laws at 128^3 (s = 1000)
+    mscore3d       3D 7-point, Rand law with s = 1e10 on the central cube [0.25, 0.75]^3 and
+                   s = 1e2 elsewhere, 128^3, blocks of 32 (the per-block selection workload)
     """
     meta = {}
     if name == "poisson2d":
@@ -412,6 +427,10 @@ def make_problem(name: str, seed: int = 0, bs: int | None = None, m: int | None 
         A = fdm3d_7pt(k, k, k)
         bp = material_blocks(mat) if bs is None else uniform_blocks(A.n, bs)
         meta["material"] = mat
+    elif name == "mscore3d":
+        mm = m or 128
+        A = multiscale_core(mm, 1e10, 1e2, seed)
+        bp = uniform_blocks(A.n, bs or 32)
     elif name.startswith("diff3d-"):
         kind = name.split("-", 1)[1]
         mm = m or 128

@@ -108,3 +108,34 @@ def test_batched_barrier_timeout_reports_and_recovers(B, systems):
         assert rc == 0 and all(s["converged"] and s["true_relres"] <= TOL for s in st)
     finally:
         bt.close()
+
+
+def test_batched_given_formats_match_single_and_oracle(B, systems):
+    # per-block formats named by the caller (every block of every system, in order): the same
+    # systems as the single-system solver with SELECT_GIVEN and the oracle with those formats
+    rng = np.random.default_rng(17)
+    fmts = [rng.integers(0, 4, len(p.block_ptr) - 1).astype(np.uint8) for p in systems]
+    rhs = [O.spmv(p.A, p.x_star) for p in systems]
+    rc, st, xs, info = _solve_batch(B, systems, rhs, select=B.SELECT_GIVEN, block_fmt=np.concatenate(fmts))
+    assert rc == 0
+    for p, b, s, fm in zip(systems, rhs, st, fmts):
+        assert s["converged"] and s["true_relres"] <= TOL
+        assert s["blocks_per_fmt"] == np.bincount(np.concatenate(fmts), minlength=4).tolist()
+        dA = B.DeviceCSR(p.A)
+        h = B.bjac_setup(dA, p.block_ptr, select=B.SELECT_GIVEN, block_fmt=fm)
+        xg = torch.zeros(p.A.n, dtype=torch.float64, device="cuda")
+        sg = h.solve(cuda(b), xg, tol=TOL, maxit=5000)
+        h.close()
+        assert abs(sg["iters"] - s["iters"]) <= max(2, 0.03 * sg["iters"]), (p.name, sg["iters"], s["iters"])
+        P = O.Preconditioner(p.A, p.block_ptr, fmt=fm)
+        ref = O.pcg(p.A, P, b, tol=TOL, maxit=5000, policy=O.POLICY_FMP, mode=1)
+        assert abs(ref["iters"] - s["iters"]) <= max(3, 0.05 * ref["iters"]), (p.name, ref["iters"], s["iters"])
+
+
+def test_batched_given_needs_formats(B, systems):
+    dAs = [B.DeviceCSR(p.A) for p in systems[:2]]
+    with pytest.raises(B.MpbjacError):
+        B.Batch(dAs, [p.block_ptr for p in systems[:2]], select=B.SELECT_GIVEN)
+    bad = np.full(sum(len(p.block_ptr) - 1 for p in systems[:2]), 7, np.uint8)
+    with pytest.raises(B.MpbjacError):
+        B.Batch(dAs, [p.block_ptr for p in systems[:2]], select=B.SELECT_GIVEN, block_fmt=bad)
