@@ -193,6 +193,14 @@ int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, in
  * INVALID_ARG for a NULL batch or on outside {0, 1}. */
 int bjac_batch_force_timeout(bjac_batch *h, int32_t on);
 
+/* Use kernel variant `variant` (0..5, in the order of bjac_batch_info's tune_ms: 32-row tiles
+ * with registers for 2, 4, 6 CTAs per SM, then 64-row tiles likewise) for the batch's next
+ * solves instead of the one the setup's timing chose; rebuilds the work tiles when the tile
+ * height changes. Synchronises the batch's stream. Returns INVALID_ARG for a NULL batch or a
+ * variant outside 0..5. Every variant gives a valid solve; they differ in speed and in the
+ * grouping of the partial sums. */
+int bjac_batch_set_variant(bjac_batch *h, int32_t variant);
+
 void bjac_batch_destroy(bjac_batch *h);
 
 /* Release everything the handle owns (synchronises its stream first). NULL is ignored. */

@@ -89,6 +89,7 @@ def lib():
                 "pcg_solve_batched": (C.c_int, [P, P, P, f64, i32, P]),
                 "bjac_batch_info": (C.c_int, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), P]),
                 "bjac_batch_force_timeout": (C.c_int, [P, i32]),
+                "bjac_batch_set_variant": (C.c_int, [P, i32]),
                 "bjac_batch_destroy": (None, [P]),
                 "bjac_mlp_grad": (C.c_int, [P, i32, P, P, i32, P, P, P]),
                 "bjac_mlp_train": (C.c_int, [P, P, P, i32, i32, C.c_float, P, P]),
@@ -355,6 +356,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_variant(self, variant: int):
+        """Force kernel variant 0..5 (32-row tiles at 2 / 4 / 6 CTAs per SM, then 64-row)."""
+        _check(lib().bjac_batch_set_variant(self.h, int(variant)))
 
     def info(self):
         nt, tr, g = C.c_int32(), C.c_int32(), C.c_int32()

@@ -498,6 +498,7 @@ struct bjac_batch {
     int4 *tinfo = nullptr;          // per-tile descriptions (two int4 each)
     double *sval = nullptr;
     std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
+    std::vector<int32_t> h_bp;      // host copy of the concatenated block offsets
     int grid = 0;
     float tune_ms[6] = {0, 0, 0, 0, 0, 0};   // timings of the kernel variants
     int variant = 0;
@@ -871,6 +872,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         h->sys_row[nsys] = row;
         h->sys_blk[nsys] = blk;
         bp[nb_tot] = row;
+        h->h_bp = bp;
         for (long long k = 0; k < nb_tot; ++k) {
             const int64_t bs = bp[k + 1] - bp[k];
             goff[k + 1] = goff[k] + bs * bs;
@@ -1105,5 +1107,22 @@ extern "C" int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *ti
     if (grid) *grid = h->grid;
     if (tune_ms)
         for (int v = 0; v < kBatchVariants; ++v) tune_ms[v] = h->tune_ms[v];
+    return MPBJAC_OK;
+}
+
+extern "C" int bjac_batch_set_variant(bjac_batch *h, int32_t variant) {
+    if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "batch is NULL");
+    if (variant < 0 || variant >= kBatchVariants) return fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..5");
+    MPB_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    if (kVarTR[variant] != kVarTR[h->variant]) {
+        const int rc = build_tiles(h, kVarTR[variant], h->h_bp);
+        if (rc) return rc;
+    }
+    h->variant = variant;
+    h->grid = max_coresident(variant, h->fp32_only);
     return MPBJAC_OK;
 }

@@ -139,3 +139,65 @@ def test_batched_given_needs_formats(B, systems):
     bad = np.full(sum(len(p.block_ptr) - 1 for p in systems[:2]), 7, np.uint8)
     with pytest.raises(B.MpbjacError):
         B.Batch(dAs, [p.block_ptr for p in systems[:2]], select=B.SELECT_GIVEN, block_fmt=bad)
+
+
+# a batch of the 256-system workload's law whose sides reach 496 and 507 (seed 6: sides 34 ... 507,
+# 912,201 rows), solved with every kernel variant forced
+_big = {}
+
+
+def _big_batch(B):
+    if not _big:
+        systems = PB.batch2d(count=12, seed=6, side_lo=32, side_hi=512)
+        assert max(p.meta["side"] for p in systems) >= 496
+        rhs = [O.spmv(p.A, p.x_star) for p in systems]
+        single = []
+        for p, b in zip(systems, rhs):
+            dA = B.DeviceCSR(p.A)
+            h = B.bjac_setup(dA, p.block_ptr, select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+            xg = torch.zeros(p.A.n, dtype=torch.float64, device="cuda")
+            single.append(h.solve(cuda(b), xg, tol=TOL, maxit=20000)["iters"])
+            h.close()
+        order = np.argsort([p.A.n for p in systems])
+        oracle = {}
+        for i in order[:3]:                      # the three smallest against the oracle
+            p = systems[i]
+            P = O.Preconditioner(p.A, p.block_ptr, fmt=O.FP32)
+            oracle[int(i)] = O.pcg(p.A, P, rhs[i], tol=TOL, maxit=20000, policy=O.POLICY_FMP, mode=1)["iters"]
+        _big.update(systems=systems, rhs=rhs, single=single, oracle=oracle)
+    return _big
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_every_kernel_variant_on_large_sides(B, variant):
+    big = _big_batch(B)
+    systems, rhs = big["systems"], big["rhs"]
+    dAs = [B.DeviceCSR(p.A) for p in systems]
+    bt = B.Batch(dAs, [p.block_ptr for p in systems], select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    try:
+        bt.set_variant(variant)
+        bs = [cuda(b) for b in rhs]
+        xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in systems]
+        rc, st = bt.solve(bs, xs, tol=TOL, maxit=20000)
+        info = bt.info()
+    finally:
+        bt.close()
+    assert rc == 0 and info["tile_rows"] == (32 if variant < 3 else 64)
+    for i, (p, s, x) in enumerate(zip(systems, st, xs)):
+        assert s["converged"] and s["true_relres"] <= TOL, (i, s)
+        assert abs(s["iters"] - big["single"][i]) <= max(2, 0.03 * big["single"][i]), (i, s["iters"], big["single"][i])
+        err = np.linalg.norm(host(x) - p.x_star) / np.linalg.norm(p.x_star)
+        assert err < 1e-5, (i, err)
+    for i, it in big["oracle"].items():
+        assert abs(st[i]["iters"] - it) <= max(3, 0.05 * it), (i, st[i]["iters"], it)
+
+
+def test_set_variant_rejects_bad_values(B, systems):
+    dAs = [B.DeviceCSR(p.A) for p in systems[:2]]
+    bt = B.Batch(dAs, [p.block_ptr for p in systems[:2]], select=B.SELECT_FIXED, fixed_fmt=B.FP32)
+    try:
+        for v in (-1, 6):
+            with pytest.raises(B.MpbjacError):
+                bt.set_variant(v)
+    finally:
+        bt.close()
