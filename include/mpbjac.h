@@ -332,7 +332,12 @@ int bjac_mlp_grad(const float *params, int32_t bf16_weights, const double *feat,
 int bjac_mlp_train(float *params, const double *feat, const int32_t *label, int32_t N, int32_t epochs, float lr,
                    float *loss_hist, void *stream);
 
-/* Logits (HOST, N x 3) of the selector for N feature rows (DEVICE). */
+/* Logits (HOST, N x 3) of the selector for N feature rows (DEVICE). bf16_weights: 1 = weights
+ * rounded to bfloat16 on the tensor cores (tcgen05; the forward pass bjac_setup's
+ * BJAC_SELECT_MLP runs: the 64 x 64 layer as BF16 MMAs with FP32 accumulation, each hidden
+ * value entering as two bfloat16 parts), 2 = the same weights on CUDA cores, 0 = binary32
+ * weights on CUDA cores. Rows of a tile whose MMA did not complete in the bounded wait are NaN.
+ * Returns MPBJAC_ERR_INVALID_ARG for another bf16_weights value. */
 int bjac_mlp_logits(const float *params, int32_t bf16_weights, const double *feat, int32_t N, float *logits,
                     void *stream);
 

@@ -408,10 +408,12 @@ def bjac_mlp_train(params, feat, label, epochs=300, lr=3e-3, stream=None):
     return pr, hist
 
 
-def bjac_mlp_logits(params, feat, bf16_weights=True, stream=None):
+def bjac_mlp_logits(params, feat, bf16_weights=True, tensor_cores=True, stream=None):
+    """Selector logits (N x 3). bfloat16 weights run on the tensor cores (the forward pass the
+    setup uses) unless tensor_cores=False; binary32 weights always run on CUDA cores."""
     _require_cuda(feat)
     pr = np.ascontiguousarray(params, dtype=np.float32)
     out = np.zeros((feat.shape[0], 3), np.float32)
-    _check(lib().bjac_mlp_logits(pr.ctypes.data, int(bool(bf16_weights)), _ptr(feat), feat.shape[0],
-                                 out.ctypes.data, _stream(stream)))
+    mode = (1 if tensor_cores else 2) if bf16_weights else 0
+    _check(lib().bjac_mlp_logits(pr.ctypes.data, mode, _ptr(feat), feat.shape[0], out.ctypes.data, _stream(stream)))
     return out

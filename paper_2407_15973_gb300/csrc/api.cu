@@ -577,6 +577,14 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
             return fail(MPBJAC_ERR_NOT_SPD, "diagonal block " + std::to_string(hstat[1]) +
                                                 " has a non-positive pivot (not positive definite)");
         }
+        if (P.select == BJAC_SELECT_MLP) {
+            for (int b = 0; b < nb; ++b)
+                if (hfmt[b] > BJAC_FP16S) {
+                    free_handle(h);
+                    return fail(MPBJAC_ERR_TIMEOUT, "the selector's tensor-core MMA did not complete (block " +
+                                                        std::to_string(b) + ")");
+                }
+        }
         if (h->have_lo && !fixed_now) {     // per-block formats: compact pool, second pass
             set_qoff(hfmt);
             MPB_TRY(dalloc(&h->d_pool, (size_t)h->pool_bytes));

@@ -316,45 +316,55 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
 // ----------------------------------------------------------------------------------------
 template <typename QT, int BS, int MODE, bool FLEX = false>
 __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet P, ApplyIO io, SolverState *S) {
-    pdl_enter();
     using Geo = RegGeom<QT, BS>;
     constexpr int RPL = Geo::kRPL, VPR = Geo::kVPR, EPV = Geo::kEPV;
     __shared__ __align__(16) float s_rh[kWarps][BS];
     __shared__ double s_red[(MODE == kApplyFused && FLEX ? 3 : 2) * kNT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = P.nb;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const size_t blk_bytes = (size_t)BS * BS * sizeof(QT);
+
+    uint4 qc[RPL][VPR], qn[RPL][VPR];
+    double rc[RPL], rn[RPL], vc[RPL], vn[RPL];
+    float sc_c = 1.0f, sc_n = 1.0f;
+    // the inverse rows of a block (and its scale) do not change during a solve
+    auto load_q = [&](int blk, uint4 (&qv)[RPL][VPR], float &sc) {
+        const uint4 *base = reinterpret_cast<const uint4 *>(P.pool + (size_t)blk * blk_bytes);
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+#pragma unroll
+            for (int v = 0; v < VPR; ++v) qv[h][v] = __ldcs(base + (size_t)(h * 32 + lane) * VPR + v);
+        }
+        if (sizeof(QT) == 2) sc = __ldg(P.scale + blk);
+    };
+    if (gw < nb) load_q(gw, qc, sc_c);       // before the wait: overlaps the predecessor's tail
+    pdl_enter();
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
         if (MODE == kApplyTemporal || MODE == kApplyInit) {
             if (!S->use_low) return;     // the binary64 set runs in the generic kernel
         }
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = P.nb;
-    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
     const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
-    const size_t blk_bytes = (size_t)BS * BS * sizeof(QT);
-
-    uint4 qc[RPL][VPR], qn[RPL][VPR];
-    double rc[RPL], rn[RPL], vc[RPL], vn[RPL];
-    float sc_c = 1.0f, sc_n = 1.0f;
-    auto load = [&](int blk, uint4 (&qv)[RPL][VPR], double (&rv)[RPL], double (&qq)[RPL], float &sc) {
-        const uint4 *base = reinterpret_cast<const uint4 *>(P.pool + (size_t)blk * blk_bytes);
+    auto load_v = [&](int blk, double (&rv)[RPL], double (&qq)[RPL]) {
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {
             const int row = h * 32 + lane;
-#pragma unroll
-            for (int v = 0; v < VPR; ++v) qv[h][v] = __ldcs(base + (size_t)row * VPR + v);
             rv[h] = ld_vec(io.r + (size_t)blk * BS + row, pol);
             if (MODE == kApplyFused) qq[h] = ld_vec(io.q + (size_t)blk * BS + row, pol);
         }
-        if (sizeof(QT) == 2) sc = __ldg(P.scale + blk);
     };
     constexpr bool flex = MODE == kApplyFused && FLEX;
     double rho = 0.0, rr = 0.0, qz = 0.0;     // qz = q.z for the flexible beta
-    if (gw < nb) load(gw, qc, rc, vc, sc_c);
+    if (gw < nb) load_v(gw, rc, vc);
     for (int blk = gw; blk < nb; blk += nw) {
         const int nxt = blk + nw;
-        if (nxt < nb) load(nxt, qn, rn, vn, sc_n);
+        if (nxt < nb) {
+            load_q(nxt, qn, sc_n);
+            load_v(nxt, rn, vn);
+        }
         double rv[RPL];
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {

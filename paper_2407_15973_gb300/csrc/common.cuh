@@ -38,11 +38,18 @@ int sm_count();
 // be scheduled while its predecessor in the stream is still draining. It waits here until
 // that predecessor has completed and its writes are visible, before touching any global
 // memory, and at once lets its own successor be scheduled (the successor waits the same
-// way). Both instructions are no-ops for a kernel launched without the attribute.
+// way). Both instructions are no-ops for a kernel launched without the attribute. Before the
+// wait a kernel may read only what no kernel of the solve writes (the matrix, the block
+// inverses): the predecessor may still be running.
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// bring one 128-byte line into L2 (no register result; a hint the memory system may drop)
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ----------------------------------------------------------------------------------------

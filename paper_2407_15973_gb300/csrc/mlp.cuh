@@ -18,7 +18,12 @@ constexpr int kMlpParams = kOffSd + kFeat;          // + feature mean and standa
 
 // params: HOST floats [kMlpParams]. Writes fmt[b] for every block (class -> format, then
 // promotion until kappa_1 * u_f <= safety_theta).
+// The forward pass runs on the tensor cores (tcgen05); a tile whose MMA does not complete in
+// the bounded wait leaves fmt 0xFF for its blocks (the caller reports a timeout).
 int launch_mlp_select(const float *params, int nb, const double *feat, const double *kap, double safety_theta,
                       uint8_t *fmt, cudaStream_t st);
+// logits[3 n] of the same tensor-core forward pass (dparams: DEVICE floats [kMlpParams]);
+// entries of a tile whose MMA timed out are NaN
+int launch_mlp_logits_tc(const float *dparams, int n, const double *feat, float *logits, cudaStream_t st);
 
 }  // namespace mpbjac

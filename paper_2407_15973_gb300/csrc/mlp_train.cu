@@ -251,7 +251,8 @@ extern "C" int bjac_mlp_train(float *params, const double *feat, const int32_t *
     return MPBJAC_OK;
 }
 
-// Class probabilities of the selector for N feature rows (DEVICE feat, HOST params / out).
+// Logits of the selector for N feature rows on CUDA cores (binary32 or bfloat16-rounded weights);
+// the tensor-core forward pass is in mlp.cu.
 __global__ void k_mlp_logits(const float *params, int bf16, const double *feat, int N, float *out) {
     __shared__ TrainW m;
     for (int t = threadIdx.x; t < kH1 * kFeat; t += blockDim.x) m.w1t[t % kFeat][t / kFeat] = maybe_bf16(params[kOffW1 + t], bf16);
@@ -294,16 +295,22 @@ __global__ void k_mlp_logits(const float *params, int bf16, const double *feat, 
 
 extern "C" int bjac_mlp_logits(const float *params, int32_t bf16_weights, const double *feat, int32_t N, float *logits,
                                void *stream) {
-    if (!params || !feat || !logits || N < 1) return fail(MPBJAC_ERR_INVALID_ARG, "bad MLP inference arguments");
+    if (!params || !feat || !logits || N < 1 || bf16_weights < 0 || bf16_weights > 2)
+        return fail(MPBJAC_ERR_INVALID_ARG, "bad MLP inference arguments");
     cudaStream_t st = (cudaStream_t)stream;
     float *dp = nullptr, *dout = nullptr;
     MPB_CUDA(cudaMallocAsync((void **)&dp, sizeof(float) * kMlpParams, st));
     MPB_CUDA(cudaMallocAsync((void **)&dout, sizeof(float) * (size_t)N * kCls, st));
     MPB_CUDA(cudaMemcpyAsync(dp, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
-    int g = (N + 7) / 8;
-    if (g > sm_count() * 4) g = sm_count() * 4;
-    k_mlp_logits<<<g, 256, 0, st>>>(dp, bf16_weights, feat, N, dout);
-    MPB_CUDA(cudaGetLastError());
+    if (bf16_weights == 1) {
+        const int rc = launch_mlp_logits_tc(dp, N, feat, dout, st);
+        if (rc != MPBJAC_OK) return rc;
+    } else {
+        int g = (N + 7) / 8;
+        if (g > sm_count() * 4) g = sm_count() * 4;
+        k_mlp_logits<<<g, 256, 0, st>>>(dp, bf16_weights ? 1 : 0, feat, N, dout);
+        MPB_CUDA(cudaGetLastError());
+    }
     MPB_CUDA(cudaMemcpyAsync(logits, dout, sizeof(float) * (size_t)N * kCls, cudaMemcpyDeviceToHost, st));
     MPB_CUDA(cudaStreamSynchronize(st));
     cudaFreeAsync(dp, st);

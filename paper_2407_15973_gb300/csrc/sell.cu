@@ -148,10 +148,23 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
                                                        const double *__restrict__ x, const double *__restrict__ b,
                                                        double *__restrict__ y, double *part, unsigned int *ticket,
                                                        double *out, SolverState *S) {
-    pdl_enter();
     constexpr int NW = kSpNT / 32;
     constexpr bool RES = KIND >= 10;
     __shared__ double red[2 * kSpNT];
+    {
+        // the warp's first slice of A (values, then columns) into L2 while the predecessor drains
+        const int s0 = blockIdx.x * NW + (threadIdx.x >> 5), ln = threadIdx.x & 31;
+        if (s0 < nslices) {
+            const int o0 = __ldg(off + s0);
+            const int len = (__ldg(off + s0 + 1) - o0) >> 5;
+            const int nvl = 2 * len, ncl = len;          // 128-byte lines: 16 values, 32 columns
+            for (int l = ln; l < nvl + ncl; l += 32) {
+                if (l < nvl) prefetch_l2(val + o0 + 16 * l);
+                else prefetch_l2(col + o0 + 32 * (l - nvl));
+            }
+        }
+    }
+    pdl_enter();
     if (KIND == kSpPcg) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
@@ -229,10 +242,15 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
                                                           const double *__restrict__ x, const double *__restrict__ b,
                                                           double *__restrict__ y, double *part, unsigned int *ticket,
                                                           double *out, SolverState *S) {
-    pdl_enter();
     constexpr int NW = kSpNT / 32;
     constexpr bool RES = KIND >= 10;
     __shared__ double red[2 * kSpNT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
+    double nv[8];
+    int nc[8], n_o0, n_len;
+    sell_head(gw, nslices, lane, off, col, val, nv, nc, n_o0, n_len);   // A only: before the wait
+    pdl_enter();
     if (KIND == kSpPcg) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
@@ -240,12 +258,7 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
         if (S->state != kRunning) return;
     }
     const uint64_t pol = vec_policy(KIND == kSpPcg ? S->l2_keep : 0);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
     double acc1 = 0.0, acc2 = 0.0;
-    double nv[8];
-    int nc[8], n_o0, n_len;
-    sell_head(gw, nslices, lane, off, col, val, nv, nc, n_o0, n_len);
     for (int s = gw; s < nslices; s += nw) {
         double cv[8];
         int cc[8];

@@ -68,6 +68,33 @@ def test_logits_match_oracle(B):
     assert np.max(np.abs(out16 - ref16)) <= 1e-5 * max(1.0, np.abs(ref16).max())
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 200_003])
+def test_tensor_core_logits(B, n):
+    # the tcgen05 forward pass (bfloat16 weights; 128-sample tiles, a ragged last tile, and at
+    # 200,003 rows several tiles per CTA) against the oracle's binary64 forward pass with the same
+    # rounded weights, and against the CUDA-core kernel. Dropping the low bfloat16 part of the
+    # hidden values would leave a relative error near 2^-9, far above the bound.
+    rng = np.random.default_rng(n)
+    feat, params, _ = _data(7, n=max(n, 300))
+    feat = feat[rng.permutation(len(feat))[:n]] if n <= len(feat) else feat
+    feat = np.ascontiguousarray(feat[:n])
+    out = B.bjac_mlp_logits(params, cuda(feat))
+    ref = O.mlp_forward(_bf16(params[:5187]), _xin(feat, params))
+    assert np.all(np.isfinite(out))
+    assert np.max(np.abs(out - ref)) <= 1e-5 * max(1.0, np.abs(ref).max())
+    cc = B.bjac_mlp_logits(params, cuda(feat), tensor_cores=False)
+    assert np.max(np.abs(out - cc)) <= 1e-5 * max(1.0, np.abs(cc).max())
+
+
+def test_logits_rejects_unknown_mode(B):
+    feat, params, _ = _data(3)
+    dfeat = cuda(feat)
+    out = np.zeros(3 * len(feat), np.float32)
+    for mode in (-1, 3):
+        rc = B.lib().bjac_mlp_logits(params.ctypes.data, mode, dfeat.data_ptr(), len(feat), out.ctypes.data, None)
+        assert rc == B.ERR_INVALID_ARG
+
+
 def test_training_learns_a_separable_rule(B):
     rng = np.random.default_rng(9)
     feat = rng.standard_normal((2000, 12))

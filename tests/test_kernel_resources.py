@@ -29,6 +29,7 @@ LOOP_KERNELS = [
     ("k_update_xp", 32),
     ("k_update_r", 32),
     ("k_flex_beta", 32),
+    ("k_mlp_tc", 128),      # the selector's tensor-core forward pass: 4 CTAs of 128 threads per SM
 ]
 # kernels known to spill a few bytes: the binary32 register applies hold two 4 KB blocks per
 # warp (k_apply_reg, and the speculative aMP apply, which also holds the binary64 path); the
@@ -63,8 +64,8 @@ def _resources(src, tmp):
 @pytest.fixture(scope="module")
 def resources(tmp_path_factory):
     tmp = str(tmp_path_factory.mktemp("ptxas"))
-    with cf.ThreadPoolExecutor(3) as ex:
-        parts = list(ex.map(lambda s: _resources(s, tmp), ["sell.cu", "apply.cu", "update.cu"]))
+    with cf.ThreadPoolExecutor(4) as ex:
+        parts = list(ex.map(lambda s: _resources(s, tmp), ["sell.cu", "apply.cu", "update.cu", "mlp.cu"]))
     res = {}
     for p in parts:
         res.update(p)
