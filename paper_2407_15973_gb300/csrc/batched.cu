@@ -68,6 +68,7 @@ struct BatchDev {
     // barrier and control
     unsigned int *bar_count, *bar_gen;
     int32_t *err, *active;
+    int32_t *changed;            // a system left the running state this iteration: rebuild the list
     int32_t bar_extra;           // arrivals a barrier waits for beyond the grid (0; 1 = forced timeout)
 };
 
@@ -292,14 +293,35 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             ti = tin;
         }
     };
-    // List of the tiles whose system is running, appended (in any order) to list `sl`, whose
-    // length must be zero. A grid barrier must follow before the list is read. The list not in
-    // use has its length cleared in phase B, after the last read of its old contents.
+    // List of the tiles whose system is running, appended to list `sl`, whose length must be
+    // zero. Each CTA scans a contiguous range of tiles and reserves room for all it keeps with
+    // one atomic per 256 tiles (the ranges land in any order). A grid barrier must follow before
+    // the list is read. The list not in use has its length cleared in phase B, after the last
+    // read of its old contents.
+    __shared__ int s_wcnt[kWarps];
+    __shared__ int s_lbase;
     auto build_list = [&](int sl) {
-        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-        for (int t = tid; t < d.ntiles; t += nthr)
-            if (__ldcg(d.state + d.tile_sys[t]) == kRunning)
-                d.alist[(size_t)sl * d.ntiles + atomicAdd(d.nlist + sl, 1)] = t;
+        const int per = (d.ntiles + gridDim.x - 1) / gridDim.x;
+        const int c0 = blockIdx.x * per, c1 = min(d.ntiles, c0 + per);
+        for (int t0 = c0; t0 < c1; t0 += kNT) {
+            const int t = t0 + threadIdx.x;
+            const bool keep = t < c1 && __ldcg(d.state + d.tile_sys[t]) == kRunning;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcnt[warp] = __popc(m);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    const int c = s_wcnt[w];
+                    s_wcnt[w] = tot;
+                    tot += c;
+                }
+                s_lbase = tot > 0 ? atomicAdd(d.nlist + sl, tot) : 0;
+            }
+            __syncthreads();
+            if (keep) d.alist[(size_t)sl * d.ntiles + s_lbase + s_wcnt[warp] + __popc(m & ((1u << lane) - 1u))] = t;
+            __syncthreads();
+        }
     };
     // Fixed-order sums of system s's tile partials by the whole CTA (every thread of the CTA
     // must call it; the results are valid in every thread). One CTA per system keeps the
@@ -373,7 +395,8 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
 
         // ---- iterations --------------------------------------------------------------
         while (*((volatile int32_t *)d.active) != 0) {
-            // A: q = A p, p.q
+            // A: q = A p, p.q (the previous iteration's list decision has been read)
+            if (blockIdx.x == 0 && threadIdx.x == 0) *d.changed = 0;
             per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
                 tile_spmv<TR>(d, ti, d.p, 0, a, b2);
             });
@@ -385,8 +408,12 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
                 if (__ldcg(d.state + s) != kRunning) continue;
                 const double sigma = sys_sum(s);
                 if (threadIdx.x == 0) {
-                    if (!finite_pos(sigma)) d.state[s] = kBreakdownSigma;
-                    else d.alpha[s] = d.rho[s] / sigma;
+                    if (!finite_pos(sigma)) {
+                        d.state[s] = kBreakdownSigma;
+                        atomicOr(d.changed, 1);
+                    } else {
+                        d.alpha[s] = d.rho[s] / sigma;
+                    }
                 }
             }
             if (!grid_barrier(d)) return;
@@ -417,25 +444,44 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
                         d.rho[s] = rz;
                         my_active = 1;
                     }
+                    if (!my_active) atomicOr(d.changed, 1);
                 }
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) *d.active = 0;
             if (!grid_barrier(d)) return;
             if (threadIdx.x == 0 && my_active) atomicOr(d.active, 1);
-            // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped)
+            // the list changes only when a system stopped (B or D of this iteration)
+            const bool rebuild = __ldcg(d.changed) != 0;
+            // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped);
+            // all loads of the tile's rows before its stores
             per_listed(slot, false, [&](int, const TileInfo &ti, double &, double &) {
                 const int s = ti.sys;
                 const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
                 if (!xp && !run) return;
                 const double al = __ldcg(d.alpha + s), be = __ldcg(d.beta + s);
-                for (int row = ti.r0 + lane; row < ti.r1; row += 32) {
-                    const double pi = d.p[row];
-                    if (xp) d.x[row] = fma(al, pi, d.x[row]);
-                    if (run) d.p[row] = fma(be, pi, d.z[row]);
+                double pv[TR / 32], xv[TR / 32], zv[TR / 32];
+#pragma unroll
+                for (int h = 0; h < TR / 32; ++h) {
+                    const int row = ti.r0 + h * 32 + lane;
+                    if (row < ti.r1) {
+                        pv[h] = d.p[row];
+                        xv[h] = xp ? d.x[row] : 0.0;
+                        zv[h] = run ? d.z[row] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < TR / 32; ++h) {
+                    const int row = ti.r0 + h * 32 + lane;
+                    if (row < ti.r1) {
+                        if (xp) d.x[row] = fma(al, pv[h], xv[h]);
+                        if (run) d.p[row] = fma(be, pv[h], zv[h]);
+                    }
                 }
             });
-            slot ^= 1;
-            build_list(slot);
+            if (rebuild) {
+                slot ^= 1;
+                build_list(slot);
+            }
             if (!grid_barrier(d)) return;
         }
         for (int s = blockIdx.x; s < d.nsys; s += gridDim.x)
@@ -580,6 +626,7 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     d.active = reinterpret_cast<int32_t *>(h->ctl + 3);
     d.bar_extra = h->force_timeout ? 1 : 0;
     d.nlist = reinterpret_cast<int32_t *>(h->ctl + 4);
+    d.changed = reinterpret_cast<int32_t *>(h->ctl + 6);
     d.soff = h->soff;
     d.tinfo = h->tinfo;
     d.scol = h->scol;
@@ -788,7 +835,7 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
 
 static int run_batched(bjac_batch *h, double tol, int maxit, cudaStream_t st, bool use_graph) {
     BatchDev d = batch_dev(h, tol, maxit);
-    MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned int), st));
+    MPB_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(unsigned int), st));
     if (!use_graph) return launch_batched(h->variant, h->fp32_only, d, st, h->grid);
     if (!h->exec || h->tol_cached != tol || h->maxit_cached != maxit || h->force_cached != h->force_timeout) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -961,7 +1008,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
     BTRY(cudaMalloc(&h->q, sizeof(double) * n_tot));
     BTRY(cudaMalloc(&h->sd, sizeof(double) * 6 * nsys));
     BTRY(cudaMalloc(&h->si, sizeof(int32_t) * 4 * nsys));
-    BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 6));
+    BTRY(cudaMalloc(&h->ctl, sizeof(unsigned int) * 8));
     BTRY(cudaMalloc(&h->d_sys_tile, sizeof(int32_t) * (nsys + 1)));
     // autotuner: tile height (32 or 64 rows per warp task) and CTAs per SM (2, 4, 6: the
     // register budget of the kernel) timed on 20 iterations of this batch; the choice is kept
