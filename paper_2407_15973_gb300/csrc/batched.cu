@@ -112,27 +112,41 @@ __device__ __forceinline__ TileInfo load_tile(const BatchDev &d, int t) {
     return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
 
-// U entries of one sliced-ELLPACK row: loads, then gathers, then the FMA chain in order
+// U entries of one sliced-ELLPACK row (U = the slice's stored length, or a chunk of it: the
+// same in every lane): loads, then gathers, then the FMA chain in order (padding skipped)
 template <int U>
-__device__ __forceinline__ void ell_part(const double *__restrict__ pv, const int32_t *__restrict__ pc, int cnt,
+__device__ __forceinline__ void ell_part(const double *__restrict__ pv, const int32_t *__restrict__ pc,
                                          const double *xin, double &acc) {
     double v[U], xv[U];
     int c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (u < cnt) {
-            v[u] = __ldcs(pv + 32 * u);
-            c[u] = __ldcs(pc + 32 * u);
-        } else {
-            v[u] = 0.0;
-            c[u] = -1;
-        }
+        v[u] = __ldcs(pv + 32 * u);
+        c[u] = __ldcs(pc + 32 * u);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldcg(xin + c[u]) : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+}
+
+// a slice row of stored length len: chunks of 8, then the exact remainder, so that no FMA is
+// issued for entries past the slice's length
+__device__ __forceinline__ void ell_row(const double *__restrict__ pv, const int32_t *__restrict__ pc, int len,
+                                        const double *xin, double &acc) {
+    int j = 0;
+    for (; j + 8 <= len; j += 8) ell_part<8>(pv + 32 * j, pc + 32 * j, xin, acc);
+    switch (len - j) {
+        case 1: ell_part<1>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 2: ell_part<2>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 3: ell_part<3>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 4: ell_part<4>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 5: ell_part<5>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 6: ell_part<6>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        case 7: ell_part<7>(pv + 32 * j, pc + 32 * j, xin, acc); break;
+        default: break;
+    }
 }
 
 // q or r rows of a tile: each lane owns one row of each of the tile's 32-row slices
@@ -150,7 +164,7 @@ __device__ __forceinline__ void tile_spmv(const BatchDev &d, const TileInfo &ti,
         const double *pv = d.sval + o0 + lane;
         const int32_t *pc = d.scol + o0 + lane;
         double acc = 0.0;
-        for (int j = 0; j < len; j += 8) ell_part<8>(pv + 32 * j, pc + 32 * j, len - j, xin, acc);
+        ell_row(pv, pc, len, xin, acc);
         if (row >= ti.r1) continue;
         if (mode == 0) {
             d.q[row] = acc;
