@@ -165,10 +165,11 @@ typedef struct bjac_batch bjac_batch;
  * matrix owned by the batch) with contiguous blocks block_ptr[s] (HOST, nb[s]+1 entries,
  * every block 1..32 rows). policy: select UNIFORM, FIXED, RULE or GIVEN (block_fmt then
  * names the format of every block of every system, systems in order; no aMP switching);
- * policy.stream is used for every call. The setup also times six variants of the persistent
- * kernel (32- or 64-row work tiles, registers for 2, 4 or 6 CTAs per SM) on this batch
- * (20 iterations each) and keeps the fastest.
- * Errors: INVALID_ARG, UNSUPPORTED, NOT_SPD, CUDA, NO_MEMORY. */
+ * policy.stream is used for every call. The setup also times eight variants of the
+ * persistent kernel (32- or 64-row work tiles with registers for 2, 4 or 6 CTAs per SM,
+ * 128-row tiles for 4 or 6) on this batch (20 iterations each) and keeps the fastest.
+ * Errors: INVALID_ARG, UNSUPPORTED (also for a row of more than 65535 entries), NOT_SPD,
+ * CUDA, NO_MEMORY. */
 int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *const *block_ptr, const int32_t *nb,
                      const bjac_policy *policy, bjac_batch **out);
 
@@ -182,8 +183,9 @@ int pcg_solve_batched(bjac_batch *h, const double *const *b, double *const *x, d
                       pcg_stats *stats);
 
 /* Work tiles, tile height chosen by the setup's timing, grid size and the timings of the
- * six kernel variants (tune_ms[6]: 32-row tiles with registers for 2, 4, 6 CTAs per SM, then
- * 64-row tiles likewise) of a batch. All outputs HOST and nullable. */
+ * eight kernel variants (tune_ms[8]: 32-row tiles with registers for 2, 4, 6 CTAs per SM,
+ * 64-row tiles likewise, then 128-row tiles for 4 and 6) of a batch. All outputs HOST and
+ * nullable. */
 int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, int32_t *grid, float *tune_ms);
 
 /* Failure-path test hook: with on = 1, the grid barriers of the batch's next solves wait for
@@ -193,12 +195,11 @@ int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *tile_rows, in
  * INVALID_ARG for a NULL batch or on outside {0, 1}. */
 int bjac_batch_force_timeout(bjac_batch *h, int32_t on);
 
-/* Use kernel variant `variant` (0..5, in the order of bjac_batch_info's tune_ms: 32-row tiles
- * with registers for 2, 4, 6 CTAs per SM, then 64-row tiles likewise) for the batch's next
- * solves instead of the one the setup's timing chose; rebuilds the work tiles when the tile
- * height changes. Synchronises the batch's stream. Returns INVALID_ARG for a NULL batch or a
- * variant outside 0..5. Every variant gives a valid solve; they differ in speed and in the
- * grouping of the partial sums. */
+/* Use kernel variant `variant` (0..7, in the order of bjac_batch_info's tune_ms) for the
+ * batch's next solves instead of the one the setup's timing chose; rebuilds the work tiles
+ * when the tile height changes. Synchronises the batch's stream. Returns INVALID_ARG for a
+ * NULL batch or a variant outside 0..7. Every variant gives a valid solve; they differ in
+ * speed and in the grouping of the partial sums. */
 int bjac_batch_set_variant(bjac_batch *h, int32_t variant);
 
 void bjac_batch_destroy(bjac_batch *h);

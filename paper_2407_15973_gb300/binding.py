@@ -358,12 +358,13 @@ class Batch:
             pass
 
     def set_variant(self, variant: int):
-        """Force kernel variant 0..5 (32-row tiles at 2 / 4 / 6 CTAs per SM, then 64-row)."""
+        """Force kernel variant 0..7 (32- and 64-row tiles at 2 / 4 / 6 CTAs per SM, then 128-row
+        tiles at 4 / 6)."""
         _check(lib().bjac_batch_set_variant(self.h, int(variant)))
 
     def info(self):
         nt, tr, g = C.c_int32(), C.c_int32(), C.c_int32()
-        ms = (C.c_float * 6)()
+        ms = (C.c_float * 8)()
         _check(lib().bjac_batch_info(self.h, C.byref(nt), C.byref(tr), C.byref(g), ms))
         return dict(ntiles=nt.value, tile_rows=tr.value, grid=g.value, tune_ms=list(ms))
 

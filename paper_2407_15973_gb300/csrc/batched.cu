@@ -51,7 +51,7 @@ struct BatchDev {
     const int32_t *tile_blk;     // [ntiles] first block of each tile
     const int32_t *sys_tile;     // [nsys+1] first tile of each system
     const int4 *tinfo;           // [2 * ntiles] per tile: r0, r1, system, first block, common
-                                 // block size (0 if mixed), slice offsets so0, so1, so2
+                                 // block size (0 if mixed), first stored entry, slice lengths
     const int32_t *soff;         // [ntiles * TR/32 + 1] first stored entry of each 32-row slice
     const int32_t *scol;         // sliced-ELLPACK column indices (-1: padding)
     const double *sval;          // sliced-ELLPACK values
@@ -102,10 +102,17 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &d) {
     return s_ok != 0;
 }
 
-// a tile's description, read with two 16-byte loads
+// a tile's description, read with two 16-byte loads: rows [r0, r1), system, first block,
+// common block size (0 if mixed), the first stored entry of its first 32-row slice and the
+// stored lengths of its (up to four) slices as 16-bit fields (slice k's entries follow slice
+// k-1's: 32 x length each)
 struct TileInfo {
-    int r0, r1, sys, blk0, ubs, so0, so1, so2;
+    int r0, r1, sys, blk0, ubs, so0, len01, len23;
 };
+__device__ __forceinline__ int slice_len(const TileInfo &ti, int h) {
+    const int w = h < 2 ? ti.len01 : ti.len23;
+    return (h & 1) ? (int)((unsigned)w >> 16) : (w & 0xFFFF);
+}
 
 __device__ __forceinline__ TileInfo load_tile(const BatchDev &d, int t) {
     const int4 a = __ldg(d.tinfo + 2 * t), b = __ldg(d.tinfo + 2 * t + 1);
@@ -155,14 +162,15 @@ __device__ __forceinline__ void tile_spmv(const BatchDev &d, const TileInfo &ti,
                                           double &part_a, double &part_b) {
     // mode 0: q = A p, part_a += p.q ; mode 1: r = b - A x, part_a += r.r, part_b += b.b
     const int lane = threadIdx.x & 31;
+    int o0 = ti.so0;
 #pragma unroll 1
     for (int h = 0; h < TR / 32; ++h) {
         if (ti.r0 + h * 32 >= ti.r1) break;              // same in every lane
         const int row = ti.r0 + h * 32 + lane;
-        const int o0 = h == 0 ? ti.so0 : ti.so1;
-        const int len = ((h == 0 ? ti.so1 : ti.so2) - o0) >> 5;
+        const int len = slice_len(ti, h);
         const double *pv = d.sval + o0 + lane;
         const int32_t *pc = d.scol + o0 + lane;
+        o0 += 32 * len;
         double acc = 0.0;
         ell_row(pv, pc, len, xin, acc);
         if (row >= ti.r1) continue;
@@ -284,8 +292,10 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         }
     };
     // the same per-tile work over the list of running tiles (built by build_list); the next
-    // listed tile's description is loaded while the current one is processed
-    auto per_listed = [&](int cnt_slot, bool partials, auto &&fn) {
+    // listed tile's description is loaded while the current one is processed. partials: how
+    // many per-tile sums the phase keeps (0, 1: a, 2: a and b2); each costs a warp tree of
+    // five FP64 adds per tile, so a phase sums only what it uses.
+    auto per_listed = [&](int cnt_slot, int partials, auto &&fn) {
         const int cnt = __ldcg(d.nlist + cnt_slot);
         const int32_t *lst = d.alist + (size_t)cnt_slot * d.ntiles;
         int t = gw < cnt ? __ldcg(lst + gw) : 0;
@@ -295,12 +305,12 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             const TileInfo tin = load_tile(d, tn);
             double a = 0.0, b2 = 0.0;
             fn(t, ti, a, b2);
-            if (partials) {
+            if (partials > 0) {
                 a = warp_sum(a);
-                b2 = warp_sum(b2);
+                if (partials > 1) b2 = warp_sum(b2);
                 if (lane == 0) {
                     d.part[2 * t] = a;
-                    d.part[2 * t + 1] = b2;
+                    if (partials > 1) d.part[2 * t + 1] = b2;
                 }
             }
             t = tn;
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         while (*((volatile int32_t *)d.active) != 0) {
             // A: q = A p, p.q (the previous iteration's list decision has been read)
             if (blockIdx.x == 0 && threadIdx.x == 0) *d.changed = 0;
-            per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
+            per_listed(slot, 1, [&](int, const TileInfo &ti, double &a, double &b2) {
                 tile_spmv<TR>(d, ti, d.p, 0, a, b2);
             });
             if (!grid_barrier(d)) return;
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
             if (!grid_barrier(d)) return;
             // C: r -= alpha q, z = M^-1 r, r.r and r.z
-            per_listed(slot, true, [&](int, const TileInfo &ti, double &a, double &b2) {
+            per_listed(slot, 2, [&](int, const TileInfo &ti, double &a, double &b2) {
                 if (__ldcg(d.state + ti.sys) != kRunning) return;     // sigma broke down in B
                 tile_apply<TR, FMT>(d, ti, __ldcg(d.alpha + ti.sys), 1, 0, s_rh[warp], s_r[warp], a, b2);
             });
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             const bool rebuild = __ldcg(d.changed) != 0;
             // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped);
             // all loads of the tile's rows before its stores
-            per_listed(slot, false, [&](int, const TileInfo &ti, double &, double &) {
+            per_listed(slot, 0, [&](int, const TileInfo &ti, double &, double &) {
                 const int s = ti.sys;
                 const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
                 if (!xp && !run) return;
@@ -560,7 +570,7 @@ struct bjac_batch {
     std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
     std::vector<int32_t> h_bp;      // host copy of the concatenated block offsets
     int grid = 0;
-    float tune_ms[6] = {0, 0, 0, 0, 0, 0};   // timings of the kernel variants
+    float tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // timings of the kernel variants
     int variant = 0;
     bool fp32_only = false;                  // every block binary32: the kernels for that format
     cudaGraph_t graph = nullptr;
@@ -652,9 +662,9 @@ static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
 // kernel variants the setup times: tile height x CTAs per SM the registers are sized for; a
 // batch whose blocks are all binary32 (the usual batched format) also gets kernels compiled for
 // that format alone, which need fewer registers
-constexpr int kBatchVariants = 6;
-constexpr int kVarTR[kBatchVariants] = {32, 32, 32, 64, 64, 64};
-[[maybe_unused]] constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6};   // as instantiated below
+constexpr int kBatchVariants = 8;
+constexpr int kVarTR[kBatchVariants] = {32, 32, 32, 64, 64, 64, 128, 128};
+[[maybe_unused]] constexpr int kVarMinB[kBatchVariants] = {2, 4, 6, 2, 4, 6, 4, 6};   // as instantiated below
 
 template <int TR, int MINB, int FMT>
 static int launch_batched_t(const BatchDev &d, cudaStream_t st, int grid) {
@@ -680,7 +690,9 @@ static int launch_batched_f(int variant, const BatchDev &d, cudaStream_t st, int
         case 2: return launch_batched_t<32, 6, FMT>(d, st, grid);
         case 3: return launch_batched_t<64, 2, FMT>(d, st, grid);
         case 4: return launch_batched_t<64, 4, FMT>(d, st, grid);
-        default: return launch_batched_t<64, 6, FMT>(d, st, grid);
+        case 5: return launch_batched_t<64, 6, FMT>(d, st, grid);
+        case 6: return launch_batched_t<128, 4, FMT>(d, st, grid);
+        default: return launch_batched_t<128, 6, FMT>(d, st, grid);
     }
 }
 
@@ -705,7 +717,9 @@ static int per_sm_f(int variant) {
         case 2: return per_sm_of<32, 6, FMT>();
         case 3: return per_sm_of<64, 2, FMT>();
         case 4: return per_sm_of<64, 4, FMT>();
-        default: return per_sm_of<64, 6, FMT>();
+        case 5: return per_sm_of<64, 6, FMT>();
+        case 6: return per_sm_of<128, 4, FMT>();
+        default: return per_sm_of<128, 6, FMT>();
     }
 }
 
@@ -792,7 +806,7 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
     // sliced-ELLPACK copy of every tile (32-row slices padded to their longest row)
     const int spt = tr / 32;
     const size_t nsl = (size_t)h->ntiles * spt;
-    std::vector<int32_t> so(nsl + 1);
+    std::vector<int32_t> so(nsl + 1), slen(nsl, 0);
     long long acc = 0;
     for (int t = 0; t < h->ntiles; ++t) {
         for (int hh = 0; hh < spt; ++hh) {
@@ -800,6 +814,8 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
             const int r0 = trow[t] + 32 * hh, r1 = std::min(trow[t + 1], r0 + 32);
             int len = 0;
             for (int row = r0; row < r1; ++row) len = std::max(len, h->h_rowptr[row + 1] - h->h_rowptr[row]);
+            if (len > 0xFFFF) return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes rows of at most 65535 entries");
+            slen[(size_t)t * spt + hh] = len;
             acc += 32ll * len;
             if (acc > (long long)INT32_MAX - 64) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
         }
@@ -818,8 +834,9 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
             if (bp[k + 1] - bp[k] != ubs) ubs = 0;
         e[4] = ubs;
         e[5] = so[(size_t)t * spt];
-        e[6] = so[(size_t)t * spt + 1];
-        e[7] = spt > 1 ? so[(size_t)t * spt + 2] : e[6];
+        auto ln = [&](int k) { return k < spt ? slen[(size_t)t * spt + k] : 0; };
+        e[6] = (int32_t)((uint32_t)ln(0) | ((uint32_t)ln(1) << 16));
+        e[7] = (int32_t)((uint32_t)ln(2) | ((uint32_t)ln(3) << 16));
     }
     cudaFree(h->tinfo);
     h->tinfo = nullptr;
@@ -1173,7 +1190,7 @@ extern "C" int bjac_batch_info(const bjac_batch *h, int32_t *ntiles, int32_t *ti
 
 extern "C" int bjac_batch_set_variant(bjac_batch *h, int32_t variant) {
     if (!h) return fail(MPBJAC_ERR_INVALID_ARG, "batch is NULL");
-    if (variant < 0 || variant >= kBatchVariants) return fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..5");
+    if (variant < 0 || variant >= kBatchVariants) return fail(MPBJAC_ERR_INVALID_ARG, "variant must be 0..7");
     MPB_CUDA(cudaStreamSynchronize(h->stream));
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);

@@ -168,7 +168,7 @@ def _big_batch(B):
     return _big
 
 
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(8))
 def test_every_kernel_variant_on_large_sides(B, variant):
     big = _big_batch(B)
     systems, rhs = big["systems"], big["rhs"]
@@ -182,7 +182,7 @@ def test_every_kernel_variant_on_large_sides(B, variant):
         info = bt.info()
     finally:
         bt.close()
-    assert rc == 0 and info["tile_rows"] == (32 if variant < 3 else 64)
+    assert rc == 0 and info["tile_rows"] == (32 if variant < 3 else 64 if variant < 6 else 128)
     for i, (p, s, x) in enumerate(zip(systems, st, xs)):
         assert s["converged"] and s["true_relres"] <= TOL, (i, s)
         assert abs(s["iters"] - big["single"][i]) <= max(2, 0.03 * big["single"][i]), (i, s["iters"], big["single"][i])
@@ -196,7 +196,7 @@ def test_set_variant_rejects_bad_values(B, systems):
     dAs = [B.DeviceCSR(p.A) for p in systems[:2]]
     bt = B.Batch(dAs, [p.block_ptr for p in systems[:2]], select=B.SELECT_FIXED, fixed_fmt=B.FP32)
     try:
-        for v in (-1, 6):
+        for v in (-1, 8):
             with pytest.raises(B.MpbjacError):
                 bt.set_variant(v)
     finally:
