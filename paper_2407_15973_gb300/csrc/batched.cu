@@ -442,8 +442,10 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             }
             if (!grid_barrier(d)) return;
             // C: r -= alpha q, z = M^-1 r, r.r and r.z
+            // (no per-tile state test: a system whose sigma broke down in B keeps a stale alpha
+            // here, and its r, z and partial sums are never read again, so the tile's loads
+            // need not wait for the state)
             per_listed(slot, 2, [&](int, const TileInfo &ti, double &a, double &b2) {
-                if (__ldcg(d.state + ti.sys) != kRunning) return;     // sigma broke down in B
                 tile_apply<TR, FMT>(d, ti, __ldcg(d.alpha + ti.sys), 1, 0, s_rh[warp], s_r[warp], a, b2);
             });
             if (!grid_barrier(d)) return;
@@ -478,21 +480,21 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
             const bool rebuild = __ldcg(d.changed) != 0;
             // E: x += alpha p, p = z + beta p (the list still holds the systems D just stopped);
             // all loads of the tile's rows before its stores
+            // (the rows are loaded together with the system's flags and scalars, not after them)
             per_listed(slot, 0, [&](int, const TileInfo &ti, double &, double &) {
-                const int s = ti.sys;
-                const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
-                if (!xp && !run) return;
-                const double al = __ldcg(d.alpha + s), be = __ldcg(d.beta + s);
                 double pv[TR / 32], xv[TR / 32], zv[TR / 32];
 #pragma unroll
                 for (int h = 0; h < TR / 32; ++h) {
                     const int row = ti.r0 + h * 32 + lane;
                     if (row < ti.r1) {
                         pv[h] = d.p[row];
-                        xv[h] = xp ? d.x[row] : 0.0;
-                        zv[h] = run ? d.z[row] : 0.0;
+                        xv[h] = d.x[row];
+                        zv[h] = d.z[row];
                     }
                 }
+                const int s = ti.sys;
+                const int xp = __ldcg(d.xpend + s), run = __ldcg(d.state + s) == kRunning;
+                const double al = __ldcg(d.alpha + s), be = __ldcg(d.beta + s);
 #pragma unroll
                 for (int h = 0; h < TR / 32; ++h) {
                     const int row = ti.r0 + h * 32 + lane;
