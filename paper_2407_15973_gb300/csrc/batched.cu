@@ -171,14 +171,17 @@ __device__ __forceinline__ void tile_spmv(const BatchDev &d, const TileInfo &ti,
         const double *pv = d.sval + o0 + lane;
         const int32_t *pc = d.scol + o0 + lane;
         o0 += 32 * len;
+        // this row's p (mode 0) or b (mode 1), loaded before the gathers: after the store of q
+        // the compiler could not move the load ahead of it
+        const double own = row < ti.r1 ? (mode == 0 ? __ldcg(xin + row) : d.b[row]) : 0.0;
         double acc = 0.0;
         ell_row(pv, pc, len, xin, acc);
         if (row >= ti.r1) continue;
         if (mode == 0) {
             d.q[row] = acc;
-            part_a = fma(acc, __ldcg(xin + row), part_a);
+            part_a = fma(acc, own, part_a);
         } else {
-            const double bi = d.b[row];
+            const double bi = own;
             const double ri = bi - acc;
             d.r[row] = ri;
             part_a = fma(ri, ri, part_a);
@@ -194,13 +197,20 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
                                            float *s_rh, double *s_r, double &part_a, double &part_b) {
     const int lane = threadIdx.x & 31;
     const int r0 = ti.r0, r1 = ti.r1;
-#pragma unroll 1
+    double rv[TR / 32], qv[TR / 32];     // every r (and q) row of the tile in one round trip
+#pragma unroll
+    for (int h = 0; h < TR / 32; ++h) {
+        const int row = r0 + h * 32 + lane;
+        rv[h] = row < r1 ? d.r[row] : 0.0;
+        qv[h] = (fused && row < r1) ? d.q[row] : 0.0;
+    }
+#pragma unroll
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
         if (row < r1) {
-            double v = d.r[row];
+            double v = rv[h];
             if (fused) {
-                v = fma(-alpha, d.q[row], v);
+                v = fma(-alpha, qv[h], v);
                 d.r[row] = v;
                 part_b = fma(v, v, part_b);
             }
