@@ -39,6 +39,7 @@ namespace mpbjac {
 
 struct BatchDev {
     int n_tot, nsys, ntiles;
+    int32_t slot_eb;             // bytes per entry of a block's pool slot (8: room for any format)
     const int32_t *rowptr, *colidx;
     const double *val;
     const int32_t *block_ptr;
@@ -197,6 +198,10 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
                                            float *s_rh, double *s_r, double &part_a, double &part_b) {
     const int lane = threadIdx.x & 31;
     const int r0 = ti.r0, r1 = ti.r1;
+    // blocks of one size: their pool slots are consecutive, so one offset (loaded with the r
+    // and q rows) places them all
+    const long long q0 = ti.ubs > 0 ? __ldg(d.qoff + ti.blk0) : 0;
+    const long long slot = ((long long)ti.ubs * ti.ubs * d.slot_eb + 15) & ~15ll;
     double rv[TR / 32], qv[TR / 32];     // every r (and q) row of the tile in one round trip
 #pragma unroll
     for (int h = 0; h < TR / 32; ++h) {
@@ -225,20 +230,22 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
         if (row < r1) {
             // this row's block: arithmetic when the tile's blocks share one size
             int bk, bs0, bs;
+            const uint8_t *base;
             if (ti.ubs > 0) {
                 const int k = (row - r0) / ti.ubs;
                 bk = ti.blk0 + k;
                 bs = ti.ubs;
                 bs0 = r0 + k * bs;
+                base = d.pool + q0 + k * slot;
             } else {
                 bk = ti.blk0;
                 while (d.block_ptr[bk + 1] <= row) ++bk;
                 bs0 = d.block_ptr[bk];
                 bs = d.block_ptr[bk + 1] - bs0;
+                base = d.pool + d.qoff[bk];
             }
             const int i = row - bs0, off = bs0 - r0;
             const int f = FMT >= 0 ? FMT : d.fmt[bk];      // a batch of one format knows it at compile time
-            const uint8_t *base = d.pool + d.qoff[bk];
             const int eb = f == BJAC_FP64 ? 8 : f == BJAC_FP32 ? 4 : 2;
             double zi;
             if (((bs * eb) & 15) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0 && (off & 3) == 0) {
@@ -559,6 +566,7 @@ using namespace mpbjac;
 // ------------------------------------------------------------------------------------------
 struct bjac_batch {
     int nsys = 0, n_tot = 0, nnz_tot = 0, nb_tot = 0, ntiles = 0, tile_rows = 32;
+    int slot_eb = 8;                            // bytes per entry of the pool slots
     cudaStream_t stream = nullptr;
     std::vector<int32_t> sys_row, sys_tile, sys_blk;
     int32_t *rowptr = nullptr, *colidx = nullptr;
@@ -622,6 +630,7 @@ __global__ void k_concat_csr(int rows, int row0, int nz0, const int32_t *rp, con
 static BatchDev batch_dev(bjac_batch *h, double tol, int maxit) {
     BatchDev d{};
     d.n_tot = h->n_tot;
+    d.slot_eb = h->slot_eb;
     d.nsys = h->nsys;
     d.ntiles = h->ntiles;
     d.rowptr = h->rowptr;
@@ -1005,6 +1014,7 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         const int64_t bs = bp[k + 1] - bp[k];
         const int by = (P.select == BJAC_SELECT_RULE || P.select == BJAC_SELECT_GIVEN)
                            ? 8 : (ffmt == BJAC_FP64 ? 8 : ffmt == BJAC_FP32 ? 4 : 2);
+        h->slot_eb = by;
         qoff[k + 1] = qoff[k] + ((bs * bs * by + 15) & ~int64_t(15));
     }
     BTRY(cudaMalloc(&h->pool, std::max<int64_t>(16, qoff[nb_tot])));
