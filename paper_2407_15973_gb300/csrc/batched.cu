@@ -224,9 +224,13 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
         }
     }
     __syncwarp();
-#pragma unroll 1
+    // z of every row of the tile, stored after the loop so that the loads of the later slices'
+    // inverse rows need not wait behind the earlier slices' stores
+    double zv[TR / 32];
+#pragma unroll
     for (int h = 0; h < TR / 32; ++h) {
         const int row = r0 + h * 32 + lane;
+        zv[h] = 0.0;
         if (row < r1) {
             // this row's block: arithmetic when the tile's blocks share one size
             int bk, bs0, bs;
@@ -280,9 +284,16 @@ __device__ __forceinline__ void tile_apply(const BatchDev &d, const TileInfo &ti
                 }
                 zi = f32_to_f64(acc * d.scale[bk]);
             }
-            d.z[row] = zi;
-            if (init) d.p[row] = zi;
+            zv[h] = zi;
             part_a = fma(s_r[h * 32 + lane], zi, part_a);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < TR / 32; ++h) {
+        const int row = r0 + h * 32 + lane;
+        if (row < r1) {
+            d.z[row] = zv[h];
+            if (init) d.p[row] = zv[h];
         }
     }
     __syncwarp();
