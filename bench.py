@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only set up the headline policy and run this many eager PCG iterations "
                          "(a short, fixed launch sequence for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="only set up a batch of this many 2D systems of the batched workload's law twice "
+                         "(the first setup times the kernel variants) and solve each time for at most "
+                         "--profile-iters iterations (200 if unset): a short launch sequence for ncu")
     return ap.parse_args()
 
 
@@ -698,8 +702,35 @@ def run_reference(args, world):
             "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_batch(args):
+    """The batched kernel on a smaller batch of the 256-system workload's law, for ncu."""
+    import torch
+    from paper_2407_15973_gb300 import binding as B
+    from paper_2407_15973_gb300 import problems as PB
+    torch.cuda.init()
+    systems = PB.batch2d(args.profile_batch, seed=0)
+    dAs = [B.DeviceCSR(p.A) for p in systems]
+    bs = []
+    for d, p in zip(dAs, systems):
+        bv = torch.empty(p.A.n, dtype=torch.float64, device="cuda")
+        B.bjac_spmv(d, torch.as_tensor(p.x_star).cuda(), bv)
+        bs.append(bv)
+    runs = []
+    for _ in range(2):
+        xs = [torch.zeros(p.A.n, dtype=torch.float64, device="cuda") for p in systems]
+        bt = B.Batch(dAs, [p.block_ptr for p in systems], select=B.SELECT_FIXED, fixed_fmt=FMT["fp32"])
+        rc, st = bt.solve(bs, xs, tol=TOL, maxit=args.profile_iters or 200)
+        runs.append({"solve_ms": round(st[0]["solve_ms"], 3), "status": rc, **bt.info()})
+        bt.close()
+    return {"profile_batch": {"systems": len(systems), "rows": int(sum(p.A.n for p in systems)),
+                              "nnz": int(sum(p.A.nnz for p in systems)), "runs": runs}}
+
+
 def main():
     args = parse()
+    if args.profile_batch:
+        print(json.dumps(profile_batch(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
