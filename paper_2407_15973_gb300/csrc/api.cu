@@ -373,12 +373,14 @@ static int choose_spmv_format(bjac_handle *h) {
     return MPBJAC_OK;
 }
 
-// the loop SpMV (q = A p, sigma = p.q, alpha) in the handle's layout
+// the loop SpMV (q = A p and per-CTA partials of p.q, which the next kernel sums into alpha)
+// in the handle's layout
 static int launch_loop_spmv(const bjac_handle *h, cudaStream_t st) {
     unsigned int *ticket = &h->d_S->tickets[kTicketSpmv];
+    double *spart = h->d_part + kSpPartOff;
     if (h->use_sell)
-        return launch_spmv_sell(h->sell, h->d_p, nullptr, h->d_q, h->d_part, ticket, nullptr, h->d_S, kSpPcg, st);
-    return launch_spmv(h->A, h->d_p, h->d_q, h->d_part, ticket, nullptr, h->d_S, 2, st);
+        return launch_spmv_sell(h->sell, h->d_p, nullptr, h->d_q, spart, ticket, nullptr, h->d_S, kSpPcg, st);
+    return launch_spmv(h->A, h->d_p, h->d_q, spart, ticket, nullptr, h->d_S, 2, st);
 }
 
 extern "C" {
@@ -627,7 +629,8 @@ int bjac_setup(const bjac_csr *A, const int32_t *block_ptr, int32_t nb, const bj
     MPB_TRY(dalloc(&h->d_z, n));
     MPB_TRY(dalloc(&h->d_p, n));
     MPB_TRY(dalloc(&h->d_q, n));
-    MPB_TRY(dalloc(&h->d_part, 3 * (size_t)kMaxGrid));     // up to 3 partial sums per CTA
+    // up to 3 partial sums per CTA of the apply, then the loop SpMV's (stride 2) at kSpPartOff
+    MPB_TRY(dalloc(&h->d_part, (size_t)kSpPartOff + 2 * (size_t)kMaxGrid));
     MPB_TRY(dalloc(&h->d_S, 1));
     if (P.fp64_fallback) MPB_TRY(dalloc(&h->d_x0, n));
     MPB_TRY(cudaMallocHost((void **)&h->h_S, sizeof(SolverState)) == cudaSuccess
@@ -658,6 +661,7 @@ static ApplyIO base_io(bjac_handle *h) {
     io.z = h->d_z;
     io.p = h->d_p;
     io.part = h->d_part;
+    io.spart = h->d_part + kSpPartOff;
     io.ticket = &h->d_S->tickets[kTicketApply];
     io.out = nullptr;
     io.err = nullptr;
@@ -765,7 +769,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     if (ev) MPB_CUDA(cudaEventRecord(ev[1], cs));
     if (kt) {
         // r -= alpha q and the convergence test first, then the sweeps of the set in use
-        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
+        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_part + kSpPartOff, h->d_S, cs));
         *launches += 1;
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         ApplyIO io = base_io(h);
@@ -785,7 +789,7 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
         MPB_TRY_RC(launch_apply_spec(kApplyRedo, h->lo, h->hi, io, h->d_S, cs));
         *launches += 2;
     } else if (temporal) {
-        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_S, cs));
+        MPB_TRY_RC(launch_update_r(h->n, h->d_q, h->d_r, h->d_part, h->d_part + kSpPartOff, h->d_S, cs));
         if (ev) MPB_CUDA(cudaEventRecord(ev[2], cs));
         rc = launch_apply_select(h, kApplyTemporal, cs, false, false);
         if (rc) return rc;

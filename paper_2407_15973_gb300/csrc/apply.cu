@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_generic(PSet lo, PSet hi, Appl
     const PSet &P = use_low ? lo : hi;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
-    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    double alpha = 0.0;
+    if (MODE == kApplyFused && !loop_alpha(S, io.spart, alpha)) return;
     double rho = 0.0, rr = 0.0;
     for (int b = gw; b < P.nb; b += nw) {
         const int s = __ldg(P.block_ptr + b), bs = __ldg(P.block_ptr + b + 1) - s;
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(TmaGeom<QT, BS>::kThreads, 1) k_apply_tma(PSet
     uint8_t *stages = smem + Geo::kHeader + (size_t)warp * Geo::kS * Geo::kStageBytes;
     const int nb = P.nb;
     const int gw = blockIdx.x * Geo::kNW + warp, nw = gridDim.x * Geo::kNW;
-    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    double alpha = 0.0;     // (before any copy is issued: a CTA may leave here)
+    if (MODE == kApplyFused && !loop_alpha(S, io.spart, alpha)) return;
     const bool with_q = (MODE == kApplyFused);
     const unsigned vbytes = BS * 8;
     const unsigned tx = Geo::kQBytes + vbytes * (with_q ? 2u : 1u);
@@ -346,7 +348,6 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
             if (!S->use_low) return;     // the binary64 set runs in the generic kernel
         }
     }
-    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
     const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
     auto load_v = [&](int blk, double (&rv)[RPL], double (&qq)[RPL]) {
 #pragma unroll
@@ -358,7 +359,9 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
     };
     constexpr bool flex = MODE == kApplyFused && FLEX;
     double rho = 0.0, rr = 0.0, qz = 0.0;     // qz = q.z for the flexible beta
-    if (gw < nb) load_v(gw, rc, vc);
+    if (gw < nb) load_v(gw, rc, vc);          // r and q do not depend on alpha: in flight meanwhile
+    double alpha = 0.0;
+    if (MODE == kApplyFused && !loop_alpha(S, io.spart, alpha)) return;
     for (int blk = gw; blk < nb; blk += nw) {
         const int nxt = blk + nw;
         if (nxt < nb) {
@@ -480,7 +483,8 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_mix32(PSet P, ApplyIO io, Solv
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
-    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
+    double alpha = 0.0;
+    if (MODE == kApplyFused && !loop_alpha(S, io.spart, alpha)) return;
     const uint64_t pol = vec_policy(MODE != kApplyStandalone ? S->l2_keep : 0);
     constexpr bool flex = MODE == kApplyFused && FLEX;
     double rho = 0.0, rr = 0.0, qz = 0.0;     // qz = q.z for the flexible beta
@@ -576,7 +580,8 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_spec(PSe
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = lo.nb;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
-    const double alpha = SPEC ? S->alpha : 0.0;
+    double alpha = 0.0;
+    if (SPEC && !loop_alpha(S, io.spart, alpha)) return;
     const uint64_t pol = vec_policy(S->l2_keep);
     const double *__restrict__ q = io.q;
     double *__restrict__ r = io.r_out;

@@ -28,6 +28,7 @@ struct ApplyIO {
     int set;               // 1 low-precision set, 0 binary64 set (standalone / fused)
     int only_set;          // -1: this launch serves both sets; else it serves only that set
     int flex;              // fused mode, register kernels: also sum q.z for the flexible-CG beta
+    const double *spart;   // fused / speculative modes: the loop SpMV's partials of p.q (loop_alpha)
 };
 
 // ----------------------------------------------------------------------------------------

@@ -226,6 +226,11 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
         part[2 * blockIdx.x] = cs[0];
         part[2 * blockIdx.x + 1] = cs[1];
     }
+    if (KIND == kSpPcg) {     // the kernel that consumes alpha sums the partials (loop_alpha)
+        if (blockIdx.x == 0)
+            for (int c = gridDim.x + threadIdx.x; c < kMaxGrid; c += blockDim.x) part[2 * c] = 0.0;
+        return;
+    }
     if (!last_cta(ticket)) return;
     const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
     const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
@@ -329,6 +334,11 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = cs[0];
         part[2 * blockIdx.x + 1] = cs[1];
+    }
+    if (KIND == kSpPcg) {     // the kernel that consumes alpha sums the partials (loop_alpha)
+        if (blockIdx.x == 0)
+            for (int c = gridDim.x + threadIdx.x; c < kMaxGrid; c += blockDim.x) part[2 * c] = 0.0;
+        return;
     }
     if (!last_cta(ticket)) return;
     const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);

@@ -199,6 +199,11 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         part[2 * blockIdx.x] = cs[0];
         part[2 * blockIdx.x + 1] = cs[1];
     }
+    if (KIND == kSpPcg) {     // the kernel that consumes alpha sums the partials (loop_alpha)
+        if (blockIdx.x == 0)
+            for (int c = gridDim.x + threadIdx.x; c < kMaxGrid; c += blockDim.x) part[2 * c] = 0.0;
+        return;
+    }
     if (!last_cta(ticket)) return;
     const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
     const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
@@ -335,6 +340,11 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = cs[0];
         part[2 * blockIdx.x + 1] = cs[1];
+    }
+    if (KIND == kSpPcg) {     // the kernel that consumes alpha sums the partials (loop_alpha)
+        if (blockIdx.x == 0)
+            for (int c = gridDim.x + threadIdx.x; c < kMaxGrid; c += blockDim.x) part[2 * c] = 0.0;
+        return;
     }
     if (!last_cta(ticket)) return;
     const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);

@@ -9,7 +9,7 @@ constexpr int kSpNT = 256;               // threads per CTA of the SpMV kernels
 enum SpmvKind {
     kSpY = 0,         // y = A x
     kSpYDot = 1,      // y = A x, *out = x . y
-    kSpPcg = 2,       // PCG: q = A p, sigma = p . q, alpha = rho / sigma
+    kSpPcg = 2,       // PCG: q = A p and per-CTA partials of p . q (summed by loop_alpha)
     kResStandalone = 10,  // r = b - A x, *out = r . r
     kResStart = 11,       // PCG start: bnorm, relres, state
     kResCheck = 12,       // true residual after the loop; restart decision
@@ -21,11 +21,6 @@ template <int KIND>
 __device__ __forceinline__ void spmv_finish(double t1, double t2, double *out, SolverState *S) {
     if (KIND == kSpYDot || KIND == kResStandalone) {
         *out = t1;
-    } else if (KIND == kSpPcg) {
-        S->x_pending = 0;      // set again once this iteration updates r
-        S->sigma = t1;
-        if (!finite_pos(t1)) S->state = kBreakdownSigma;
-        else S->alpha = S->rho / t1;
     } else if (KIND == kResStart) {
         const double bnorm = sqrt(t2);
         S->bnorm = bnorm;

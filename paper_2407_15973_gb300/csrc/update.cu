@@ -28,11 +28,12 @@ static int vec_grid2(int n) {
 // aMP loop: r -= alpha q, relres = ||r|| / ||b||, convergence test, precision for the next
 // preconditioner application (Algorithms 3.2 / 3.3 read this relres). r, q: 16-byte aligned.
 __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restrict__ q, double *__restrict__ r,
-                                                  double *part, SolverState *S) {
+                                                  double *part, const double *spart, SolverState *S) {
     pdl_enter();
     __shared__ double red[kNT];
     if (S->state != kRunning) return;
-    const double alpha = S->alpha;
+    double alpha;
+    if (!loop_alpha(S, spart, alpha)) return;
     const uint64_t pol = vec_policy(S->l2_keep);
     double rr = 0.0;
     const int n2 = n >> 1;
@@ -158,8 +159,9 @@ int launch_flex_beta(int n, const double *q, const double *z, double *part, Solv
     return MPBJAC_OK;
 }
 
-int launch_update_r(int n, const double *q, double *r, double *part, SolverState *S, cudaStream_t st) {
-    MPB_CUDA(launch_kernel(k_update_r, vec_grid2(n), kNT, 0, st, n, q, r, part, S));
+int launch_update_r(int n, const double *q, double *r, double *part, const double *spart, SolverState *S,
+                    cudaStream_t st) {
+    MPB_CUDA(launch_kernel(k_update_r, vec_grid2(n), kNT, 0, st, n, q, r, part, spart, S));
     return MPBJAC_OK;
 }
 

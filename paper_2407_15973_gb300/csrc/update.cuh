@@ -4,9 +4,11 @@
 
 namespace mpbjac {
 
-// aMP loop: r -= alpha q with ||r||^2 (grid reduction through part), relres, convergence,
-// and the precision of the next preconditioner application.
-int launch_update_r(int n, const double *q, double *r, double *part, SolverState *S, cudaStream_t st);
+// aMP loop: alpha from the loop SpMV's partials (spart, loop_alpha), r -= alpha q with ||r||^2
+// (grid reduction through part), relres, convergence, and the precision of the next
+// preconditioner application.
+int launch_update_r(int n, const double *q, double *r, double *part, const double *spart, SolverState *S,
+                    cudaStream_t st);
 
 // x += alpha p (deferred from this iteration) and p = z + beta p; sets the graph's loop
 // condition when use_cond is 1.

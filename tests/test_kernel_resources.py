@@ -33,9 +33,10 @@ LOOP_KERNELS = [
 ]
 # kernels known to spill a few bytes: the binary32 register applies hold two 4 KB blocks per
 # warp (k_apply_reg, and the speculative aMP apply, which also holds the binary64 path); the
-# flexible speculative applies keep a third running sum at 64 registers
+# flexible register and speculative applies keep a third running sum at 64 registers
 SPILL_ALLOWED = ("k_apply_regIfLi32E", "k_apply_specIf", "k_apply_specI13__nv_bfloat16Li4ELb1E",
-                 "k_apply_specI6__halfLi4ELb1E")
+                 "k_apply_specI6__halfLi4ELb1E", "k_apply_regI13__nv_bfloat16Li32ELi3ELb1E",
+                 "k_apply_regI6__halfLi32ELi3ELb1E")
 
 
 def _resources(src, tmp):
