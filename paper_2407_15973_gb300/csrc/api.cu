@@ -373,14 +373,16 @@ static int choose_spmv_format(bjac_handle *h) {
     return MPBJAC_OK;
 }
 
-// the loop SpMV (q = A p and per-CTA partials of p.q, which the next kernel sums into alpha)
-// in the handle's layout
-static int launch_loop_spmv(const bjac_handle *h, cudaStream_t st) {
+// the loop SpMV in the handle's layout: q = A p and per-CTA partials of p.q, which the next
+// kernel sums into alpha (loop_alpha); or, when the next kernel is the generic apply
+// (finish_alpha), with sigma and alpha finished by the SpMV's last CTA
+static int launch_loop_spmv(const bjac_handle *h, cudaStream_t st, bool finish_alpha) {
     unsigned int *ticket = &h->d_S->tickets[kTicketSpmv];
     double *spart = h->d_part + kSpPartOff;
     if (h->use_sell)
-        return launch_spmv_sell(h->sell, h->d_p, nullptr, h->d_q, spart, ticket, nullptr, h->d_S, kSpPcg, st);
-    return launch_spmv(h->A, h->d_p, h->d_q, spart, ticket, nullptr, h->d_S, 2, st);
+        return launch_spmv_sell(h->sell, h->d_p, nullptr, h->d_q, spart, ticket, nullptr, h->d_S,
+                                finish_alpha ? kSpPcgAlpha : kSpPcg, st);
+    return launch_spmv(h->A, h->d_p, h->d_q, spart, ticket, nullptr, h->d_S, finish_alpha ? 3 : 2, st);
 }
 
 extern "C" {
@@ -762,7 +764,8 @@ static int capture_body(bjac_handle *h, int which, cudaStream_t cs, cudaGraphCon
     const bool kt = h->pol.select == BJAC_SELECT_KT;
     if (ev) MPB_CUDA(cudaEventRecord(ev[0], cs));
     pdl_set(pdl && pdl_first);
-    int rc = launch_loop_spmv(h, cs);
+    const bool generic_next = !kt && !temporal && !(use_low && lo_uses_tma(h));
+    int rc = launch_loop_spmv(h, cs, generic_next);
     if (rc) return rc;
     *launches += 1;
     pdl_set(pdl);

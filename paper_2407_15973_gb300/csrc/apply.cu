@@ -55,8 +55,10 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_generic(PSet lo, PSet hi, Appl
     const PSet &P = use_low ? lo : hi;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
-    double alpha = 0.0;
-    if (MODE == kApplyFused && !loop_alpha(S, io.spart, alpha)) return;
+    // alpha from the state: in front of this kernel the loop SpMV finishes p.q and alpha
+    // itself (kSpPcgAlpha). Summing its partials here (loop_alpha) made this kernel 15 %
+    // slower on binary32 / 16-bit sets of uneven blocks, for a reason not found.
+    const double alpha = (MODE == kApplyFused) ? S->alpha : 0.0;
     double rho = 0.0, rr = 0.0;
     for (int b = gw; b < P.nb; b += nw) {
         const int s = __ldg(P.block_ptr + b), bs = __ldg(P.block_ptr + b + 1) - s;

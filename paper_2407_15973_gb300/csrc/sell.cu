@@ -165,13 +165,13 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
         }
     }
     pdl_enter();
-    if (KIND == kSpPcg) {
+    if (sp_loop<KIND>()) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
         if (S->state != kRunning) return;
     }
-    const uint64_t pol = vec_policy(KIND == kSpPcg ? S->l2_keep : 0);
+    const uint64_t pol = vec_policy(sp_loop<KIND>() ? S->l2_keep : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW;
     double acc1 = 0.0, acc2 = 0.0;
@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
     int nc[8], n_o0, n_len;
     sell_head(gw, nslices, lane, off, col, val, nv, nc, n_o0, n_len);   // A only: before the wait
     pdl_enter();
-    if (KIND == kSpPcg) {
+    if (sp_loop<KIND>()) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
         if (S->state != kRunning) return;
     }
-    const uint64_t pol = vec_policy(KIND == kSpPcg ? S->l2_keep : 0);
+    const uint64_t pol = vec_policy(sp_loop<KIND>() ? S->l2_keep : 0);
     double acc1 = 0.0, acc2 = 0.0;
     for (int s = gw; s < nslices; s += nw) {
         double cv[8];
@@ -444,6 +444,7 @@ int launch_spmv_sell(const SellMat &M, const double *x, const double *b, double 
         case kSpY: return launch_sell_t<kSpY>(M, x, b, y, part, ticket, out, S, st);
         case kSpYDot: return launch_sell_t<kSpYDot>(M, x, b, y, part, ticket, out, S, st);
         case kSpPcg: return launch_sell_t<kSpPcg>(M, x, b, y, part, ticket, out, S, st);
+        case kSpPcgAlpha: return launch_sell_t<kSpPcgAlpha>(M, x, b, y, part, ticket, out, S, st);
         case kResStandalone: return launch_sell_t<kResStandalone>(M, x, b, y, part, ticket, out, S, st);
         case kResStart: return launch_sell_t<kResStart>(M, x, b, y, part, ticket, out, S, st);
         case kResCheck: return launch_sell_t<kResCheck>(M, x, b, y, part, ticket, out, S, st);

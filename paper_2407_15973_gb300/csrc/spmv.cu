@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
     __shared__ double red[2 * kSpNT];
     __shared__ int s_bad;
 
-    if (KIND == kSpPcg) {
+    if (sp_loop<KIND>()) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
     __shared__ double s_v[NW][CH];
     __shared__ int32_t s_c[NW][CH];
     __shared__ double red[2 * kSpNT];
-    if (KIND == kSpPcg) {
+    if (sp_loop<KIND>()) {
         // the previous iteration's x update is done (stream order): clear its flag even when
         // this iteration does not run, so a loop body after convergence changes nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) S->x_pending = 0;
@@ -437,7 +437,7 @@ static int launch_kind(const bjac_csr &A, const double *x, const double *b, doub
 int prepare_spmv(const bjac_csr &A) {
 #define MPB_ATTR(G, K) \
     MPB_CUDA(cudaFuncSetAttribute(k_spmv<G::kCap, G::kStages, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem))
-#define MPB_ATTRS(G) MPB_ATTR(G, kSpY); MPB_ATTR(G, kSpYDot); MPB_ATTR(G, kSpPcg); \
+#define MPB_ATTRS(G) MPB_ATTR(G, kSpY); MPB_ATTR(G, kSpYDot); MPB_ATTR(G, kSpPcg); MPB_ATTR(G, kSpPcgAlpha); \
     MPB_ATTR(G, kResStandalone); MPB_ATTR(G, kResStart); MPB_ATTR(G, kResCheck)
     if (long_rows(A)) {
         MPB_ATTRS(SpLong);
@@ -532,6 +532,7 @@ int launch_spmv(const bjac_csr &A, const double *x, double *y, double *part, uns
                 double *dot_out, SolverState *S, int mode, cudaStream_t st) {
     if (mode == 0) return launch_kind<kSpY>(A, x, nullptr, y, part, ticket, dot_out, S, st);
     if (mode == 1) return launch_kind<kSpYDot>(A, x, nullptr, y, part, ticket, dot_out, S, st);
+    if (mode == 3) return launch_kind<kSpPcgAlpha>(A, x, nullptr, y, part, ticket, dot_out, S, st);
     return launch_kind<kSpPcg>(A, x, nullptr, y, part, ticket, dot_out, S, st);
 }
 

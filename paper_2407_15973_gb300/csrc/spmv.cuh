@@ -6,10 +6,15 @@ namespace mpbjac {
 
 constexpr int kSpNT = 256;               // threads per CTA of the SpMV kernels
 
+// the kinds of the PCG loop's SpMV
+template <int KIND>
+__host__ __device__ constexpr bool sp_loop() { return KIND == 2 || KIND == 3; }
+
 enum SpmvKind {
     kSpY = 0,         // y = A x
     kSpYDot = 1,      // y = A x, *out = x . y
     kSpPcg = 2,       // PCG: q = A p and per-CTA partials of p . q (summed by loop_alpha)
+    kSpPcgAlpha = 3,  // PCG: q = A p, sigma = p . q and alpha by the last CTA (for the generic apply)
     kResStandalone = 10,  // r = b - A x, *out = r . r
     kResStart = 11,       // PCG start: bnorm, relres, state
     kResCheck = 12,       // true residual after the loop; restart decision
@@ -21,6 +26,11 @@ template <int KIND>
 __device__ __forceinline__ void spmv_finish(double t1, double t2, double *out, SolverState *S) {
     if (KIND == kSpYDot || KIND == kResStandalone) {
         *out = t1;
+    } else if (KIND == kSpPcgAlpha) {
+        S->x_pending = 0;      // set again once this iteration updates r
+        S->sigma = t1;
+        if (!finite_pos(t1)) S->state = kBreakdownSigma;
+        else S->alpha = S->rho / t1;
     } else if (KIND == kResStart) {
         const double bnorm = sqrt(t2);
         S->bnorm = bnorm;
