@@ -598,7 +598,6 @@ struct bjac_batch {
     int32_t *soff = nullptr, *scol = nullptr, *alist = nullptr;   // sliced-ELLPACK tiles, tile lists
     int4 *tinfo = nullptr;          // per-tile descriptions (two int4 each)
     double *sval = nullptr;
-    std::vector<int32_t> h_rowptr;  // host copy of the concatenated row pointers
     std::vector<int32_t> h_bp;      // host copy of the concatenated block offsets
     int grid = 0;
     float tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // timings of the kernel variants
@@ -797,6 +796,21 @@ __global__ void k_batch_ell(int nslices, int spt, const int32_t *__restrict__ ti
     }
 }
 
+// stored length of every 32-row slice of every tile (its longest row): one warp per slice
+__global__ void k_batch_slice_len(int nslices, int spt, const int32_t *__restrict__ tile_row,
+                                  const int32_t *__restrict__ rowptr, int32_t *__restrict__ slen) {
+    const int lane = threadIdx.x & 31;
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nslices) return;
+    const int t = sl / spt, hh = sl - t * spt;
+    const int r0 = tile_row[t] + 32 * hh, r1 = min(tile_row[t + 1], r0 + 32);
+    const int row = r0 + lane;
+    int len = row < r1 ? rowptr[row + 1] - rowptr[row] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) slen[sl] = len;
+}
+
 static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
     // tiles of at most tr rows, cut at system boundaries and at block boundaries
     std::vector<int32_t> trow, tsys, tblk;
@@ -839,18 +853,25 @@ static int build_tiles(bjac_batch *h, int tr, const std::vector<int32_t> &bp) {
     const int spt = tr / 32;
     const size_t nsl = (size_t)h->ntiles * spt;
     std::vector<int32_t> so(nsl + 1), slen(nsl, 0);
+    {
+        // the slices' stored lengths on the device (one warp per slice), read back once
+        int32_t *dlen = nullptr;
+        MPB_CUDA(cudaMalloc(&dlen, sizeof(int32_t) * std::max<size_t>(1, nsl)));
+        const int grid = (int)((nsl * 32 + 255) / 256);
+        k_batch_slice_len<<<grid, 256, 0, h->stream>>>((int)nsl, spt, h->tile_row, h->rowptr, dlen);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(slen.data(), dlen, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost,
+                                                  h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(dlen);
+        if (e != cudaSuccess) return cuda_fail(e, "slice lengths of the batch");
+    }
     long long acc = 0;
-    for (int t = 0; t < h->ntiles; ++t) {
-        for (int hh = 0; hh < spt; ++hh) {
-            so[(size_t)t * spt + hh] = (int32_t)acc;
-            const int r0 = trow[t] + 32 * hh, r1 = std::min(trow[t + 1], r0 + 32);
-            int len = 0;
-            for (int row = r0; row < r1; ++row) len = std::max(len, h->h_rowptr[row + 1] - h->h_rowptr[row]);
-            if (len > 0xFFFF) return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes rows of at most 65535 entries");
-            slen[(size_t)t * spt + hh] = len;
-            acc += 32ll * len;
-            if (acc > (long long)INT32_MAX - 64) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
-        }
+    for (size_t k = 0; k < nsl; ++k) {
+        so[k] = (int32_t)acc;
+        if (slen[k] > 0xFFFF) return fail(MPBJAC_ERR_UNSUPPORTED, "the batched solver takes rows of at most 65535 entries");
+        acc += 32ll * slen[k];
+        if (acc > (long long)INT32_MAX - 64) return fail(MPBJAC_ERR_INVALID_ARG, "batch too large for int32");
     }
     so[nsl] = (int32_t)acc;
     // tile descriptions: rows, system, first block, common block size, slice offsets
@@ -1002,9 +1023,6 @@ extern "C" int bjac_batch_setup(int32_t nsys, const bjac_csr *A, const int32_t *
         }
         const int32_t last = nz;
         BTRY(cudaMemcpyAsync(h->rowptr + n_tot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        h->h_rowptr.resize(n_tot + 1);
-        BTRY(cudaMemcpyAsync(h->h_rowptr.data(), h->rowptr, sizeof(int32_t) * (n_tot + 1), cudaMemcpyDeviceToHost,
-                             st));
         BTRY(cudaStreamSynchronize(st));
     }
     BTRY(cudaMalloc(&h->block_ptr, sizeof(int32_t) * (nb_tot + 1)));
