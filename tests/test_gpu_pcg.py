@@ -225,3 +225,21 @@ def test_amp_speculative_graph_equals_eager(B, temporal, adp):
     e = _gpu_solve(B, pr, b, hist=True, graph_mode=1, **pol)
     assert g["iters"] == e["iters"] and g["low_applies"] == e["low_applies"]
     assert np.array_equal(g["x"], e["x"]) and np.array_equal(g["hist"], e["hist"])
+
+
+@pytest.mark.parametrize("layout", [1, 2])      # CSR, SELL-32
+@pytest.mark.parametrize("fmt", ["fp32", "bf16"])
+def test_alpha_paths_give_the_same_bits(B, fmt, layout):
+    # In front of the generic apply the loop SpMV's last CTA sums the per-CTA partials of p.q
+    # into sigma and alpha; in front of the register and TMA applies every CTA of the apply sums
+    # them itself (loop_alpha). Both sum in the same fixed order, and every apply kernel gives
+    # the oracle emulation's bits, so the whole solve must be the same bits through each.
+    pr, b, _ = _problem("subcube24_bs32")
+    f = {"fp32": B.FP32, "bf16": B.BF16}[fmt]
+    runs = [_gpu_solve(B, pr, b, select=B.SELECT_FIXED, fixed_fmt=f, apply_variant=v, spmv_format=layout)
+            for v in (1, 2, 3)]     # generic, TMA, register
+    for st in runs:
+        assert st["converged"] and st["true_relres"] <= TOL
+    for st in runs[1:]:
+        assert st["iters"] == runs[0]["iters"]
+        assert np.array_equal(st["x"].view(np.uint64), runs[0]["x"].view(np.uint64))
