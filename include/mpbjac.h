@@ -322,14 +322,21 @@ int bjac_spmv_tuning(const bjac_csr *A, int32_t *variant, float *ms);
  * params: HOST, bjac_mlp_param_count() floats (weights, then feature mean and standard
  * deviation used to standardise the inputs). feat: DEVICE N x 12 doubles (raw features as
  * bjac_export returns them); label: DEVICE N int32 classes (0 FP64, 1 FP32, 2 16-bit).
- * bf16_weights: 1 to use the weights rounded to bfloat16 (as inference does), 0 for the
- * binary32 values. grad: HOST, the first 5187 entries (weights only); loss: HOST. */
+ * bf16_weights: 1 = the weights rounded to bfloat16 (as inference does) on the tensor cores
+ * (tcgen05: layer 2's forward product, its back-propagation and its weight gradient as BF16
+ * MMAs with FP32 accumulation, each binary32 activation or error entering as two bfloat16
+ * parts), 2 = the same weights on CUDA cores, 0 = the binary32 values on CUDA cores.
+ * grad: HOST, the first 5187 entries (weights only); loss: HOST. Returns
+ * MPBJAC_ERR_INVALID_ARG for another bf16_weights value and MPBJAC_ERR_TIMEOUT when an MMA did
+ * not complete within the bounded wait. */
 int bjac_mlp_grad(const float *params, int32_t bf16_weights, const double *feat, const int32_t *label, int32_t N,
                   float *grad, float *loss, void *stream);
 
 /* Full-batch Adam (beta 0.9 / 0.999) for `epochs` steps on the same loss with bfloat16
- * forward weights and binary32 masters; params (HOST) is updated in place (the feature mean
- * and deviation entries are left as given). loss_hist: HOST, epochs floats, nullable. */
+ * forward weights (the tensor-core gradient of bjac_mlp_grad mode 1) and binary32 masters;
+ * params (HOST) is updated in place (the feature mean and deviation entries are left as
+ * given). loss_hist: HOST, epochs floats, nullable; with it, an MMA timeout is reported as
+ * MPBJAC_ERR_TIMEOUT. */
 int bjac_mlp_train(float *params, const double *feat, const int32_t *label, int32_t N, int32_t epochs, float lr,
                    float *loss_hist, void *stream);
 

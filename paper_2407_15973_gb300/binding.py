@@ -388,13 +388,17 @@ class Batch:
                     for s in st]
 
 
-def bjac_mlp_grad(params, feat, label, bf16_weights=True, stream=None):
-    """(loss, gradient of the 5187 weights) of the selector on DEVICE feat (N x 12) / label (N)."""
+def bjac_mlp_grad(params, feat, label, bf16_weights=True, tensor_cores=True, stream=None, mode=None):
+    """(loss, gradient of the 5187 weights) of the selector on DEVICE feat (N x 12) / label (N).
+    bfloat16 weights run on the tensor cores unless tensor_cores=False; binary32 weights on CUDA
+    cores. `mode` passes the C mode (0, 1, 2) through unchanged."""
     _require_cuda(feat, label)
     pr = np.ascontiguousarray(params, dtype=np.float32)
     g = np.zeros(5187, np.float32)
     loss = C.c_float()
-    _check(lib().bjac_mlp_grad(pr.ctypes.data, int(bool(bf16_weights)), _ptr(feat), _ptr(label), feat.shape[0],
+    if mode is None:
+        mode = (1 if tensor_cores else 2) if bf16_weights else 0
+    _check(lib().bjac_mlp_grad(pr.ctypes.data, int(mode), _ptr(feat), _ptr(label), feat.shape[0],
                                g.ctypes.data, C.byref(loss), _stream(stream)))
     return float(loss.value), g
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUTDIR, "libmpbjac.so")
-SOURCES = ["spmv.cu", "sell.cu", "apply.cu", "setup.cu", "mlp.cu", "api.cu", "mlp_train.cu", "batched.cu", "noalloc.cu", "update.cu", "kt.cu"]
+SOURCES = ["spmv.cu", "sell.cu", "apply.cu", "setup.cu", "mlp.cu", "api.cu", "mlp_train.cu", "mlp_grad_tc.cu", "batched.cu", "noalloc.cu", "update.cu", "kt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

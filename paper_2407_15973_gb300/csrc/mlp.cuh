@@ -25,5 +25,12 @@ int launch_mlp_select(const float *params, int nb, const double *feat, const dou
 // logits[3 n] of the same tensor-core forward pass (dparams: DEVICE floats [kMlpParams]);
 // entries of a tile whose MMA timed out are NaN
 int launch_mlp_logits_tc(const float *dparams, int n, const double *feat, float *logits, cudaStream_t st);
+// Gradient of the loss sum / N over N samples with the weights rounded to bfloat16, layer 2's
+// three products on the tensor cores: CTA c of `grid` (mlp_grad_tc_grid(N)) writes its partial
+// gradient to partial[c][kMlpWeights] and its loss sum to loss_part[c] (NaN after an MMA that
+// did not complete in the bounded wait)
+int mlp_grad_tc_grid(int N);
+int launch_mlp_grad_tc(const float *dparams, const double *feat, const int32_t *label, int N, float *partial,
+                       double *loss_part, int grid, cudaStream_t st);
 
 }  // namespace mpbjac

@@ -4,6 +4,9 @@
 // or the binary32 masters (bf16_weights = 0); gradients are taken with respect to the
 // weights actually used and applied to the masters.
 //
+// The bfloat16-weight gradient runs on the tensor cores (mlp_grad_tc.cu); the kernel below
+// serves the binary32 weights and, for comparison, the bfloat16 weights on CUDA cores.
+//
 // Determinism: one warp handles samples gw, gw + nw, ... in a fixed order and accumulates
 // their gradient in its own shared-memory slice (each lane owns distinct entries, so no
 // atomics); the slices are written out and summed over warps in index order.
@@ -167,32 +170,50 @@ static int grad_launch(int N) {
     return g < 1 ? 1 : g;
 }
 
+// partial gradients (kMlpWeights floats each) that the gradient pass of `mode` writes
+static int grad_parts(int mode, int N) { return mode == 1 ? mlp_grad_tc_grid(N) : grad_launch(N) * kTrainWarps; }
+
+// one gradient pass: mode 0 binary32 weights, 1 bfloat16 weights on the tensor cores, 2 bfloat16
+// weights on CUDA cores; dpart / dloss hold grad_parts(mode, N) entries
+static int grad_pass(int mode, const float *dp, const double *feat, const int32_t *label, int N, float *dpart,
+                     double *dloss, cudaStream_t st) {
+    if (mode == 1) return launch_mlp_grad_tc(dp, feat, label, N, dpart, dloss, mlp_grad_tc_grid(N), st);
+    static bool attr = false;
+    const size_t smem = sizeof(float) * kTrainWarps * kMlpWeights;
+    if (!attr) {
+        MPB_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_mlp_grad<<<grad_launch(N), kTrainNT, smem, st>>>(dp, mode ? 1 : 0, feat, label, N, dpart, dloss);
+    MPB_CUDA(cudaGetLastError());
+    return MPBJAC_OK;
+}
+
 }  // namespace mpbjac
 
 using namespace mpbjac;
 
 extern "C" int bjac_mlp_grad(const float *params, int32_t bf16_weights, const double *feat, const int32_t *label,
                              int32_t N, float *grad, float *loss, void *stream) {
-    if (!params || !feat || !label || !grad || N < 1) return fail(MPBJAC_ERR_INVALID_ARG, "bad MLP gradient arguments");
+    if (!params || !feat || !label || !grad || N < 1 || bf16_weights < 0 || bf16_weights > 2)
+        return fail(MPBJAC_ERR_INVALID_ARG, "bad MLP gradient arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    const int g = grad_launch(N), nwarps = g * kTrainWarps;
+    const int nparts = grad_parts(bf16_weights, N);
     float *dp = nullptr, *dpart = nullptr, *dgrad = nullptr;
     double *dloss = nullptr;
     MPB_CUDA(cudaMallocAsync((void **)&dp, sizeof(float) * kMlpParams, st));
-    MPB_CUDA(cudaMallocAsync((void **)&dpart, sizeof(float) * (size_t)nwarps * kMlpWeights, st));
+    MPB_CUDA(cudaMallocAsync((void **)&dpart, sizeof(float) * (size_t)nparts * kMlpWeights, st));
     MPB_CUDA(cudaMallocAsync((void **)&dgrad, sizeof(float) * kMlpWeights, st));
-    MPB_CUDA(cudaMallocAsync((void **)&dloss, sizeof(double) * nwarps, st));
+    MPB_CUDA(cudaMallocAsync((void **)&dloss, sizeof(double) * nparts, st));
     MPB_CUDA(cudaMemcpyAsync(dp, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
-    const size_t smem = sizeof(float) * kTrainWarps * kMlpWeights;
-    MPB_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mlp_grad<<<g, kTrainNT, smem, st>>>(dp, bf16_weights, feat, label, N, dpart, dloss);
-    MPB_CUDA(cudaGetLastError());
-    k_mlp_reduce_adam<<<(kMlpWeights + 255) / 256, 256, 0, st>>>(dpart, nwarps, dgrad, nullptr, nullptr, nullptr, 0, 0, 0,
+    int rc = grad_pass(bf16_weights, dp, feat, label, N, dpart, dloss, st);
+    if (rc != MPBJAC_OK) return rc;
+    k_mlp_reduce_adam<<<(kMlpWeights + 255) / 256, 256, 0, st>>>(dpart, nparts, dgrad, nullptr, nullptr, nullptr, 0, 0, 0,
                                                                  0, 0, 0);
     MPB_CUDA(cudaGetLastError());
-    std::vector<double> hl(nwarps);
+    std::vector<double> hl(nparts);
     MPB_CUDA(cudaMemcpyAsync(grad, dgrad, sizeof(float) * kMlpWeights, cudaMemcpyDeviceToHost, st));
-    MPB_CUDA(cudaMemcpyAsync(hl.data(), dloss, sizeof(double) * nwarps, cudaMemcpyDeviceToHost, st));
+    MPB_CUDA(cudaMemcpyAsync(hl.data(), dloss, sizeof(double) * nparts, cudaMemcpyDeviceToHost, st));
     MPB_CUDA(cudaStreamSynchronize(st));
     double l = 0.0;
     for (double v : hl) l += v;
@@ -202,6 +223,7 @@ extern "C" int bjac_mlp_grad(const float *params, int32_t bf16_weights, const do
     cudaFreeAsync(dgrad, st);
     cudaFreeAsync(dloss, st);
     MPB_CUDA(cudaStreamSynchronize(st));
+    if (l != l) return fail(MPBJAC_ERR_TIMEOUT, "MLP gradient MMA did not complete");
     return MPBJAC_OK;
 }
 
@@ -210,7 +232,7 @@ extern "C" int bjac_mlp_train(float *params, const double *feat, const int32_t *
     if (!params || !feat || !label || N < 1 || epochs < 1 || !(lr > 0.0f))
         return fail(MPBJAC_ERR_INVALID_ARG, "bad MLP training arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    const int g = grad_launch(N), nwarps = g * kTrainWarps;
+    const int nwarps = grad_parts(1, N);
     float *dp = nullptr, *dpart = nullptr, *dgrad = nullptr, *m1 = nullptr, *m2 = nullptr;
     double *dloss = nullptr;
     MPB_CUDA(cudaMallocAsync((void **)&dp, sizeof(float) * kMlpParams, st));
@@ -222,12 +244,10 @@ extern "C" int bjac_mlp_train(float *params, const double *feat, const int32_t *
     MPB_CUDA(cudaMemcpyAsync(dp, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
     MPB_CUDA(cudaMemsetAsync(m1, 0, sizeof(float) * kMlpWeights, st));
     MPB_CUDA(cudaMemsetAsync(m2, 0, sizeof(float) * kMlpWeights, st));
-    const size_t smem = sizeof(float) * kTrainWarps * kMlpWeights;
-    MPB_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     std::vector<double> hl(nwarps);
     for (int ep = 1; ep <= epochs; ++ep) {
-        k_mlp_grad<<<g, kTrainNT, smem, st>>>(dp, 1, feat, label, N, dpart, dloss);
-        MPB_CUDA(cudaGetLastError());
+        const int rc = grad_pass(1, dp, feat, label, N, dpart, dloss, st);
+        if (rc != MPBJAC_OK) return rc;
         k_mlp_reduce_adam<<<(kMlpWeights + 255) / 256, 256, 0, st>>>(dpart, nwarps, dgrad, dp, m1, m2, lr, 0.9f, 0.999f,
                                                                      1e-8f, ep, 1);
         MPB_CUDA(cudaGetLastError());
@@ -237,6 +257,7 @@ extern "C" int bjac_mlp_train(float *params, const double *feat, const int32_t *
             double l = 0.0;
             for (double v : hl) l += v;
             loss_hist[ep - 1] = (float)(l / N);
+            if (l != l) return fail(MPBJAC_ERR_TIMEOUT, "MLP gradient MMA did not complete");
         }
     }
     MPB_CUDA(cudaMemcpyAsync(params, dp, sizeof(float) * kMlpWeights, cudaMemcpyDeviceToHost, st));

@@ -46,16 +46,55 @@ def test_gradient_fp32_weights_match_oracle(B, seed):
     assert np.max(np.abs(g[big] - go[big]) / np.abs(go[big])) <= 1e-3
 
 
-def test_gradient_bf16_weights(B):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_gradient_bf16_weights(B, tensor_cores):
     feat, params, label = _data(2)
-    loss, g = B.bjac_mlp_grad(params, cuda(feat), cuda(label, torch.int32), bf16_weights=True)
+    loss, g = B.bjac_mlp_grad(params, cuda(feat), cuda(label, torch.int32), bf16_weights=True,
+                              tensor_cores=tensor_cores)
     # the weights inference uses: each one rounded to bfloat16
     w16 = _bf16(params[:5187])
     lo16, go16 = O.mlp_loss_grad(w16, _xin(feat, params), label)
+    assert abs(loss - lo16) <= 1e-5 * abs(lo16)
     assert np.linalg.norm(g - go16) <= 1e-4 * np.linalg.norm(go16)
     # and against the unrounded binary32 weights (the stated 2e-2)
     lo, go = O.mlp_loss_grad(params[:5187].astype(np.float64), _xin(feat, params), label)
     assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 5000, 200_003])
+def test_tensor_core_gradient(B, n):
+    # the tcgen05 gradient (layer 2's forward product, back-propagation and weight gradient as
+    # BF16 MMAs; 128-sample tiles, a ragged last tile, and at 200,003 samples several tiles per
+    # CTA accumulated in TMEM) against the oracle's binary64 gradient with the same rounded
+    # weights, block by block of the parameter vector so that a wrong operand in one product
+    # (W2's gradient comes only from the MMA, b2 and W1 only through it) fails on its own.
+    # Taking hi.hi alone for the weight gradient would leave a relative error near 2^-9.
+    rng = np.random.default_rng(100 + n)
+    feat = rng.standard_normal((n, 12)) * rng.uniform(0.5, 3, 12) + rng.uniform(-2, 2, 12)
+    _, params, _ = _data(11)
+    label = rng.integers(0, 3, n).astype(np.int32)
+    loss, g = B.bjac_mlp_grad(params, cuda(feat), cuda(label, torch.int32))
+    lo16, go16 = O.mlp_loss_grad(_bf16(params[:5187]), _xin(feat, params), label)
+    assert np.all(np.isfinite(g))
+    assert abs(loss - lo16) <= 1e-5 * abs(lo16)
+    parts = {"W1": (0, 768), "b1": (768, 832), "W2": (832, 4928), "b2": (4928, 4992), "W3": (4992, 5184),
+             "b3": (5184, 5187)}
+    for name, (a, b) in parts.items():
+        ref = go16[a:b]
+        assert np.linalg.norm(g[a:b] - ref) <= 1e-4 * np.linalg.norm(ref) + 1e-9, name
+    # the same weights on CUDA cores
+    _, gc = B.bjac_mlp_grad(params, cuda(feat), cuda(label, torch.int32), tensor_cores=False)
+    assert np.linalg.norm(g - gc) <= 1e-4 * np.linalg.norm(gc)
+
+
+def test_gradient_rejects_unknown_mode(B):
+    feat, params, label = _data(3)
+    g = np.zeros(5187, np.float32)
+    dfeat, dlabel = cuda(feat), cuda(label, torch.int32)
+    for mode in (-1, 3):
+        rc = B.lib().bjac_mlp_grad(params.ctypes.data, mode, dfeat.data_ptr(), dlabel.data_ptr(), len(feat),
+                                   g.ctypes.data, None, None)
+        assert rc == B.ERR_INVALID_ARG
 
 
 def test_logits_match_oracle(B):

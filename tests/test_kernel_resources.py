@@ -30,6 +30,7 @@ LOOP_KERNELS = [
     ("k_update_r", 32),
     ("k_flex_beta", 32),
     ("k_mlp_tc", 128),      # the selector's tensor-core forward pass: 4 CTAs of 128 threads per SM
+    ("k_mlp_grad_tc", 255),  # its tensor-core gradient: one CTA of 128 threads per SM, no spills
 ]
 # kernels known to spill a few bytes: the binary32 register applies hold two 4 KB blocks per
 # warp (k_apply_reg, and the speculative aMP apply, which also holds the binary64 path); the
@@ -66,7 +67,7 @@ def _resources(src, tmp):
 def resources(tmp_path_factory):
     tmp = str(tmp_path_factory.mktemp("ptxas"))
     with cf.ThreadPoolExecutor(4) as ex:
-        parts = list(ex.map(lambda s: _resources(s, tmp), ["sell.cu", "apply.cu", "update.cu", "mlp.cu"]))
+        parts = list(ex.map(lambda s: _resources(s, tmp), ["sell.cu", "apply.cu", "update.cu", "mlp.cu", "mlp_grad_tc.cu"]))
     res = {}
     for p in parts:
         res.update(p)
