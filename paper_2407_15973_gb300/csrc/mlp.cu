@@ -81,12 +81,12 @@ __global__ void __launch_bounds__(kTcNT) k_mlp_tc(const float *params, int nb, c
     const uint32_t tm = s.tmem;
     const uint32_t a_hi = smem_u32(s.a_hi), a_lo = smem_u32(s.a_lo), bw = smem_u32(s.w2);
     constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kH2);
-    const int ntiles = (nb + kTcM - 1) / kTcM;
+    const int ntiles = (int)(((long long)nb + kTcM - 1) / kTcM);
     unsigned phase = 0;
     int tile = blockIdx.x;
     bool failed = false;
     for (; tile < ntiles; tile += gridDim.x) {
-        const int b = tile * kTcM + t;
+        const long long b = (long long)tile * kTcM + t;
         float x[kFeat];
 #pragma unroll
         for (int k = 0; k < kFeat; ++k)
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kTcNT) k_mlp_tc(const float *params, int nb, c
         // freed, and mark this tile and the CTA's later ones as not evaluated
         if (t == 0) (void)mbar_wait_bounded(&s.bar, phase);
         for (; tile < ntiles; tile += gridDim.x) {
-            const int b = tile * kTcM + t;
+            const long long b = (long long)tile * kTcM + t;
             if (b >= nb) continue;
             if (SELECT) fmt[b] = 0xFF;
             else
@@ -181,9 +181,9 @@ __global__ void __launch_bounds__(kTcNT) k_mlp_tc(const float *params, int nb, c
 }
 
 static int mlp_tc_grid(int nb) {
-    int g = (nb + kTcM - 1) / kTcM;
+    long long g = ((long long)nb + kTcM - 1) / kTcM;
     if (g > sm_count() * 4) g = sm_count() * 4;
-    return g < 1 ? 1 : g;
+    return g < 1 ? 1 : (int)g;
 }
 
 int launch_mlp_select(const float *params, int nb, const double *feat, const double *kap, double safety_theta,

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kGNT, 1) k_mlp_grad_tc(const float *params, co
     const uint32_t sh_hi = smem_u32(s.h1t_hi), sh_lo = smem_u32(s.h1t_lo);
     const uint32_t sd_hi = smem_u32(s.d3t_hi), sd_lo = smem_u32(s.d3t_lo);
     const float inv_n = 1.0f / (float)N;
-    const int ntiles = (N + kGM - 1) / kGM;
+    const int ntiles = (int)(((long long)N + kGM - 1) / kGM);
     unsigned phase = 0;
     bool failed = false, first = true;
     double loss_t = 0.0;                       // this thread's samples, in tile order
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kGNT, 1) k_mlp_grad_tc(const float *params, co
     float *row = s.stage + (size_t)t * kSW;    // this sample's staging row
     int par = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, par ^= 1) {
-        const int smp = tile * kGM + t;
+        const long long smp = (long long)tile * kGM + t;
         const bool valid = smp < N;
         float x[kFeat];
 #pragma unroll
@@ -427,9 +427,9 @@ __global__ void __launch_bounds__(kGNT, 1) k_mlp_grad_tc(const float *params, co
 }
 
 int mlp_grad_tc_grid(int N) {
-    int g = (N + kGM - 1) / kGM;
+    long long g = ((long long)N + kGM - 1) / kGM;
     if (g > sm_count()) g = sm_count();
-    return g < 1 ? 1 : g;
+    return g < 1 ? 1 : (int)g;
 }
 
 int launch_mlp_grad_tc(const float *dparams, const double *feat, const int32_t *label, int N, float *partial,

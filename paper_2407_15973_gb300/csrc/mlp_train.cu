@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kTrainNT) k_mlp_grad(const float *params, int 
           *gb3 = g + kOffB3;
     const float inv_n = 1.0f / (float)N;
     double loss = 0.0;
-    for (int s = gw; s < N; s += nw) {
+    for (long long s = gw; s < N; s += nw) {
         const float xk = lane < kFeat ? (float)((feat[(size_t)s * kFeat + lane] - (double)m.mu[lane]) / (double)m.sd[lane])
                                       : 0.0f;
         // forward: two hidden units per lane (o = lane, lane + 32)
@@ -164,10 +164,10 @@ __global__ void k_mlp_reduce_adam(const float *partial, int nwarps, float *grad,
 }
 
 static int grad_launch(int N) {
-    int g = (N + kTrainWarps - 1) / kTrainWarps;
+    long long g = ((long long)N + kTrainWarps - 1) / kTrainWarps;
     const int cap = sm_count() * 4;
     if (g > cap) g = cap;
-    return g < 1 ? 1 : g;
+    return g < 1 ? 1 : (int)g;
 }
 
 // partial gradients (kMlpWeights floats each) that the gradient pass of `mode` writes
@@ -289,7 +289,7 @@ __global__ void k_mlp_logits(const float *params, int bf16, const double *feat, 
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int s = gw; s < N; s += nw) {
+    for (long long s = gw; s < N; s += nw) {
         const float xk = lane < kFeat ? (float)((feat[(size_t)s * kFeat + lane] - (double)m.mu[lane]) / (double)m.sd[lane])
                                       : 0.0f;
         float a0 = m.b1[lane], a1 = m.b1[lane + 32];
@@ -327,9 +327,9 @@ extern "C" int bjac_mlp_logits(const float *params, int32_t bf16_weights, const 
         const int rc = launch_mlp_logits_tc(dp, N, feat, dout, st);
         if (rc != MPBJAC_OK) return rc;
     } else {
-        int g = (N + 7) / 8;
+        long long g = ((long long)N + 7) / 8;
         if (g > sm_count() * 4) g = sm_count() * 4;
-        k_mlp_logits<<<g, 256, 0, st>>>(dp, bf16_weights ? 1 : 0, feat, N, dout);
+        k_mlp_logits<<<(int)g, 256, 0, st>>>(dp, bf16_weights ? 1 : 0, feat, N, dout);
         MPB_CUDA(cudaGetLastError());
     }
     MPB_CUDA(cudaMemcpyAsync(logits, dout, sizeof(float) * (size_t)N * kCls, cudaMemcpyDeviceToHost, st));
