@@ -249,41 +249,46 @@ __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0
 // buffer; its CTA 0 zeroes the slots up to kMaxGrid that no CTA wrote) and no final
 // reduction: the kernel that consumes alpha sums them itself, in every CTA, in one fixed order
 // whatever the CTA's size: 256 lanes, lane v adding slots v, v + 256, ... in turn (the zero
-// slots come last and change nothing), a butterfly within each group of 32 lanes, then the 8
-// group sums in order (the order of a single 256-thread CTA's block sum over the partials).
+// slots come last and change nothing); then one warp, lane l adding the sums of lanes
+// l, l + 32, ..., l + 224 in turn, and a butterfly over the warp. On sm_103a the FP64 pipe
+// does 2 lanes per clock per SM, so every FP64 instruction of a warp counts: this order takes
+// about 42 of them per CTA, against 88 when each group of 32 lanes ends in its own butterfly.
 // Every CTA gets the same sigma and alpha = rho / sigma; CTA 0 records them in S. When sigma is
 // not a positive finite number, every CTA returns false and CTA 0 records the breakdown, so all
 // of them leave before any ticket. Every thread of the CTA must call it.
 constexpr int kSpPartOff = 3 * kMaxGrid;
 __device__ __forceinline__ bool loop_alpha(SolverState *S, const double *spart, double &alpha) {
-    __shared__ double s_grp[8];
+    __shared__ double s_lane[256];
     __shared__ double s_alpha;
     __shared__ int s_ok;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    static_assert(kMaxGrid >= 256, "every lane has a first slot");
     const double rho = threadIdx.x == 0 ? S->rho : 0.0;
-    for (int g = warp; g < 8; g += nwarp) {
-        double v = 0.0;
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+        double a = __ldg(spart + 2 * v);       // written by the previous kernel: read-only here
 #pragma unroll
-        for (int k = 0; k < (kMaxGrid + 255) / 256; ++k) {
-            const int c = 32 * g + lane + 256 * k;
-            if (c < kMaxGrid) v += __ldg(spart + 2 * c);     // written by the previous kernel: read-only here
+        for (int k = 1; k < (kMaxGrid + 255) / 256; ++k) {
+            const int c = v + 256 * k;
+            if (c < kMaxGrid) a += __ldg(spart + 2 * c);
         }
-        v = warp_sum(v);
-        if (lane == 0) s_grp[g] = v;
+        s_lane[v] = a;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double t = s_lane[lane];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) t += s_grp[g];
-        const bool ok = finite_pos(t);
-        const double a = ok ? rho / t : 0.0;
-        s_ok = ok;
-        s_alpha = a;
-        if (blockIdx.x == 0) {
-            S->sigma = t;
-            if (ok) S->alpha = a;
-            else S->state = kBreakdownSigma;
+        for (int j = 1; j < 8; ++j) t += s_lane[lane + 32 * j];
+        t = warp_sum(t);
+        if (lane == 0) {
+            const bool ok = finite_pos(t);
+            const double a = ok ? rho / t : 0.0;
+            s_ok = ok;
+            s_alpha = a;
+            if (blockIdx.x == 0) {
+                S->sigma = t;
+                if (ok) S->alpha = a;
+                else S->state = kBreakdownSigma;
+            }
         }
     }
     __syncthreads();
