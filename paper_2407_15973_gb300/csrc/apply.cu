@@ -438,10 +438,16 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_reg(PSet
     if (threadIdx.x == 0)
         for (int k = 0; k < nv; ++k) io.part[nv * blockIdx.x + k] = b[k];
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, nv, s_red);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, nv, s_red + kNT);
-    const double t3 = flex ? reduce_partials<kNT>(io.part + 2, gridDim.x, nv, s_red + 2 * kNT) : 0.0;
-    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1, flex, t3);
+    double t[3] = {0.0, 0.0, 0.0};
+    if constexpr (flex) {
+        reduce_partials_to0<kNT, 3>(io.part, gridDim.x, nv, s_red, t);
+    } else {
+        double t2[2];
+        reduce_partials_to0<kNT, 2>(io.part, gridDim.x, nv, s_red, t2);
+        t[0] = t2[0];
+        t[1] = t2[1];
+    }
+    if (threadIdx.x == 0) apply_finish<MODE>(t[0], t[1], io, S, 1, flex, t[2]);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -547,10 +553,16 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_mix32(PSet P, ApplyIO io, Solv
     if (threadIdx.x == 0)
         for (int k = 0; k < nv; ++k) io.part[nv * blockIdx.x + k] = b[k];
     if (!last_cta(io.ticket)) return;
-    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, nv, s_red);
-    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, nv, s_red + kNT);
-    const double t3 = flex ? reduce_partials<kNT>(io.part + 2, gridDim.x, nv, s_red + 2 * kNT) : 0.0;
-    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, 1, flex, t3);
+    double t[3] = {0.0, 0.0, 0.0};
+    if constexpr (flex) {
+        reduce_partials_to0<kNT, 3>(io.part, gridDim.x, nv, s_red, t);
+    } else {
+        double t2[2];
+        reduce_partials_to0<kNT, 2>(io.part, gridDim.x, nv, s_red, t2);
+        t[0] = t2[0];
+        t[1] = t2[1];
+    }
+    if (threadIdx.x == 0) apply_finish<MODE>(t[0], t[1], io, S, 1, flex, t[2]);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -673,10 +685,10 @@ __global__ void __launch_bounds__(kNT, sizeof(QT) == 2 ? 4 : 3) k_apply_spec(PSe
     if (threadIdx.x == 0)
         for (int k = 0; k < NV; ++k) io.part[NV * blockIdx.x + k] = b[k];
     if (!last_cta(io.ticket)) return;
-    const double t_rho = reduce_partials<kNT>(io.part, gridDim.x, NV, s_red);
-    const double t_rr = SPEC ? reduce_partials<kNT>(io.part + 1, gridDim.x, NV, s_red + kNT) : 0.0;
-    const double t_qz = FLEX ? reduce_partials<kNT>(io.part + 2, gridDim.x, NV, s_red + 2 * kNT) : 0.0;
+    double tv[NV];
+    reduce_partials_to0<kNT, NV>(io.part, gridDim.x, NV, s_red, tv);
     if (threadIdx.x != 0) return;
+    const double t_rho = tv[0], t_rr = SPEC ? tv[1] : 0.0, t_qz = FLEX ? tv[NV - 1] : 0.0;
     if (SPEC) {
         // the recurrence residual of this iteration: relres, convergence, the set it picks
         S->iter += 1;

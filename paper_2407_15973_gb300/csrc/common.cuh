@@ -243,6 +243,24 @@ __device__ __forceinline__ double reduce_partials(const double *part, int count,
     return block_sum<NT>(v, sm);
 }
 
+// The sums over i < count of part[i * stride + k], k < NV (per-CTA partials written by other
+// CTAs), in a fixed order, valid in thread 0 only: each thread adds every NT-th partial in
+// turn, then warp 0 adds the NT per-thread sums (cta_sum_to0) and ends in one butterfly. On
+// the 2-lane FP64 pipe that is about 36 FP64 warp instructions per value, against about 128
+// for reduce_partials (a butterfly in every warp, then every thread adding the warp sums); the
+// last CTA of a loop kernel runs it while the next kernel waits. sm: NV * NT doubles.
+template <int NT, int NV>
+__device__ __forceinline__ void reduce_partials_to0(const double *part, int count, int stride, double *sm,
+                                                    double (&out)[NV]) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = threadIdx.x < count ? __ldcg(part + (size_t)threadIdx.x * stride + k) : 0.0;
+    for (int i = threadIdx.x + NT; i < count; i += NT)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + (size_t)i * stride + k);
+    cta_sum_to0<NT, NV>(v, sm, out);
+}
+
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e308; }
 
 // The loop SpMV leaves one partial sum of p.q per CTA (stride 2, at kSpPartOff in the part

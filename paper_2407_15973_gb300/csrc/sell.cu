@@ -232,9 +232,15 @@ __global__ void __launch_bounds__(kSpNT, 6) k_spmv_sell(int n, int nslices, cons
         return;
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
-    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+    double t[2] = {0.0, 0.0};
+    if (RES) {
+        reduce_partials_to0<kSpNT, 2>(part, gridDim.x, 2, red, t);
+    } else {
+        double t1[1];
+        reduce_partials_to0<kSpNT, 1>(part, gridDim.x, 2, red, t1);
+        t[0] = t1[0];
+    }
+    if (threadIdx.x == 0) spmv_finish<KIND>(t[0], t[1], out, S);
 }
 
 // The same SpMV with the first chunk (up to 8 entries per row) of a warp's next slice loaded
@@ -341,9 +347,15 @@ __global__ void __launch_bounds__(kSpNT, 3) k_spmv_sell_pf(int n, int nslices, c
         return;
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
-    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+    double t[2] = {0.0, 0.0};
+    if (RES) {
+        reduce_partials_to0<kSpNT, 2>(part, gridDim.x, 2, red, t);
+    } else {
+        double t1[1];
+        reduce_partials_to0<kSpNT, 1>(part, gridDim.x, 2, red, t1);
+        t[0] = t1[0];
+    }
+    if (threadIdx.x == 0) spmv_finish<KIND>(t[0], t[1], out, S);
 }
 
 // ----------------------------------------------------------------------------------------

@@ -205,9 +205,15 @@ __global__ void __launch_bounds__(kSpNT) k_spmv(int n, int nnz, const int32_t *_
         return;
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
-    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+    double tv[2] = {0.0, 0.0};
+    if (RES) {
+        reduce_partials_to0<kSpNT, 2>(part, gridDim.x, 2, red, tv);
+    } else {
+        double t1[1];
+        reduce_partials_to0<kSpNT, 1>(part, gridDim.x, 2, red, t1);
+        tv[0] = t1[0];
+    }
+    if (threadIdx.x == 0) spmv_finish<KIND>(tv[0], tv[1], out, S);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -347,9 +353,15 @@ __global__ void __launch_bounds__(kSpNT) k_spmv_warp(int n, int nnz, const int32
         return;
     }
     if (!last_cta(ticket)) return;
-    const double t1 = reduce_partials<kSpNT>(part, gridDim.x, 2, red);
-    const double t2 = RES ? reduce_partials<kSpNT>(part + 1, gridDim.x, 2, red + kSpNT) : 0.0;
-    if (threadIdx.x == 0) spmv_finish<KIND>(t1, t2, out, S);
+    double tv[2] = {0.0, 0.0};
+    if (RES) {
+        reduce_partials_to0<kSpNT, 2>(part, gridDim.x, 2, red, tv);
+    } else {
+        double t1[1];
+        reduce_partials_to0<kSpNT, 1>(part, gridDim.x, 2, red, t1);
+        tv[0] = t1[0];
+    }
+    if (threadIdx.x == 0) spmv_finish<KIND>(tv[0], tv[1], out, S);
 }
 
 // ----------------------------------------------------------------------------------------

@@ -59,8 +59,10 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
     cta_sum_to0<kNT, 1>(v, red, bsum);
     if (threadIdx.x == 0) part[blockIdx.x] = bsum[0];
     if (!last_cta(&S->tickets[kTicketUpdR])) return;
-    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
+    double tv[1];
+    reduce_partials_to0<kNT, 1>(part, gridDim.x, 1, red, tv);
     if (threadIdx.x != 0) return;
+    const double t = tv[0];
     S->iter += 1;
     S->x_pending = 1;
     S->rr = t;
@@ -147,8 +149,10 @@ __global__ void __launch_bounds__(kNT) k_flex_beta(int n, const double *__restri
     cta_sum_to0<kNT, 1>(v, red, bsum);
     if (threadIdx.x == 0) part[blockIdx.x] = bsum[0];
     if (!last_cta(&S->tickets[kTicketFlex])) return;
-    const double t = reduce_partials<kNT>(part, gridDim.x, 1, red);
+    double tv[1];
+    reduce_partials_to0<kNT, 1>(part, gridDim.x, 1, red, tv);
     if (threadIdx.x != 0) return;
+    const double t = tv[0];
     const double beta = -S->alpha * t / S->rho_prev;
     if (!(fabs(beta) < 1.0e308)) S->state = kBreakdown;
     else S->beta = beta;
