@@ -79,22 +79,40 @@ __global__ void __launch_bounds__(kNT) k_update_r(int n, const double *__restric
 // The state it reads was final before this kernel started, so thread 0 of CTA 0 sets the
 // graph's while-condition without any grid-wide step (x_pending is cleared by the next
 // SpMV). z and p are 16-byte aligned (handle memory); x is the caller's vector and is checked.
+// Each thread's first pair of p and x is loaded before the programmatic-launch wait: the only
+// kernel that may still run then is this kernel's predecessor in the loop (an apply, the
+// residual update or the flexible beta), and none of those writes p or x; the kernels that do
+// (this kernel one iteration back, the initial apply) have completed. z is written by the
+// predecessor and is read after the wait. S->x and S->l2_keep are set before the solve.
 __global__ void __launch_bounds__(kNT) k_update_xp(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    SolverState *S, cudaGraphConditionalHandle cond, int use_cond) {
+    double *__restrict__ x = S->x;
+    const uint64_t pol = vec_policy(S->l2_keep);
+    const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
+    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    const int n2 = n >> 1;
+    const double2 *z2 = reinterpret_cast<const double2 *>(z);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    double2 p0 = make_double2(0.0, 0.0), x0 = make_double2(0.0, 0.0);
+    if (vec && gid < n2) {
+        p0 = ld_vec2(p2 + gid, pol);
+        x0 = ld_vec2(x2 + gid, pol);
+    }
     pdl_enter();
     const int xp = S->x_pending;
     const int run = S->state == kRunning;
-    double *__restrict__ x = S->x;
     const double alpha = S->alpha, beta = S->beta;
-    const uint64_t pol = vec_policy(S->l2_keep);
-    const int gid = blockIdx.x * kNT + threadIdx.x, stride = gridDim.x * kNT;
-    if ((xp | run) && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        const int n2 = n >> 1;
-        const double2 *z2 = reinterpret_cast<const double2 *>(z);
-        double2 *p2 = reinterpret_cast<double2 *>(p);
-        double2 *x2 = reinterpret_cast<double2 *>(x);
+    if ((xp | run) && vec) {
+        if (gid < n2) {
+            if (xp) st_vec2(x2 + gid, make_double2(fma(alpha, p0.x, x0.x), fma(alpha, p0.y, x0.y)), pol);
+            if (run) {
+                const double2 zv = ld_vec2(z2 + gid, pol);
+                st_vec2(p2 + gid, make_double2(fma(beta, p0.x, zv.x), fma(beta, p0.y, zv.y)), pol);
+            }
+        }
 #pragma unroll 2
-        for (int i = gid; i < n2; i += stride) {
+        for (int i = gid + stride; i < n2; i += stride) {
             const double2 pv = ld_vec2(p2 + i, pol);
             if (xp) {
                 double2 xv = ld_vec2(x2 + i, pol);
