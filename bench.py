@@ -284,7 +284,7 @@ def run_ours(args, rank, world, dist):
         from paper_2407_15973_gb300 import selector as SEL
         if os.path.exists(SEL.DEFAULT_WEIGHTS):
             table["mlp"] = dict(select=B.SELECT_MLP, mlp_params=SEL.load(), safety_theta=SEL.load_safety_theta())
-        # BASELINE's 128^3 configuration names blocks of 32 and of 64
+        # the 128^3 workload is also measured with blocks of 64 rows
         bp64 = PB.uniform_blocks(n, 64)
         table["uniform-fp64-bs64"] = dict(select=B.SELECT_UNIFORM, block_ptr=bp64)
         for f in ("fp32", "bf16"):
