@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_generic(PSet lo, PSet hi, Appl
     pdl_enter();
     __shared__ __align__(16) double s_r[kWarps][128];
     __shared__ __align__(16) float s_rh[kWarps][128];
-    __shared__ double s_red[2 * kNT];
+    __shared__ double s_red[kWarps];
     int use_low = io.set;
     if (MODE != kApplyStandalone) {
         if (S->state != kRunning) return;
@@ -122,17 +122,16 @@ __global__ void __launch_bounds__(kNT, 3) k_apply_generic(PSet lo, PSet hi, Appl
         __syncwarp();
     }
     if (MODE == kApplyStandalone && io.out == nullptr) return;
-    const double v[2] = {rho, rr};
-    double b[2];
-    cta_sum_to0<kNT, 2>(v, s_red, b);
+    const double b1 = block_sum<kNT>(rho, s_red);
+    const double b2 = block_sum<kNT>(rr, s_red);
     if (threadIdx.x == 0) {
-        io.part[2 * blockIdx.x] = b[0];
-        io.part[2 * blockIdx.x + 1] = b[1];
+        io.part[2 * blockIdx.x] = b1;
+        io.part[2 * blockIdx.x + 1] = b2;
     }
     if (!last_cta(io.ticket)) return;
-    double t[2];
-    reduce_partials_to0<kNT, 2>(io.part, gridDim.x, 2, s_red, t);
-    if (threadIdx.x == 0) apply_finish<MODE>(t[0], t[1], io, S, use_low);
+    const double t1 = reduce_partials<kNT>(io.part, gridDim.x, 2, s_red);
+    const double t2 = reduce_partials<kNT>(io.part + 1, gridDim.x, 2, s_red);
+    if (threadIdx.x == 0) apply_finish<MODE>(t1, t2, io, S, use_low);
 }
 
 // ----------------------------------------------------------------------------------------

@@ -376,27 +376,22 @@ __global__ void __launch_bounds__(kNT, MINB) k_pcg_batched(BatchDev d) {
         }
     };
     // Fixed-order sums of system s's tile partials by the whole CTA (every thread of the CTA
-    // must call it; the results are valid in thread 0 only): each thread adds every kNT-th
-    // tile partial, then warp 0 adds the per-thread sums (cta_sum_to0). One CTA per system
-    // keeps the largest systems' sums short.
-    __shared__ double s_sum[2 * kNT];
+    // must call it; the results are valid in every thread). One CTA per system keeps the
+    // largest systems' sums short.
+    __shared__ double s_sum[kWarps];
     auto sys_sum2 = [&](int s, double &a, double &b2) {
-        double v[2] = {0.0, 0.0};
+        double va = 0.0, vb = 0.0;
         for (int t = d.sys_tile[s] + threadIdx.x; t < d.sys_tile[s + 1]; t += kNT) {
-            v[0] += __ldcg(d.part + 2 * t);
-            v[1] += __ldcg(d.part + 2 * t + 1);
+            va += __ldcg(d.part + 2 * t);
+            vb += __ldcg(d.part + 2 * t + 1);
         }
-        double o[2];
-        cta_sum_to0<kNT, 2>(v, s_sum, o);
-        a = o[0];
-        b2 = o[1];
+        a = block_sum<kNT>(va, s_sum);
+        b2 = block_sum<kNT>(vb, s_sum);
     };
     auto sys_sum = [&](int s) {
-        double v[1] = {0.0};
-        for (int t = d.sys_tile[s] + threadIdx.x; t < d.sys_tile[s + 1]; t += kNT) v[0] += __ldcg(d.part + 2 * t);
-        double o[1];
-        cta_sum_to0<kNT, 1>(v, s_sum, o);
-        return o[0];
+        double va = 0.0;
+        for (int t = d.sys_tile[s] + threadIdx.x; t < d.sys_tile[s + 1]; t += kNT) va += __ldcg(d.part + 2 * t);
+        return block_sum<kNT>(va, s_sum);
     };
 
     // which list length is current: it alternates at every list build; the loop ends with an
